@@ -1,0 +1,333 @@
+"""Parameter-set and polynomial design for the normalize-and-square Softmax circuit.
+
+This module plays the role the paper gives to its external tools (the HEaaN parameter
+preset and Sollya, Sec. 5.1.1-5.1.2): it fixes the RNS prime chains and computes the
+polynomial approximations the circuit evaluates.  Its outputs are plain data files
+under ``params/`` that the CUDA library and the independent CPU oracle both read as
+inputs; neither side runs this code at evaluation time.
+
+* Prime chains: primes q = 1 (mod 2N) near 2^b (Sec. 5.1.1, Table 4 gives only
+  log(QP) <= 1555, N = 2^16, h = 192; the split into levels is this design's choice).
+* exp on [-A, 0] (Sec. 3.4, Table 2): minimax in the Chebyshev basis, degree 2^t - 1.
+* x^{-1/2} (Sec. 5.1.2): weighted minimax minimising max |sqrt(v) P(v) - 1|, with the
+  approximate-renormalisation intervals [(1-a)^2/n, (1+a)^2] of Sec. 5.1.2 and the
+  wider first interval [n exp(-M/2^(k-1)), n] of Sec. 3.4.2.
+* EvalMod (bootstrapping): Chebyshev interpolant of cos(2 pi (K u - 1/4) / 2^r), followed
+  by r double-angle steps, giving sin(2 pi x) for x = K u.
+
+Minimax here is the discrete minimax on a dense Chebyshev-distributed grid, solved as a
+linear program (scipy HiGHS) instead of Sollya's Remez exchange.
+
+Run ``python -m paper_2410_11184_gb300.design`` to regenerate ``params/*.json``.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+PARAMS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "params")
+
+
+# ----------------------------------------------------------------------------- primes
+def is_prime(n: int) -> bool:
+    """Deterministic Miller-Rabin for n < 2^64 (bases 2..37 suffice)."""
+    if n < 2:
+        return False
+    small = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+    for p in small:
+        if n % p == 0:
+            return n == p
+    d, s = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        s += 1
+    for a in small:
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(s - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def primes_below(two_n: int, bits: int, count: int, used: set) -> list:
+    """Largest primes q < 2^bits with q = 1 mod 2N, not in ``used``."""
+    out = []
+    k = ((1 << bits) - 2) // two_n
+    while len(out) < count:
+        q = k * two_n + 1
+        if q < (1 << bits) and q not in used and is_prime(q):
+            out.append(q)
+            used.add(q)
+        k -= 1
+    return out
+
+
+def primes_alternating(two_n: int, bits: int, count: int, used: set) -> list:
+    """Primes q = 1 mod 2N nearest to 2^bits, taken alternately below and above so that
+    the running product stays close to 2^(bits * i) (keeps CKKS scales near 2^bits)."""
+    centre = 1 << bits
+    k_up = centre // two_n + 1
+    k_dn = centre // two_n
+    out = []
+    take_up = False
+    while len(out) < count:
+        if take_up:
+            while True:
+                q = k_up * two_n + 1
+                k_up += 1
+                if q not in used and is_prime(q):
+                    break
+        else:
+            while True:
+                q = k_dn * two_n + 1
+                k_dn -= 1
+                if q not in used and is_prime(q):
+                    break
+        out.append(q)
+        used.add(q)
+        take_up = not take_up
+    return out
+
+
+def make_chain(name, log_n, q0_bits, groups, p_bits, alpha, h, sigma, log_scale, bts,
+               max_logqp=None):
+    """Build one prime chain.  ``groups`` is a list of (label, bits, count) for q1.. in
+    order of level; consecutive groups with equal ``bits`` share one alternating family."""
+    two_n = 2 << log_n
+    used = set()
+    q0 = primes_below(two_n, q0_bits, 1, used)
+    qs = list(q0)
+    labels = ["base"]
+    i = 0
+    while i < len(groups):
+        bits = groups[i][1]
+        j = i
+        total = 0
+        while j < len(groups) and groups[j][1] == bits:
+            total += groups[j][2]
+            j += 1
+        fam = primes_alternating(two_n, bits, total, used)
+        qs += fam
+        for g in groups[i:j]:
+            labels += [g[0]] * g[2]
+        i = j
+    ps = primes_below(two_n, p_bits, alpha, used)
+    logqp = sum(math.log2(q) for q in qs) + sum(math.log2(p) for p in ps)
+    # keep log(QP) within the security bound: swap the prime furthest above its 2^b
+    # for the next free prime below 2^b of the same size until the bound holds
+    while max_logqp is not None and logqp > max_logqp:
+        i = max(range(1, len(qs)), key=lambda t: qs[t] / 2.0 ** round(math.log2(qs[t])))
+        bits = round(math.log2(qs[i]))
+        repl = primes_below(two_n, bits, 1, used)[0]
+        used.discard(qs[i])
+        qs[i] = repl
+        logqp = sum(math.log2(q) for q in qs) + sum(math.log2(p) for p in ps)
+    chain = {
+        "name": name,
+        "log_n": log_n,
+        "q": [str(q) for q in qs],
+        "p": [str(p) for p in ps],
+        "q_role": labels,
+        "alpha": alpha,
+        "h": h,
+        "sigma": sigma,
+        "log_scale": log_scale,
+        "log_qp": logqp,
+    }
+    chain.update(bts)
+    return chain
+
+
+def build_chains():
+    chains = {}
+    # Toy, insecure, test-only: 1 x 60 + 20 x 40 scaling + 3 x 60 special, no bootstrapping.
+    chains["toy"] = make_chain(
+        "toy", 12, 60, [("user", 40, 20)], 60, 3, 64, 3.2, 40,
+        {"user_top_level": 20, "bootstrap": 0})
+    # 128-bit-security size (log QP <= 1555, N = 2^16, h = 192), full-slot bootstrapping.
+    # Level map (StC-first bootstrapping): q0 | StC 1..3 | user 4..12 | CtS 13..15 | EvalMod 16..24
+    bts_layout = {
+        "user_top_level": 12, "bootstrap": 1, "stc_levels": 3, "cts_levels": 3,
+        "evalmod_levels": 9, "bts_min_level": 3,
+    }
+    chains["fgb16"] = make_chain(
+        "fgb16", 16, 60,
+        [("stc", 42, 3), ("user", 42, 9), ("cts", 58, 3), ("evalmod", 58, 9)],
+        59, 5, 192, 3.2, 42, dict(bts_layout), max_logqp=1555.0)
+    # Same layout at N = 2^12 (insecure, test-only) so the bootstrapping path can be
+    # checked limb for limb against the oracle in seconds.
+    chains["toybts"] = make_chain(
+        "toybts", 12, 60,
+        [("stc", 42, 3), ("user", 42, 9), ("cts", 58, 3), ("evalmod", 58, 9)],
+        59, 5, 64, 3.2, 42, dict(bts_layout), max_logqp=1555.0)
+    return chains
+
+
+# ---------------------------------------------------------------- Chebyshev utilities
+def cheb_vander(u: np.ndarray, deg: int) -> np.ndarray:
+    """Matrix of T_0..T_deg evaluated at u (u in [-1, 1])."""
+    V = np.empty((len(u), deg + 1))
+    V[:, 0] = 1.0
+    if deg >= 1:
+        V[:, 1] = u
+    for k in range(2, deg + 1):
+        V[:, k] = 2.0 * u * V[:, k - 1] - V[:, k - 2]
+    return V
+
+
+def cheb_grid(npts: int) -> np.ndarray:
+    """Chebyshev-extrema-distributed points on [-1, 1] plus the end points."""
+    return np.cos(np.pi * np.arange(npts) / (npts - 1))[::-1]
+
+
+def weighted_minimax(f, w, a, b, deg, npts=None):
+    """Discrete weighted minimax: minimise max_x |w(x) (sum c_i T_i(u(x)) - f(x))| over a
+    dense grid of [a, b], u(x) = (2x - a - b) / (b - a); solved as an LP."""
+    from scipy.optimize import linprog
+
+    npts = npts or max(3000, 40 * (deg + 1))
+    u = cheb_grid(npts)
+    x = 0.5 * (b - a) * u + 0.5 * (a + b)
+    V = cheb_vander(u, deg)
+    wx = w(x)
+    fx = f(x)
+    WV = V * wx[:, None]
+    wf = wx * fx
+    ones = np.ones((npts, 1))
+    A_ub = np.vstack([np.hstack([WV, -ones]), np.hstack([-WV, -ones])])
+    b_ub = np.concatenate([wf, -wf])
+    cost = np.zeros(deg + 2)
+    cost[-1] = 1.0
+    res = linprog(cost, A_ub=A_ub, b_ub=b_ub, bounds=[(None, None)] * (deg + 2),
+                  method="highs")
+    if not res.success:
+        raise RuntimeError("minimax LP failed: " + res.message)
+    coeffs = res.x[:-1]
+    # measured error on a much finer uniform+Chebyshev grid
+    uu = np.concatenate([np.linspace(-1, 1, 40001), cheb_grid(40001)])
+    xx = 0.5 * (b - a) * uu + 0.5 * (a + b)
+    err = np.max(np.abs(w(xx) * (cheb_vander(uu, deg) @ coeffs - f(xx))))
+    return coeffs, float(err)
+
+
+def cheb_interp(g, deg):
+    """Chebyshev interpolant of g on [-1, 1] at the deg+1 Chebyshev nodes."""
+    n = deg + 1
+    theta = np.pi * (np.arange(n) + 0.5) / n
+    gv = g(np.cos(theta))
+    c = np.array([2.0 / n * np.sum(gv * np.cos(k * theta)) for k in range(n)])
+    c[0] *= 0.5
+    uu = np.linspace(-1, 1, 200001)
+    err = np.max(np.abs(cheb_vander(uu, deg) @ c - g(uu)))
+    return c, float(err)
+
+
+def hexlist(c):
+    return [float(v).hex() for v in c]
+
+
+# ------------------------------------------------------------------ Softmax plans
+def softmax_k(M: float, n: int) -> int:
+    """k = ceil(log M - log ln n) (Thm. 3.3)."""
+    return int(math.ceil(math.log2(M) - math.log2(math.log(n))))
+
+
+def design_softmax(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
+    """Polynomials of Alg. 2 / Alg. 3 for inputs in [-M, 0]^n with k iterations."""
+    A = M / 2.0 ** k
+    # y0 = exp(x / 2^k), x in [-M, 0]; Chebyshev variable u = 2x/M + 1.
+    ce, ee = weighted_minimax(lambda u: np.exp(A * (u - 1.0) / 2.0), lambda u: np.ones_like(u),
+                              -1.0, 1.0, exp_deg)
+    polys = [{"kind": "exp", "a": -1.0, "b": 1.0, "deg": exp_deg, "coeffs": hexlist(ce),
+              "err": ee}]
+    iters = []
+    # Iteration 1: S = sum y0^2 in [n e^{-2A}, n]; v = S / n in [e^{-2A}, 1].
+    lo = math.exp(-2.0 * A) * (1.0 - ee) ** 2
+    hi = (1.0 + ee) ** 2
+    alpha = None
+    for j, d in enumerate(inv_degs, start=1):
+        if j > 1:
+            lo = (1.0 - alpha) ** 2 / n
+            hi = (1.0 + alpha) ** 2
+        a = lo * (1.0 - margin)
+        b = hi * (1.0 + margin)
+        c, eps = weighted_minimax(lambda v: v ** -0.5, lambda v: v ** 0.5, a, b, d)
+        alpha = 2.0 * eps + eps * eps
+        gain_s = 1.0 / n if j == 1 else 1.0
+        iters.append({
+            "deg": d, "a": a, "b": b, "coeffs": hexlist(c), "eps": eps, "alpha": alpha,
+            # v = gain_s * S is the polynomial input; lambda = P(v) * sqrt(gain_s).
+            "gain_s": gain_s,
+            # the mask carries sqrt(gain_s) * gain_l so that lambda * gain_l <= ~1 at
+            # bootstrapping; the factor gain_l is removed by scale bookkeeping.
+            "gain_l": 1.0 / math.sqrt(n),
+        })
+    return {
+        "name": name, "chain": chain_name, "n": n, "M": M, "k": k, "A": A,
+        "exp": polys[0], "iters": iters,
+        # every bootstrapping input is multiplied by this factor inside SlotToCoeff and the
+        # factor is removed from the output by scale bookkeeping: it lowers q_0 / (scale *
+        # message) and so the EvalMod error, while keeping the sin() linearisation error
+        # (2 pi boost Delta / q_0)^2 / 6 below 2^-25 for messages of magnitude <= 1
+        "bts_boost": 16.0,
+    }
+
+
+def design_evalmod(K, r, deg):
+    """cos(2 pi (K u - 1/4) / 2^r) on u in [-1, 1]; r double angles give sin(2 pi K u)."""
+    g = lambda u: np.cos(2.0 * np.pi * (K * u - 0.25) / 2.0 ** r)
+    c, err = cheb_interp(g, deg)
+    return {"K": K, "r": r, "deg": deg, "coeffs": hexlist(c), "err": err}
+
+
+def build_all(write=True):
+    chains = build_chains()
+    plans = {
+        # config: toy N=2^12, 128 Softmax of dim 16 on [-8, 0], 2 rounds, no bootstrapping
+        "cfg1_n16_M8": design_softmax("cfg1_n16_M8", "toy", 16, 8.0, 2, 7, [7, 31]),
+        # N=2^16, dim 256 on [-128, 0]: k = 5, exp depth 4, x^{-1/2} depths 6, 5x3, 7 (Table 3)
+        "n256_M128": design_softmax("n256_M128", "fgb16", 256, 128.0, 5, 15, [63, 31, 31, 31, 127]),
+        "n128_M64": design_softmax("n128_M64", "fgb16", 128, 64.0, softmax_k(64, 128), 15,
+                                   [63] + [15] * (softmax_k(64, 128) - 2) + [127]),
+        # bootstrapping-path checks at N=2^12: dim 16 on [-32, 0], k = 4
+        "toybts_n16_M32": design_softmax("toybts_n16_M32", "toybts", 16, 32.0, 4, 15,
+                                         [15, 15, 15, 31]),
+    }
+    evalmod = {"fgb16": design_evalmod(25.0, 3, 63), "toybts": design_evalmod(25.0, 3, 63)}
+    if write:
+        os.makedirs(PARAMS_DIR, exist_ok=True)
+        with open(os.path.join(PARAMS_DIR, "chains.json"), "w") as fh:
+            json.dump(chains, fh, indent=1)
+        with open(os.path.join(PARAMS_DIR, "plans.json"), "w") as fh:
+            json.dump(plans, fh, indent=1)
+        with open(os.path.join(PARAMS_DIR, "evalmod.json"), "w") as fh:
+            json.dump(evalmod, fh, indent=1)
+    return chains, plans, evalmod
+
+
+def load_params():
+    """Read the committed parameter files."""
+    out = []
+    for fn in ("chains.json", "plans.json", "evalmod.json"):
+        with open(os.path.join(PARAMS_DIR, fn)) as fh:
+            out.append(json.load(fh))
+    return tuple(out)
+
+
+if __name__ == "__main__":
+    chains, plans, evalmod = build_all(write=True)
+    for c in chains.values():
+        print(c["name"], "logQP=%.2f" % c["log_qp"], "nq=%d np=%d" % (len(c["q"]), len(c["p"])))
+    for p in plans.values():
+        print(p["name"], "k=%d exp_err=%.3g" % (p["k"], p["exp"]["err"]),
+              [("%d" % it["deg"], "%.3g" % it["alpha"]) for it in p["iters"]])
+    for k, e in evalmod.items():
+        print(k, "evalmod err=%.3g" % e["err"])
