@@ -84,6 +84,8 @@ def lib():
                                     u64p, intp, dblp]
         L.orc_softmax.argtypes = [C.c_void_p, intp, dblp, dblp, dblp, intp, dblp, dblp, u64p, C.c_int,
                                   C.c_int, C.c_double, intp, dblp]
+        L.orc_mix.restype = C.c_uint64
+        L.orc_mix.argtypes = [C.c_uint64]
         L.orc_counters.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
         L.orc_reset_counters.argtypes = [C.c_void_p]
         _lib = L

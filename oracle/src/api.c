@@ -331,3 +331,5 @@ void orc_counters(orc_ctx *c, long *out) {
     out[0] = c->n_ks; out[1] = c->n_rot; out[2] = c->n_hmult; out[3] = c->n_rescale; out[4] = c->n_bts;
 }
 void orc_reset_counters(orc_ctx *c) { c->n_ks = c->n_rot = c->n_hmult = c->n_rescale = c->n_bts = 0; }
+
+uint64_t orc_mix(uint64_t z) { return splitmix_mix(z); }

@@ -73,6 +73,7 @@ static void sk_limb(const orc_ctx *c, int t, const int8_t *s, uint64_t *out) {
 }
 
 int keygen_secret(orc_ctx *c, uint64_t seed) {
+    if (c->h < 1 || c->h > N_) { snprintf(c->err, sizeof c->err, "keygen: h=%d, N=%d", c->h, N_); return -1; }
     c->seed = seed;
     c->s = calloc(N_, 1);
     sample_hwt(N_, c->h, seed, c->s);
