@@ -1,0 +1,150 @@
+/*
+ * he_gb300 -- C ABI of the GB300 (sm_103a) RNS-CKKS library for the normalize-and-square
+ * homomorphic Softmax of Cho, Hanrot, Kim, Park, Stehle (arXiv 2410.11184).
+ *
+ * Conventions
+ *   - Return value: 0 on success, a negative HE_E* code on failure; he_last_error() gives a
+ *     message.  Invalid arguments never reach a kernel.
+ *   - Ciphertexts (he_ct) live in device memory owned by the caller (e.g. torch tensors):
+ *     data = [n_ct][2][level+1][N] uint64, RNS limbs q_0..q_level, NTT (evaluation) form.
+ *     level and scale are metadata the library reads and updates.
+ *   - Everything runs on the stream given at context creation (a cudaStream_t, or NULL for
+ *     the legacy default stream).  Calls return after enqueueing unless stated otherwise;
+ *     host-buffer calls synchronise the stream.
+ *   - The library owns the context, its tables and the evaluation keys (device memory it
+ *     allocates); he_context_destroy frees them.
+ *   - Section/equation references are to the paper (CCS 2024 version).
+ */
+#ifndef HE_GB300_H
+#define HE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HE_OK 0
+#define HE_EINVAL (-1)   /* bad argument (sizes, levels, n not a power of two, ...) */
+#define HE_ELEVEL (-2)   /* not enough levels left for the requested operation */
+#define HE_ENOMEM (-3)   /* device allocation failed */
+#define HE_ECUDA (-4)    /* a CUDA call failed */
+#define HE_ENOKEY (-5)   /* a needed evaluation key was not generated */
+#define HE_ETIMEOUT (-6) /* a bounded device wait gave up */
+
+typedef struct he_ctx he_ctx;
+
+/* CKKS parameters (Sec. 2.2; Table 4 for the 128-bit-security size).  Q = q_0 ... q_{n_q-1},
+ * P = p_0 ... p_{n_p-1}; alpha = n_p primes per key-switching digit. */
+typedef struct {
+    int log_n;                 /* ring degree N = 2^log_n, N/2 slots */
+    int n_q;
+    const uint64_t *q;         /* n_q primes, q_i = 1 mod 2N, < 2^61 */
+    int n_p;
+    const uint64_t *p;         /* n_p special primes */
+    int h;                     /* Hamming weight of the ternary secret */
+    double sigma;              /* Gaussian error parameter */
+    int log_scale;             /* nominal scale Delta = 2^log_scale */
+    int user_top_level;        /* level of fresh and bootstrapped ciphertexts */
+    int bootstrap;             /* 1: build bootstrapping keys and tables */
+    int stc_levels, cts_levels, bts_min_level;
+    double em_K;               /* EvalMod range: x = t/q_0 in [-K, K] */
+    int em_r;                  /* double-angle steps */
+    int em_deg;                /* Chebyshev degree of cos(2 pi (K u - 1/4) / 2^r) */
+    const double *em_coeffs;   /* em_deg + 1 coefficients */
+} he_params;
+
+/* Softmax circuit parameters (Alg. 2 / Alg. 3; Sec. 5.1.2 for the polynomials). */
+typedef struct {
+    int n;                     /* Softmax dimension (power of two dividing N/2) */
+    int k;                     /* normalize-and-square rounds */
+    double M;                  /* inputs in [-M, 0] (Assumption 3.5) */
+    int exp_deg;
+    const double *exp_coeffs;  /* exp(x/2^k) in the Chebyshev basis of u = 2x/M + 1 */
+    const int *inv_deg;        /* k degrees */
+    const double *inv_coeffs;  /* concatenated Chebyshev coefficients of x^{-1/2} per round */
+    const double *inv_a, *inv_b;     /* interval of round j */
+    const double *gain_s, *gain_l;   /* input gain of round j, bootstrapping gain of lambda_j */
+    double bts_boost;          /* input gain applied inside every bootstrapping */
+} he_softmax_plan;
+
+typedef struct {
+    uint64_t *data;            /* device pointer, [n_ct][2][level+1][N] */
+    int level;
+    double scale;
+    int n_ct;
+} he_ct;
+
+/* Context: builds NTT, basis-conversion and embedding tables on the device.
+ * cuda_stream: a cudaStream_t (or NULL).  *out receives the handle. */
+int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out);
+void he_context_destroy(he_ctx *ctx);
+const char *he_last_error(const he_ctx *ctx);
+int he_ring_degree(const he_ctx *ctx);
+
+/* KeyGen (Sec. 2.2): secret, public key, relinearisation and conjugation keys, rotation keys
+ * for the n_rot slot rotations in rot_steps, and (if bootstrapping) every rotation key that
+ * SlotToCoeff / CoeffToSlot need.  Randomness: counter-based SplitMix64 keyed by seed. */
+int he_keygen(he_ctx *ctx, uint64_t seed, const int *rot_steps, int n_rot);
+/* Rotation keys a Softmax of dimension n over m ciphertexts needs (strides L 2^i, Alg. 3). */
+int he_keygen_softmax(he_ctx *ctx, int n, int m);
+
+/* Enc (Sec. 2.2) of L = m N0 / n Softmax inputs x [L][n] (row-major FP64, host memory,
+ * count = L n), packed as in Sec. 4.2 into m ciphertexts at user_top_level with scale
+ * (2/M) q_top.  out->data must hold m * 2 * (user_top_level+1) * N words (device). */
+int he_encrypt(he_ctx *ctx, const double *x, size_t count, int n, int m, double M, uint64_t seed, he_ct *out);
+/* Dec of m ciphertexts into y [L][n] (host), unpacking Sec. 4.2. Synchronises. */
+int he_decrypt(he_ctx *ctx, const he_ct *cts, int n, double *y, size_t count);
+/* Dec of one ciphertext (index ct) into N/2 complex slots (host, interleaved re/im). */
+int he_decrypt_slots(he_ctx *ctx, const he_ct *cts, int ct, double *slots);
+/* Enc of N/2 complex slots (host, interleaved) into ciphertext index ct of out at level/scale. */
+int he_encrypt_slots(he_ctx *ctx, const double *slots, int level, double scale, uint64_t seed, int ct_index,
+                     he_ct *out, int ct);
+
+/* Softmax (Alg. 2 with Alg. 3, many-ciphertext form of Sec. 4.2) on the m = cts->n_ct
+ * ciphertexts, in place: the output level is lower, data is overwritten, level/scale updated.
+ * batched = 1: every operation runs over all m ciphertexts in one launch (key read once);
+ * batched = 0: the same operation list, one ciphertext at a time. */
+int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched);
+
+/* ---- the hot-path operations, one call each (device buffers as above) ---- */
+/* negacyclic NTT (inverse=0) / inverse NTT of n_limb limbs mod q_0.. in place (device) */
+int he_ntt(he_ctx *ctx, uint64_t *data, int n_poly, int n_limb, int inverse);
+/* coefficient-form host copy of a ciphertext batch [n_ct][2][level+1][N] (synchronises) */
+int he_ct_to_coeff(he_ctx *ctx, const he_ct *x, uint64_t *host);
+/* loads a coefficient-form host ciphertext batch into x (x->data, level, scale, n_ct set) */
+int he_ct_from_coeff(he_ctx *ctx, const uint64_t *host, he_ct *x);
+/* encode N/2 complex slots (interleaved, host) at scale into a device plaintext [level+1][N] (NTT) */
+int he_encode(he_ctx *ctx, const double *slots, double scale, int level, uint64_t *pt);
+int he_add(he_ctx *ctx, he_ct *a, const he_ct *b);                 /* a += b */
+int he_mul_plain(he_ctx *ctx, he_ct *a, const uint64_t *pt);       /* a *= pt (no rescale) */
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out);           /* out at level-1 */
+/* tensor + relinearise + rescale (Mult of Sec. 2.2) */
+int he_hmult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out);
+/* relinearise a degree-2 batch d [n_ct][3][level+1][N] into out (no rescale) */
+int he_relinearize(he_ctx *ctx, const uint64_t *d, int level, int n_ct, he_ct *out);
+/* Rot(ct, r): slot j of the output holds slot (j + r) mod N/2 (Sec. 2.2) */
+int he_rotate(he_ctx *ctx, const he_ct *a, int r, he_ct *out);
+int he_conjugate(he_ctx *ctx, const he_ct *a, he_ct *out);
+/* p(u) = sum c_k T_k(u) at level_out with scale scale_out (levels: ceil(log2(deg+1))) */
+int he_poly_eval(he_ctx *ctx, const he_ct *u, const double *coeffs, int deg, int level_out, double scale_out,
+                 he_ct *out);
+/* one level of SlotToCoeff (inverse=0) or CoeffToSlot (inverse=1), split into nlev levels */
+int he_lintrans(he_ctx *ctx, const he_ct *a, int nlev, int inverse, int which, double gain, double pt_scale,
+                he_ct *out);
+/* bootstrapping: out (level user_top) encrypts gain * message with scale out_scale */
+int he_bootstrap(he_ctx *ctx, const he_ct *a, double gain, double out_scale, he_ct *out);
+/* ModRaise of a level-0 batch to level top */
+int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
+
+/* operation counters since creation: [key switches, rotations, hmults, rescales, bootstraps] */
+int he_counters(const he_ctx *ctx, long *out5);
+/* bounded device wait self test: a kernel polls a flag nobody sets for at most max_iter polls
+ * and returns HE_ETIMEOUT; the context stays usable. */
+int he_selftest_bounded_wait(he_ctx *ctx, long max_iter);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,74 @@
+// Device-side building blocks for the RNS-CKKS kernels (sm_103a).
+//
+// Residues are uint64 in [0, q) with q < 2^61 (NTT-friendly primes q = 1 mod 2N).
+//  - mul_mod   : Barrett reduction of the 128-bit product with mu = floor(2^(s+63) / q),
+//                s = bitlen(q): the quotient estimate is at most 2 below the true one.
+//  - mul_shoup : Shoup's multiplication by a fixed w with w' = floor(w 2^64 / q).
+// Limb maps describe a batch of polynomials stored as [poly][limb][N]: limb l of the batch
+// uses modulus index prime[l % nper].
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define HE_MAX_LIMBS 64
+#define HE_MAX_MODS 64
+
+struct ModC {
+    uint64_t q;
+    uint64_t mu;   // floor(2^(s+63) / q)
+    int s;         // bit length of q
+    int pad;
+};
+
+struct LimbMap {
+    int nper;                       // limbs per polynomial
+    int prime[HE_MAX_LIMBS];        // modulus index of limb i of each polynomial
+};
+
+__device__ __forceinline__ uint64_t he_mulhi(uint64_t a, uint64_t b) {
+    return (uint64_t)__umul64hi((unsigned long long)a, (unsigned long long)b);
+}
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+    uint64_t c = a + b;
+    return c >= q ? c - q : c;
+}
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return a >= b ? a - b : a + q - b;
+}
+
+__device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
+
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t wp, uint64_t q) {
+    uint64_t h = he_mulhi(a, wp);
+    uint64_t r = a * w - h * q;
+    return r >= q ? r - q : r;
+}
+
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const ModC &m) {
+    uint64_t lo = a * b, hi = he_mulhi(a, b);
+    uint64_t x1 = (lo >> (m.s - 2)) | (hi << (66 - m.s));
+    uint64_t qe = he_mulhi(x1, m.mu) >> 1;
+    uint64_t r = lo - qe * m.q;
+    if (r >= m.q) r -= m.q;
+    if (r >= m.q) r -= m.q;
+    return r;
+}
+
+// x (any uint64) mod q
+__device__ __forceinline__ uint64_t reduce_u64(uint64_t x, const ModC &m) {
+    return x >= m.q ? x % m.q : x;
+}
+
+// signed 64-bit value mod q
+__device__ __forceinline__ uint64_t reduce_i64(int64_t x, const ModC &m) {
+    if (x >= 0) return reduce_u64((uint64_t)x, m);
+    uint64_t r = reduce_u64((uint64_t)(-(x + 1)), m);   // -(x+1) >= 0
+    // x = -(r' + 1) with r' = -(x+1); x mod q = q - 1 - (r' mod q)
+    return m.q - 1 - r;
+}
+
+__device__ __forceinline__ int brev_bits(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+#define HE_CHECK_LAUNCH() (cudaGetLastError())

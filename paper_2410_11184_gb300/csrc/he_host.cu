@@ -1,0 +1,1650 @@
+// Host orchestration of the RNS-CKKS hot path and the C ABI declared in include/he_gb300.h.
+//
+// Ciphertext batches live on the device as [n_ct][2][level+1][N] uint64 in NTT form.  The
+// host only sequences kernel launches on the context stream and tracks levels and scales;
+// all polynomial arithmetic runs in he_kernels.cu.  Scale bookkeeping, encoded constants and
+// the order of operations follow the definitions written out in the comments below (the
+// same definitions the CPU reference follows), so that results are bit-identical.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "he_kernels.cuh"
+#include "../../include/he_gb300.h"
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+static const double HE_PI = 3.14159265358979323846;
+
+// ------------------------------------------------------------------------- host arithmetic
+static uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)(((u128)a * b) % q); }
+static uint64_t h_pow(uint64_t a, uint64_t e, uint64_t q) {
+    uint64_t r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = h_mulmod(r, a, q);
+        a = h_mulmod(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+static uint64_t h_inv(uint64_t a, uint64_t q) { return h_pow(a % q, q - 2, q); }
+static uint64_t h_shoup(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
+static uint64_t h_red128(i128 x, uint64_t q) {
+    i128 r = x % (i128)q;
+    if (r < 0) r += q;
+    return (uint64_t)r;
+}
+static i128 h_round(double x) { return (i128)nearbyint(x); }
+static int ilog2c(int x) { int r = 0; while ((1 << r) < x) r++; return r; }
+
+// primitive 2N-th root of unity: the first g^((q-1)/2N) (g = 2, 3, ...) with N-th power -1
+static uint64_t h_root(uint64_t q, int n) {
+    uint64_t e = (q - 1) / (2 * (uint64_t)n);
+    for (uint64_t g = 2; g < 1000000; g++) {
+        uint64_t x = h_pow(g, e, q);
+        if (h_pow(x, n, q) == q - 1) return x;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------------- context
+struct DCt;
+using DPtr = std::shared_ptr<uint64_t>;
+
+struct LtPlain {
+    int a, b;          // giant index, baby index
+    DPtr pt;           // [level+1][N] NTT
+};
+struct LtLevel {
+    int hmin, g, E;
+    std::vector<int> baby;           // baby steps b present
+    std::vector<LtPlain> pts;
+};
+
+struct he_ctx {
+    int logN = 0, N = 0, n0 = 0, nq = 0, np = 0, alpha = 0, h = 0, nm = 0;
+    double sigma = 3.2;
+    int log_scale = 40, user_top = 0, bootstrap = 0, stc_levels = 3, cts_levels = 3, bts_min = 3;
+    double em_K = 0;
+    int em_r = 0, em_deg = 0;
+    std::vector<double> em_c;
+    std::vector<uint64_t> mods;
+    std::vector<ModC> modc;
+    ModC *d_mods = nullptr;
+    uint64_t *d_tw = nullptr, *d_ninv = nullptr;
+    std::vector<std::vector<size_t>> cv_off;
+    uint64_t *d_cv = nullptr;
+    uint64_t *d_mdcv = nullptr, *d_pinv = nullptr, *d_qlinv = nullptr;
+    int *d_pidx = nullptr;
+    double2 *d_zeta = nullptr;
+    int *d_rg = nullptr;
+    std::vector<double2> zeta;
+    std::vector<int> rg;
+    uint64_t *d_cdt = nullptr;
+    int cdt_len = 0;
+    uint64_t *d_radix = nullptr, *d_radinv = nullptr;
+    double *d_qd = nullptr;
+    bool have_keys = false;
+    uint64_t seed = 0;
+    uint64_t *d_s = nullptr, *d_pk = nullptr;
+    std::map<int, uint64_t *> keys;
+    int ndig_top = 0;
+    std::map<std::string, LtLevel> lt_cache;
+    cudaStream_t st = nullptr;
+    std::string err;
+    long cnt[5] = {0, 0, 0, 0, 0};
+    int max_grid = 152 * 16;
+};
+
+struct HeErr {
+    int code;
+    std::string msg;
+};
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) throw HeErr{HE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+#define LAUNCH_CHECK() CK(cudaGetLastError())
+#define REQUIRE(cond, code, msg)                                          \
+    do {                                                                  \
+        if (!(cond)) throw HeErr{code, msg};                              \
+    } while (0)
+
+static DPtr dalloc(he_ctx *c, size_t words) {
+    void *p = nullptr;
+    if (words == 0) words = 1;
+    cudaError_t e = cudaMallocAsync(&p, words * 8, c->st);
+    if (e != cudaSuccess) throw HeErr{HE_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
+    cudaStream_t st = c->st;
+    return DPtr((uint64_t *)p, [st](uint64_t *q) { cudaFreeAsync(q, st); });
+}
+
+static dim3 grid_for(he_ctx *c, long total) {
+    long b = (total + 255) / 256;
+    return dim3((unsigned)std::max(1L, std::min(b, (long)c->max_grid)));
+}
+
+// ------------------------------------------------------------------------- limb maps
+static LimbMap qmap(int L) {
+    LimbMap m;
+    m.nper = L;
+    for (int i = 0; i < L; i++) m.prime[i] = i;
+    return m;
+}
+static LimbMap extmap(he_ctx *c, int L) {
+    LimbMap m;
+    m.nper = L + c->alpha;
+    for (int i = 0; i < L; i++) m.prime[i] = i;
+    for (int k = 0; k < c->alpha; k++) m.prime[L + k] = c->nq + k;
+    return m;
+}
+static LimbMap pmap(he_ctx *c) {
+    LimbMap m;
+    m.nper = c->alpha;
+    for (int k = 0; k < c->alpha; k++) m.prime[k] = c->nq + k;
+    return m;
+}
+static LimbMap allmap(he_ctx *c) {
+    LimbMap m;
+    m.nper = c->nm;
+    for (int i = 0; i < c->nm; i++) m.prime[i] = i;
+    return m;
+}
+static LimbMap single(int p) {
+    LimbMap m;
+    m.nper = 1;
+    m.prime[0] = p;
+    return m;
+}
+
+// ------------------------------------------------------------------------- NTT launches
+static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long poly_stride, bool inverse) {
+    if (count <= 0) return;
+    int logN1 = c->logN / 2;
+    int N1 = 1 << logN1, N2 = c->N >> logN1;
+    int C = std::min(16, N2);
+    int R = std::max(1, std::min(N1, 2048 / N2));
+    dim3 g1(N2 / C, count), g2(N1 / R, count);
+    size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
+    if (!inverse) {
+        k_ntt_cols_fwd<<<g1, 256, sm1, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, C);
+        k_ntt_rows_fwd<<<g2, 256, sm2, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, R);
+    } else {
+        k_ntt_rows_inv<<<g2, 256, sm2, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, R);
+        k_ntt_cols_inv<<<g1, 256, sm1, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->d_ninv,
+                                                 c->logN, logN1, C);
+    }
+    LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------------- ciphertexts
+struct DCt {
+    DPtr buf;              // owner (empty when viewing caller memory)
+    uint64_t *d = nullptr;
+    int level = 0;
+    double scale = 1.0;
+    int nct = 1;
+    long cs(const he_ctx *c) const { return 2L * (level + 1) * c->N; }   // ciphertext stride
+    long ps(const he_ctx *c) const { return (long)(level + 1) * c->N; }  // polynomial stride
+};
+
+static DCt ct_new(he_ctx *c, int level, int nct, double scale) {
+    DCt x;
+    x.level = level;
+    x.nct = nct;
+    x.scale = scale;
+    x.buf = dalloc(c, (size_t)nct * 2 * (level + 1) * c->N);
+    x.d = x.buf.get();
+    return x;
+}
+
+static DCt ct_view(const he_ct *h) {
+    DCt x;
+    x.d = h->data;
+    x.level = h->level;
+    x.scale = h->scale;
+    x.nct = h->n_ct;
+    return x;
+}
+
+static DCt ct_copy(he_ctx *c, const DCt &a) {
+    DCt y = ct_new(c, a.level, a.nct, a.scale);
+    CK(cudaMemcpyAsync(y.d, a.d, (size_t)a.nct * a.cs(c) * 8, cudaMemcpyDeviceToDevice, c->st));
+    return y;
+}
+
+// copy of a with only limbs 0..level (dropping limbs keeps value mod the smaller Q and scale)
+static DCt ct_drop(he_ctx *c, const DCt &a, int level) {
+    REQUIRE(level <= a.level && level >= 0, HE_ELEVEL, "drop: level");
+    if (level == a.level) return ct_copy(c, a);
+    DCt y = ct_new(c, level, a.nct, a.scale);
+    CK(cudaMemcpy2DAsync(y.d, (size_t)y.ps(c) * 8, a.d, (size_t)a.ps(c) * 8, (size_t)y.ps(c) * 8, 2 * a.nct,
+                         cudaMemcpyDeviceToDevice, c->st));
+    return y;
+}
+
+// one ciphertext of a batch, as a view
+static DCt ct_sub(const he_ctx *c, const DCt &a, int i) {
+    DCt y;
+    y.buf = a.buf;
+    y.d = a.d + (long)i * a.cs(c);
+    y.level = a.level;
+    y.scale = a.scale;
+    y.nct = 1;
+    return y;
+}
+
+static bool scales_match(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
+
+static void ct_add_inplace(he_ctx *c, DCt &a, const DCt &b, bool sub = false) {
+    REQUIRE(a.level == b.level && a.nct == b.nct, HE_EINVAL, "add: level/count mismatch");
+    REQUIRE(scales_match(a.scale, b.scale), HE_EINVAL, "add: scale mismatch");
+    int count = 2 * a.nct * (a.level + 1);
+    LimbMap m = qmap(a.level + 1);
+    long total = (long)count << c->logN;
+    k_add<<<grid_for(c, total), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), b.d, b.ps(c), count, a.level + 1, m,
+                                                  c->d_mods, c->logN, sub ? 1 : 0);
+    LAUNCH_CHECK();
+}
+
+static Scal scal_of(he_ctx *c, i128 k, int L) {
+    Scal s;
+    for (int i = 0; i < L; i++) s.v[i] = h_red128(k, c->mods[i]);
+    return s;
+}
+
+static void ct_mul_int(he_ctx *c, DCt &a, i128 k) {
+    int L = a.level + 1, count = 2 * a.nct * L;
+    Scal s = scal_of(c, k, L);
+    k_mul_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), s, count, L,
+                                                                          qmap(L), c->d_mods, c->logN);
+    LAUNCH_CHECK();
+}
+
+// adds the constant k (every slot, as a constant polynomial) to c0 of every ciphertext
+static void ct_add_const(he_ctx *c, DCt &a, i128 k) {
+    int L = a.level + 1, count = a.nct * L;
+    Scal s = scal_of(c, k, L);
+    k_add_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.cs(c), s, count, L, qmap(L),
+                                                                          c->d_mods, c->logN);
+    LAUNCH_CHECK();
+}
+
+static void ct_mul_plain(he_ctx *c, DCt &a, const uint64_t *pt) {
+    int L = a.level + 1, count = 2 * a.nct * L;
+    k_mul<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), pt, 0, count, L, qmap(L),
+                                                                   c->d_mods, c->logN, 0);
+    LAUNCH_CHECK();
+}
+
+// rescale: r = centred last limb; c_i <- (c_i - r) q_l^{-1}
+static DCt rescale(he_ctx *c, const DCt &a) {
+    int l = a.level, L = l + 1;
+    REQUIRE(l >= 1, HE_ELEVEL, "rescale at level 0");
+    int npoly = 2 * a.nct;
+    DPtr last = dalloc(c, (size_t)npoly * c->N);
+    CK(cudaMemcpy2DAsync(last.get(), (size_t)c->N * 8, a.d + (long)l * c->N, (size_t)L * c->N * 8, (size_t)c->N * 8,
+                         npoly, cudaMemcpyDeviceToDevice, c->st));
+    ntt(c, last.get(), npoly, single(l), c->N, true);
+    DPtr tmp = dalloc(c, (size_t)npoly * l * c->N);
+    long tot = (long)npoly * l << c->logN;
+    k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp.get(), last.get(), npoly, l, qmap(l), c->d_mods,
+                                                           c->mods[l], c->logN);
+    LAUNCH_CHECK();
+    ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false);
+    DCt y = ct_new(c, l - 1, a.nct, a.scale / (double)c->mods[l]);
+    k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, a.d, tmp.get(), npoly, L, qmap(l), c->d_mods,
+                                                        c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
+    LAUNCH_CHECK();
+    c->cnt[3]++;
+    return y;
+}
+
+// ------------------------------------------------------------------------- key switching
+// ModUp of nct polynomials x (NTT form, L limbs, stride sx between polynomials):
+// digits [nct][ndig][L + alpha][N] in NTT form.
+static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
+    int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
+    DPtr tmp = dalloc(c, (size_t)nct * L * c->N);
+    CK(cudaMemcpy2DAsync(tmp.get(), (size_t)L * c->N * 8, x, (size_t)sx * 8, (size_t)L * c->N * 8, nct,
+                         cudaMemcpyDeviceToDevice, c->st));
+    ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true);
+    DPtr dig = dalloc(c, (size_t)nct * nd * nl * c->N);
+    LimbMap em = extmap(c, L);
+    for (int j = 0; j < nd; j++) {
+        int lo = j * al, ds = std::min(al, L - lo);
+        long tot = (long)nct * nl << c->logN;
+        k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N, tmp.get(),
+                                                      (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
+                                                      c->d_cv + c->cv_off[L - 1][j], c->logN);
+        LAUNCH_CHECK();
+    }
+    ntt(c, dig.get(), nct * nd * nl, em, (long)nl * c->N, false);
+    return dig;
+}
+
+// inner product with key (automorphism g applied to the digits when g > 1), ModDown, and
+// accumulation into out (nct ciphertexts at level L-1, stride so)
+static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, const uint64_t *key, uint64_t *out,
+                      long so, bool accumulate) {
+    int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
+    DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
+    k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc.get(), dig, nct, nd, L, al, extmap(c, L),
+                                                                    c->d_mods, key, c->nm, c->nq, g, c->logN);
+    LAUNCH_CHECK();
+    ntt(c, acc.get() + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true);
+    DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
+    long tot = (long)2 * nct * L << c->logN;
+    k_moddown_conv<<<grid_for(c, tot), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
+                                                         c->d_mods, c->d_mdcv, c->nq, c->logN);
+    LAUNCH_CHECK();
+    ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false);
+    k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc.get(), conv.get(), 2 * nct, L, al, qmap(L),
+                                                        c->d_mods, c->d_pinv, c->logN, accumulate ? 1 : 0);
+    LAUNCH_CHECK();
+    c->cnt[0]++;
+}
+
+static const uint64_t *get_key(he_ctx *c, int galois) {
+    auto it = c->keys.find(galois);
+    if (it == c->keys.end()) {
+        char b[96];
+        snprintf(b, sizeof b, "no evaluation key for galois element %d", galois);
+        throw HeErr{HE_ENOKEY, b};
+    }
+    return it->second;
+}
+
+// d: [nct][3][L][N] (ct stride 3 L N) -> ciphertexts (d0 + k0, d1 + k1), scale given
+static DCt relinearize(he_ctx *c, const uint64_t *d, int level, int nct, double scale) {
+    int L = level + 1;
+    DCt y = ct_new(c, level, nct, scale);
+    CK(cudaMemcpy2DAsync(y.d, (size_t)2 * L * c->N * 8, d, (size_t)3 * L * c->N * 8, (size_t)2 * L * c->N * 8, nct,
+                         cudaMemcpyDeviceToDevice, c->st));
+    DPtr dig = ks_modup(c, d + 2L * L * c->N, 3L * L * c->N, nct, L);
+    ks_finish(c, dig.get(), nct, L, 0, get_key(c, 0), y.d, y.cs(c), true);
+    return y;
+}
+
+static void tensor_into(he_ctx *c, uint64_t *d, const DCt &a, const DCt &b, int level, bool accumulate) {
+    int L = level + 1;
+    long tot = (long)a.nct * L << c->logN;
+    k_tensor<<<grid_for(c, tot), 256, 0, c->st>>>(d, 3L * L * c->N, a.d, a.cs(c), b.d, b.cs(c), a.nct, L, qmap(L),
+                                                   c->d_mods, c->logN, accumulate ? 1 : 0);
+    LAUNCH_CHECK();
+}
+
+// tensor, relinearise, rescale; operands at different levels: the higher one is dropped
+static DCt hmult(he_ctx *c, const DCt &a, const DCt &b) {
+    int level = std::min(a.level, b.level);
+    REQUIRE(level >= 1, HE_ELEVEL, "hmult at level 0");
+    REQUIRE(a.nct == b.nct || b.nct == 1 || a.nct == 1, HE_EINVAL, "hmult: batch sizes");
+    int nct = std::max(a.nct, b.nct);
+    DPtr d = dalloc(c, (size_t)nct * 3 * (level + 1) * c->N);
+    if (a.nct == b.nct) {
+        tensor_into(c, d.get(), a, b, level, false);
+    } else {
+        // one operand shared by every ciphertext of the other batch
+        const DCt &many = a.nct > 1 ? a : b, &one = a.nct > 1 ? b : a;
+        for (int i = 0; i < nct; i++)
+            tensor_into(c, d.get() + (long)i * 3 * (level + 1) * c->N, ct_sub(c, many, i), one, level, false);
+    }
+    DCt r = relinearize(c, d.get(), level, nct, a.scale * b.scale);
+    c->cnt[2]++;
+    return rescale(c, r);
+}
+
+// Rot by galois elements: ModUp(c1) once, then for every g: X -> X^g on the digits and c0,
+// inner product with swk(s(X^g) -> s), ModDown.
+static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vector<int> &gal) {
+    int L = x.level + 1;
+    std::vector<DCt> out;
+    DPtr dig;
+    bool need = false;
+    for (int g : gal) need |= g != 1;
+    if (need) dig = ks_modup(c, x.d + (long)L * c->N, x.cs(c), x.nct, L);
+    for (int g : gal) {
+        if (g == 1) {
+            out.push_back(ct_copy(c, x));
+            continue;
+        }
+        const uint64_t *key = get_key(c, g);
+        DCt y = ct_new(c, x.level, x.nct, x.scale);
+        CK(cudaMemsetAsync(y.d, 0, (size_t)y.nct * y.cs(c) * 8, c->st));
+        long tot = (long)x.nct * L << c->logN;
+        k_automorph<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, y.cs(c), x.d, x.cs(c), x.nct * L, L, g, c->logN);
+        LAUNCH_CHECK();
+        ks_finish(c, dig.get(), x.nct, L, g, key, y.d, y.cs(c), true);
+        out.push_back(y);
+        c->cnt[1]++;
+    }
+    return out;
+}
+
+static DCt rotate(he_ctx *c, const DCt &x, int g) { return rotate_hoisted(c, x, std::vector<int>{g})[0]; }
+
+static int galois_for_rot(he_ctx *c, long r) {
+    long n0 = c->n0, m = 2L * c->N;
+    r %= n0;
+    if (r < 0) r += n0;
+    long g = 1;
+    for (long i = 0; i < r; i++) g = (g * 5) % m;
+    return (int)g;
+}
+
+static DCt mod_raise(he_ctx *c, const DCt &a, int top) {
+    REQUIRE(a.level == 0, HE_EINVAL, "mod_raise needs level 0");
+    int npoly = 2 * a.nct, L = top + 1;
+    DPtr x0 = dalloc(c, (size_t)npoly * c->N);
+    CK(cudaMemcpyAsync(x0.get(), a.d, (size_t)npoly * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
+    ntt(c, x0.get(), npoly, single(0), c->N, true);
+    DCt y = ct_new(c, top, a.nct, a.scale);
+    long tot = (long)npoly * L << c->logN;
+    k_modraise<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, x0.get(), npoly, L, qmap(L), c->d_mods, c->mods[0], c->logN);
+    LAUNCH_CHECK();
+    ntt(c, y.d, npoly * L, qmap(L), (long)L * c->N, false);
+    return y;
+}
+
+// ------------------------------------------------------------------------- encoding
+// slots z (N0 complex, host) -> plaintext round(scale t) in NTT form, limbs 0..level
+static DPtr encode(he_ctx *c, const std::vector<double2> &z, double scale, int level) {
+    int n0 = c->n0, L = level + 1;
+    DPtr w = dalloc(c, (size_t)2 * n0);
+    double2 *wd = (double2 *)w.get();
+    CK(cudaMemcpyAsync(wd, z.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice, c->st));
+    dim3 g = grid_for(c, n0 / 2);
+    for (int len = n0; len >= 2; len >>= 1) k_sfft_inv_stage<<<g, 256, 0, c->st>>>(wd, n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+    k_bitrev_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, c->logN - 1);
+    k_scale_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, (double)n0);
+    LAUNCH_CHECK();
+    DPtr pt = dalloc(c, (size_t)L * c->N);
+    k_round_to_limbs<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(pt.get(), 0, wd, scale, L, L, qmap(L),
+                                                                         c->d_mods, c->logN);
+    LAUNCH_CHECK();
+    ntt(c, pt.get(), L, qmap(L), (long)L * c->N, false);
+    return pt;
+}
+
+// device small integers (signed) -> NTT-form residues for the limbs of map
+static void small_to_ntt(he_ctx *c, uint64_t *out, const int64_t *v, const LimbMap &m) {
+    k_small_to_limbs<<<grid_for(c, (long)m.nper << c->logN), 256, 0, c->st>>>(out, 0, v, m.nper, m.nper, m, c->d_mods,
+                                                                               c->logN);
+    LAUNCH_CHECK();
+    ntt(c, out, m.nper, m, (long)m.nper * c->N, false);
+}
+
+enum { DOM_SK = 1, DOM_SK_SIGN = 2, DOM_PK_A = 3, DOM_PK_E = 4, DOM_ENC_V = 5, DOM_ENC_E0 = 6, DOM_ENC_E1 = 7 };
+static uint64_t dom_key(int key_id, int digit, int which) {
+    return 0x100000ULL + ((uint64_t)key_id * 256ULL + (uint64_t)digit) * 2ULL + (uint64_t)which;
+}
+
+static void sample_small(he_ctx *c, int64_t *out, uint64_t seed, uint64_t dom, uint64_t ctr0, int kind) {
+    k_sample_small<<<grid_for(c, c->N), 256, 0, c->st>>>(out, c->N, seed, dom, ctr0, c->d_cdt, c->cdt_len, kind);
+    LAUNCH_CHECK();
+}
+
+static void encrypt_into(he_ctx *c, const std::vector<double2> &z, int level, double scale, uint64_t seed, int ct_index,
+                         uint64_t *out) {
+    REQUIRE(c->have_keys, HE_ENOKEY, "encrypt before keygen");
+    int L = level + 1;
+    DPtr pt = encode(c, z, scale, level);
+    DPtr sm = dalloc(c, 3 * (size_t)c->N);
+    int64_t *v = (int64_t *)sm.get(), *e0 = v + c->N, *e1 = e0 + c->N;
+    uint64_t ctr = (uint64_t)ct_index * c->N;
+    sample_small(c, v, seed, DOM_ENC_V, ctr, 1);
+    sample_small(c, e0, seed, DOM_ENC_E0, ctr, 0);
+    sample_small(c, e1, seed, DOM_ENC_E1, ctr, 0);
+    DPtr lv = dalloc(c, 3 * (size_t)L * c->N);
+    uint64_t *vn = lv.get(), *e0n = vn + (long)L * c->N, *e1n = e0n + (long)L * c->N;
+    LimbMap m = qmap(L);
+    small_to_ntt(c, vn, v, m);
+    small_to_ntt(c, e0n, e0, m);
+    small_to_ntt(c, e1n, e1, m);
+    long tot = (long)L << c->logN;
+    uint64_t *c0 = out, *c1 = out + (long)L * c->N;
+    const uint64_t *pkb = c->d_pk, *pka = c->d_pk + (long)c->nq * c->N;
+    k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, vn, 0, pkb, 0, L, L, m, c->d_mods, c->logN, 0);
+    k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, vn, 0, pka, 0, L, L, m, c->d_mods, c->logN, 0);
+    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, e0n, 0, L, L, m, c->d_mods, c->logN, 0);
+    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, pt.get(), 0, L, L, m, c->d_mods, c->logN, 0);
+    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, c1, 0, e1n, 0, L, L, m, c->d_mods, c->logN, 0);
+    LAUNCH_CHECK();
+}
+
+static std::vector<double2> decrypt_slots(he_ctx *c, const DCt &x, int i) {
+    REQUIRE(c->have_keys, HE_ENOKEY, "decrypt before keygen");
+    int L = x.level + 1;
+    const uint64_t *c0 = x.d + (long)i * x.cs(c), *c1 = c0 + (long)L * c->N;
+    DPtr m = dalloc(c, (size_t)L * c->N);
+    long tot = (long)L << c->logN;
+    k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, c1, 0, c->d_s, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, m.get(), 0, c0, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+    LAUNCH_CHECK();
+    ntt(c, m.get(), L, qmap(L), (long)L * c->N, true);
+    DPtr w = dalloc(c, (size_t)2 * c->n0);
+    double2 *wd = (double2 *)w.get();
+    k_crt_to_double<<<grid_for(c, c->N), 128, 0, c->st>>>(wd, m.get(), L, qmap(L), c->d_mods, c->d_radix, c->d_radinv,
+                                                          c->d_qd, x.scale, c->logN);
+    k_bitrev_c<<<grid_for(c, c->n0), 256, 0, c->st>>>(wd, c->n0, c->logN - 1);
+    for (int len = 2; len <= c->n0; len <<= 1)
+        k_sfft_fwd_stage<<<grid_for(c, c->n0 / 2), 256, 0, c->st>>>(wd, c->n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+    LAUNCH_CHECK();
+    std::vector<double2> z(c->n0);
+    CK(cudaMemcpyAsync(z.data(), wd, sizeof(double2) * c->n0, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return z;
+}
+
+// ------------------------------------------------------------------------- key generation
+static void keygen(he_ctx *c, uint64_t seed) {
+    c->seed = seed;
+    int N = c->N, nm = c->nm;
+    DPtr sint = dalloc(c, N);
+    k_sample_hwt<<<(N + 255) / 256, 256, 256 * 8, c->st>>>((int64_t *)sint.get(), N, c->h, seed, DOM_SK, DOM_SK_SIGN);
+    LAUNCH_CHECK();
+    if (!c->d_s) CK(cudaMalloc(&c->d_s, (size_t)nm * N * 8));
+    small_to_ntt(c, c->d_s, (int64_t *)sint.get(), allmap(c));
+    // public key over Q
+    if (!c->d_pk) CK(cudaMalloc(&c->d_pk, (size_t)2 * c->nq * N * 8));
+    uint64_t *pkb = c->d_pk, *pka = c->d_pk + (long)c->nq * N;
+    DPtr e = dalloc(c, N), el = dalloc(c, (size_t)nm * N);
+    sample_small(c, (int64_t *)e.get(), seed, DOM_PK_E, 0, 0);
+    LimbMap qm = qmap(c->nq);
+    small_to_ntt(c, el.get(), (int64_t *)e.get(), qm);
+    k_sample_uniform<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pka, 0, c->nq, c->nq, qm, c->d_mods, seed,
+                                                                              DOM_PK_A, c->logN);
+    LAUNCH_CHECK();
+    ntt(c, pka, c->nq, qm, (long)c->nq * N, false);
+    Scal z0;
+    memset(&z0, 0, sizeof z0);
+    k_key_combine<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pkb, pka, el.get(), c->d_s, nullptr, z0, c->nq,
+                                                                           0, 0, qm, c->d_mods, c->logN);
+    LAUNCH_CHECK();
+    c->have_keys = true;
+}
+
+static void make_key(he_ctx *c, int galois) {
+    if (c->keys.count(galois)) return;
+    int N = c->N, nm = c->nm, nd = c->ndig_top;
+    uint64_t *key = nullptr;
+    CK(cudaMalloc(&key, (size_t)nd * 2 * nm * N * 8));
+    LimbMap am = allmap(c);
+    DPtr sp = dalloc(c, (size_t)nm * N), e = dalloc(c, N), el = dalloc(c, (size_t)nm * N);
+    long tot = (long)nm << c->logN;
+    if (galois == 0)
+        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, c->d_s, 0, nm, nm, am, c->d_mods, c->logN, 0);
+    else
+        k_automorph<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, nm, nm, galois, c->logN);
+    LAUNCH_CHECK();
+    Scal pm;
+    for (int t = 0; t < nm; t++) {
+        uint64_t q = c->mods[t], v = 1 % q;
+        for (int k = 0; k < c->np; k++) v = h_mulmod(v, c->mods[c->nq + k] % q, q);
+        pm.v[t] = v;
+    }
+    for (int j = 0; j < nd; j++) {
+        uint64_t *b = key + (size_t)(2 * j) * nm * N, *a = key + (size_t)(2 * j + 1) * nm * N;
+        sample_small(c, (int64_t *)e.get(), c->seed, dom_key(galois, j, 1), 0, 0);
+        small_to_ntt(c, el.get(), (int64_t *)e.get(), am);
+        k_sample_uniform<<<grid_for(c, tot), 256, 0, c->st>>>(a, 0, nm, nm, am, c->d_mods, c->seed, dom_key(galois, j, 0),
+                                                               c->logN);
+        LAUNCH_CHECK();
+        ntt(c, a, nm, am, (long)nm * N, false);
+        int dlo = j * c->alpha, dhi = std::min((j + 1) * c->alpha, c->nq);
+        k_key_combine<<<grid_for(c, tot), 256, 0, c->st>>>(b, a, el.get(), c->d_s, sp.get(), pm, nm, dlo, dhi, am,
+                                                            c->d_mods, c->logN);
+        LAUNCH_CHECK();
+    }
+    c->keys[galois] = key;
+}
+
+// ------------------------------------------------------------------------- polynomial evaluation
+// Chebyshev evaluation with exact scale targets (same recursion and constants as the
+// reference definition): see eval() below.
+struct PolyEval {
+    he_ctx *c;
+    std::map<int, DCt> T;
+    int lin;
+
+    DCt adjust(const DCt &x, int lt, double st) {
+        REQUIRE(x.level >= lt + 1, HE_ELEVEL, "adjust: level");
+        DCt y = ct_drop(c, x, lt + 1);
+        double q = (double)c->mods[lt + 1];
+        ct_mul_int(c, y, h_round((st * q) / x.scale));
+        y.scale = st * q;
+        return rescale(c, y);
+    }
+
+    const DCt &getT(int k) {
+        auto it = T.find(k);
+        if (it != T.end()) return it->second;
+        REQUIRE(k >= 1, HE_EINVAL, "getT");
+        if ((k & (k - 1)) == 0) {
+            const DCt &h = getT(k / 2);
+            DCt x = hmult(c, h, h);
+            ct_mul_int(c, x, 2);
+            ct_add_const(c, x, h_round(-x.scale));
+            T[k] = x;
+        } else {
+            int a = 1;
+            while (a * 2 < k) a *= 2;
+            int b = k - a;
+            getT(a);
+            getT(b);
+            getT(a - b);
+            DCt p = hmult(c, T[a], T[b]);
+            ct_mul_int(c, p, 2);
+            DCt s = adjust(T[a - b], p.level, p.scale);
+            ct_add_inplace(c, p, s, true);
+            T[k] = p;
+        }
+        return T[k];
+    }
+
+    static int trim(const std::vector<double> &cf, int d) {
+        while (d > 0 && cf[d] == 0.0) d--;
+        return d;
+    }
+
+    DCt lincomb(const std::vector<double> &cf, int d, int lt, double st) {
+        double q = (double)c->mods[lt + 1];
+        DCt out;
+        bool have = false;
+        for (int k = 1; k <= d; k++) {
+            if (cf[k] == 0.0) continue;
+            const DCt &tk = getT(k);
+            DCt x = ct_drop(c, tk, lt + 1);
+            ct_mul_int(c, x, h_round(((cf[k] * st) * q) / tk.scale));
+            x.scale = st * q;
+            if (!have) {
+                out = x;
+                have = true;
+            } else {
+                ct_add_inplace(c, out, x);
+            }
+        }
+        REQUIRE(have, HE_EINVAL, "lincomb: constant polynomial");
+        ct_add_const(c, out, h_round((cf[0] * st) * q));
+        return rescale(c, out);
+    }
+
+    DCt eval(const std::vector<double> &cf_in, int d, int lt, double st) {
+        d = trim(cf_in, d);
+        REQUIRE(d >= 1, HE_EINVAL, "eval: degree 0");
+        int avail = lin - lt;
+        int j = ilog2c(d + 1);
+        REQUIRE(avail >= j, HE_ELEVEL, "eval: not enough levels");
+        if (d < 8 && avail >= ilog2c(d) + 1) return lincomb(cf_in, d, lt, st);
+        int a = 1 << (j - 1);
+        std::vector<double> q(d - a + 1, 0.0), r(a, 0.0);
+        q[0] = cf_in[a];
+        for (int i = 1; i <= d - a; i++) q[i] = 2.0 * cf_in[a + i];
+        for (int i = 0; i < a; i++) r[i] = cf_in[i];
+        for (int i = a + 1; i <= d; i++) r[2 * a - i] = r[2 * a - i] - cf_in[i];
+        getT(a);
+        int dq = trim(q, d - a);
+        DCt out;
+        if (dq == 0) {
+            std::vector<double> tmp(a + 1, 0.0);
+            tmp[a] = q[0];
+            out = lincomb(tmp, a, lt, st);
+        } else {
+            double sq = (st * (double)c->mods[lt + 1]) / T[a].scale;
+            DCt Q = eval(q, dq, lt + 1, sq);
+            DCt ta = ct_drop(c, T[a], lt + 1);
+            out = hmult(c, ta, Q);
+        }
+        int dr = trim(r, a - 1);
+        if (dr >= 1) {
+            DCt R = eval(r, dr, lt, st);
+            ct_add_inplace(c, out, R);
+        } else {
+            ct_add_const(c, out, h_round(r[0] * out.scale));
+        }
+        return out;
+    }
+};
+
+static DCt poly_eval(he_ctx *c, const DCt &u, const std::vector<double> &cf, int level_out, double scale_out) {
+    PolyEval pe;
+    pe.c = c;
+    pe.T[1] = u;
+    pe.lin = u.level;
+    return pe.eval(cf, (int)cf.size() - 1, level_out, scale_out);
+}
+
+// ------------------------------------------------------------------------- linear transforms
+// SlotToCoeff = butterfly stages of the special FFT (len = 2, 4, ..., N0) without the bit
+// reversal; CoeffToSlot = their inverses in reverse order.  Stages are grouped into nlev
+// levels of consecutive stages; each level is sum_d diag_d (.) Rot(x, d), evaluated by
+// baby-step/giant-step with d = e hmin, e = a g + b.
+struct LtDesc {
+    int nstage;
+    int h[32];
+    int inverse;
+};
+
+static std::vector<LtDesc> lt_levels(he_ctx *c, int nlev, int inverse) {
+    int s = c->logN - 1;
+    std::vector<int> sizes(nlev);
+    int base = s / nlev, rem = s % nlev;
+    for (int g = 0; g < nlev; g++) sizes[g] = base + (g < rem ? 1 : 0);
+    std::vector<LtDesc> fwd(nlev);
+    int h = 1;
+    for (int g = 0; g < nlev; g++) {
+        fwd[g].nstage = sizes[g];
+        fwd[g].inverse = 0;
+        for (int k = 0; k < sizes[g]; k++) {
+            fwd[g].h[k] = h;
+            h <<= 1;
+        }
+    }
+    if (!inverse) return fwd;
+    std::vector<LtDesc> inv(nlev);
+    for (int g = 0; g < nlev; g++) {
+        const LtDesc &f = fwd[nlev - 1 - g];
+        inv[g].nstage = f.nstage;
+        inv[g].inverse = 1;
+        for (int k = 0; k < f.nstage; k++) inv[g].h[k] = f.h[f.nstage - 1 - k];
+    }
+    return inv;
+}
+
+static double2 cmulh(double2 a, double2 b) {
+    double2 r;
+    double re = a.x * b.x - a.y * b.y;
+    double im = a.x * b.y + a.y * b.x;
+    r.x = re;
+    r.y = im;
+    return r;
+}
+
+static double2 lt_twiddle(he_ctx *c, int h, int j) {
+    int lenq = 8 * h, m = 2 * c->N;
+    return c->zeta[(c->rg[j] % lenq) * (m / lenq)];
+}
+
+static void lt_sources(he_ctx *c, int h, int inverse, int i, int *src, double2 *f) {
+    int n0 = c->n0, pos = i % (2 * h);
+    if (pos < h) {
+        double2 t = lt_twiddle(c, h, pos);
+        src[0] = i;
+        src[1] = (i + h) % n0;
+        if (!inverse) {
+            f[0] = make_double2(1.0, 0.0);
+            f[1] = t;
+        } else {
+            f[0] = make_double2(0.5, 0.0);
+            f[1] = make_double2(0.5, 0.0);
+        }
+    } else {
+        int j = pos - h;
+        double2 t = lt_twiddle(c, h, j);
+        src[0] = (i - h + n0) % n0;
+        src[1] = i;
+        if (!inverse) {
+            f[0] = make_double2(1.0, 0.0);
+            f[1] = make_double2(-t.x, -t.y);
+        } else {
+            f[0] = make_double2(t.x * 0.5, -(t.y * 0.5));
+            f[1] = make_double2(-(t.x * 0.5), t.y * 0.5);
+        }
+    }
+}
+
+static int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+static int bsgs_g(int r) { return 1 << ((r + 2) / 2); }
+
+static const LtLevel &lt_prepare(he_ctx *c, const LtDesc &lv, double gain, double pt_scale, int level) {
+    char keyb[160];
+    snprintf(keyb, sizeof keyb, "%d:%d:%d:%a:%a:%d", lv.inverse, lv.nstage, lv.h[0], gain, pt_scale, level);
+    auto it = c->lt_cache.find(keyb);
+    if (it != c->lt_cache.end()) return it->second;
+    int n0 = c->n0, r = lv.nstage;
+    int hmin = lv.h[0];
+    for (int k = 1; k < r; k++) hmin = std::min(hmin, lv.h[k]);
+    int E = (1 << r) - 1;
+    std::vector<double2> diag((size_t)(2 * E + 1) * n0, make_double2(0.0, 0.0));
+    std::vector<char> nz(2 * E + 1, 0);
+    double2 gn = make_double2(gain, 0.0);
+    for (int i = 0; i < n0; i++) {
+        for (int path = 0; path < (1 << r); path++) {
+            double2 fac[32];
+            int idx = i;
+            for (int k = r - 1; k >= 0; k--) {
+                int src[2];
+                double2 f[2];
+                lt_sources(c, lv.h[k], lv.inverse, idx, src, f);
+                int pick = (path >> k) & 1;
+                fac[k] = f[pick];
+                idx = src[pick];
+            }
+            double2 p = make_double2(1.0, 0.0);
+            for (int k = 0; k < r; k++) p = cmulh(p, fac[k]);
+            p = cmulh(p, gn);
+            int off = ((idx - i) % n0 + n0) % n0;
+            int e = off / hmin;
+            if (e > E) e -= n0 / hmin;
+            diag[(size_t)(e + E) * n0 + i] = p;
+        }
+    }
+    for (int e = 0; e <= 2 * E; e++)
+        for (int i = 0; i < n0 && !nz[e]; i++)
+            if (diag[(size_t)e * n0 + i].x != 0.0 || diag[(size_t)e * n0 + i].y != 0.0) nz[e] = 1;
+    LtLevel L;
+    L.hmin = hmin;
+    L.E = E;
+    L.g = bsgs_g(r);
+    std::vector<char> needb(L.g, 0);
+    for (int e = -E; e <= E; e++)
+        if (nz[e + E]) needb[e - floordiv(e, L.g) * L.g] = 1;
+    for (int b = 0; b < L.g; b++)
+        if (needb[b]) L.baby.push_back(b);
+    std::vector<double2> rd(n0);
+    for (int a = floordiv(-E, L.g); a <= floordiv(E, L.g); a++) {
+        for (int b = 0; b < L.g; b++) {
+            int e = a * L.g + b;
+            if (e < -E || e > E || !nz[e + E]) continue;
+            long sh = (long)a * L.g * hmin;
+            const double2 *dv = diag.data() + (size_t)(e + E) * n0;
+            for (int i = 0; i < n0; i++) rd[i] = dv[(((i - sh) % n0) + n0) % n0];
+            LtPlain p;
+            p.a = a;
+            p.b = b;
+            p.pt = encode(c, rd, pt_scale, level);
+            L.pts.push_back(p);
+        }
+    }
+    return c->lt_cache.emplace(keyb, std::move(L)).first->second;
+}
+
+static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain, double pt_scale) {
+    const LtLevel &L = lt_prepare(c, lv, gain, pt_scale, x.level);
+    std::vector<int> gal;
+    for (int b : L.baby) gal.push_back(galois_for_rot(c, (long)b * L.hmin));
+    std::vector<DCt> baby = rotate_hoisted(c, x, gal);
+    std::map<int, int> bidx;
+    for (size_t i = 0; i < L.baby.size(); i++) bidx[L.baby[i]] = (int)i;
+    DCt acc;
+    bool have_acc = false;
+    size_t pi = 0;
+    while (pi < L.pts.size()) {
+        int a = L.pts[pi].a;
+        DCt inner;
+        bool have = false;
+        for (; pi < L.pts.size() && L.pts[pi].a == a; pi++) {
+            DCt t = ct_copy(c, baby[bidx[L.pts[pi].b]]);
+            ct_mul_plain(c, t, L.pts[pi].pt.get());
+            if (!have) {
+                inner = t;
+                have = true;
+            } else {
+                inner.scale = t.scale;
+                ct_add_inplace(c, inner, t);
+            }
+        }
+        inner.scale = x.scale * pt_scale;
+        if (a != 0) inner = rotate(c, inner, galois_for_rot(c, (long)a * L.g * L.hmin));
+        if (!have_acc) {
+            acc = inner;
+            have_acc = true;
+        } else {
+            ct_add_inplace(c, acc, inner);
+        }
+    }
+    return rescale(c, acc);
+}
+
+static std::vector<int> lt_rotation_steps(he_ctx *c, const LtDesc &lv) {
+    int r = lv.nstage, E = (1 << r) - 1, g = bsgs_g(r);
+    int hmin = lv.h[0];
+    for (int k = 1; k < r; k++) hmin = std::min(hmin, lv.h[k]);
+    std::vector<int> out;
+    for (int b = 1; b < g; b++) out.push_back(b * hmin);
+    for (int a = floordiv(-E, g); a <= floordiv(E, g); a++)
+        if (a != 0) out.push_back(a * g * hmin);
+    return out;
+}
+
+// ------------------------------------------------------------------------- bootstrapping
+static DCt bootstrap(he_ctx *c, const DCt &x, double gain, double out_scale) {
+    REQUIRE(c->bootstrap, HE_EINVAL, "bootstrapping not enabled");
+    REQUIRE(x.level >= c->stc_levels, HE_ELEVEL, "bootstrap: level too low");
+    DCt y = ct_drop(c, x, c->stc_levels);
+    std::vector<LtDesc> lv = lt_levels(c, c->stc_levels, 0);
+    for (int g = 0; g < c->stc_levels; g++) y = lt_eval_level(c, y, lv[g], g == 0 ? gain : 1.0, (double)c->mods[y.level]);
+    double d_in = y.scale;
+    int top = c->nq - 1;
+    DCt z = mod_raise(c, y, top);
+    z.scale = (double)c->mods[0];
+    int em_in = top - c->cts_levels;
+    double s_em = (double)c->mods[em_in];
+    lv = lt_levels(c, c->cts_levels, 1);
+    for (int g = 0; g < c->cts_levels; g++) {
+        double gn = g == c->cts_levels - 1 ? 1.0 / (2.0 * c->em_K) : 1.0;
+        double qs = (double)c->mods[z.level];
+        double pts = g == c->cts_levels - 1 ? (qs * s_em) / z.scale : qs;
+        z = lt_eval_level(c, z, lv[g], gn, pts);
+    }
+    DCt cj = rotate(c, z, 2 * c->N - 1);
+    ct_add_inplace(c, z, cj);
+    int lp = c->user_top + c->em_r;
+    double s_f = (out_scale * (double)c->mods[0]) / (2.0 * HE_PI * d_in);
+    double s_in = s_f;
+    for (int i = c->em_r; i >= 1; i--) s_in = sqrt(s_in * (double)c->mods[lp - i + 1]);
+    DCt cc = poly_eval(c, z, c->em_c, lp, s_in);
+    for (int i = 0; i < c->em_r; i++) {
+        DCt sq = hmult(c, cc, cc);
+        ct_mul_int(c, sq, 2);
+        ct_add_const(c, sq, h_round(-sq.scale));
+        cc = sq;
+    }
+    cc.scale = ((cc.scale * (2.0 * HE_PI)) * d_in) / (double)c->mods[0];
+    c->cnt[4]++;
+    return cc;
+}
+
+// ------------------------------------------------------------------------- Softmax circuit
+struct Plan {
+    int n, k, exp_deg;
+    double M, boost;
+    std::vector<double> exp_c;
+    std::vector<int> inv_deg;
+    std::vector<std::vector<double>> inv_c;
+    std::vector<double> a, b, gs, gl;
+};
+
+static double qd(he_ctx *c, int l) { return (double)c->mods[l]; }
+
+static void affine_to_unit(he_ctx *c, DCt &x, double a, double b) {
+    double alpha = 2.0 / (b - a), beta = -(a + b) / (b - a);
+    x.scale = x.scale / alpha;
+    ct_add_const(c, x, h_round(beta * x.scale));
+}
+
+static DCt bts_boosted(he_ctx *c, const Plan &p, const DCt &x, double gain, double out_scale) {
+    DCt y = bootstrap(c, x, gain * p.boost, out_scale / p.boost);
+    y.scale = y.scale * p.boost;
+    return y;
+}
+
+static bool main_bts(he_ctx *c, const Plan &p, int j, int ly) {
+    return c->bootstrap && (ly < c->bts_min + 1 || (j < p.k - 1 && ly - 2 < c->bts_min + 1));
+}
+static bool s_bts(he_ctx *c, const Plan &p, int j, int ly) {
+    return c->bootstrap && ((ly - 1) - ilog2c(p.inv_deg[j] + 1) - 1 < c->bts_min);
+}
+static double y_target(he_ctx *c, const Plan &p, int j, int ly) {
+    double delta = std::ldexp(1.0, c->log_scale);
+    if (j >= p.k || main_bts(c, p, j, ly) || s_bts(c, p, j, ly)) return delta;
+    double ap = (2.0 / (p.b[j] - p.a[j])) * p.gs[j];
+    return sqrt((ap * qd(c, ly - 1)) * qd(c, ly));
+}
+
+static DCt rotsum(he_ctx *c, DCt x, int stride, int nrot) {
+    for (int i = 0; i < nrot; i++) {
+        DCt r = rotate(c, x, galois_for_rot(c, (long)stride << i));
+        ct_add_inplace(c, x, r);
+    }
+    return x;
+}
+
+// ys: the m main-thread ciphertexts, as one batch (batched) or m batches of one
+static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> ys, int m) {
+    int n0 = c->n0, n = p.n;
+    int stride = (int)((long)m * n0 / n);
+    int nrot = ilog2c(n / m);
+    int ut = c->user_top;
+    double delta = std::ldexp(1.0, c->log_scale);
+    for (auto &y : ys) {
+        affine_to_unit(c, y, -p.M, 0.0);
+        int lvl = y.level - ilog2c(p.exp_deg + 1);
+        y = poly_eval(c, y, p.exp_c, lvl, y_target(c, p, 0, lvl));
+    }
+    for (int j = 0; j < p.k; j++) {
+        int ly = ys[0].level;
+        if (main_bts(c, p, j, ly)) {
+            double so = y_target(c, p, j, ut);
+            for (auto &y : ys) y = bts_boosted(c, p, y, 1.0, so);
+            ly = ys[0].level;
+        }
+        // S = Relin(sum_c y_c (x) y_c)
+        int L = ly + 1;
+        DPtr d = dalloc(c, (size_t)3 * L * c->N);
+        bool first = true;
+        for (auto &y : ys) {
+            if (y.nct == 1) {
+                tensor_into(c, d.get(), y, y, ly, !first);
+                first = false;
+            } else {
+                // sum of the per-ciphertext tensors of the batch
+                DPtr dd = dalloc(c, (size_t)y.nct * 3 * L * c->N);
+                tensor_into(c, dd.get(), y, y, ly, false);
+                for (int i = 0; i < y.nct; i++) {
+                    int cnt = 3 * L;
+                    long tot = (long)cnt << c->logN;
+                    if (first && i == 0)
+                        CK(cudaMemcpyAsync(d.get(), dd.get(), (size_t)3 * L * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
+                    else
+                        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), 0, d.get(), 0, dd.get() + (long)i * 3 * L * c->N,
+                                                                    0, cnt, L, qmap(L), c->d_mods, c->logN, 0);
+                    LAUNCH_CHECK();
+                }
+                first = false;
+            }
+        }
+        DCt S = relinearize(c, d.get(), ly, 1, ys[0].scale * ys[0].scale);
+        c->cnt[2]++;
+        S = rescale(c, S);
+        S = rotsum(c, S, stride, nrot);
+        int dj = ilog2c(p.inv_deg[j] + 1);
+        DCt v;
+        if (!s_bts(c, p, j, ly)) {
+            v = S;
+            v.scale = v.scale / p.gs[j];
+        } else {
+            double so = (2.0 / (p.b[j] - p.a[j])) * qd(c, ut);
+            v = bts_boosted(c, p, S, p.gs[j], so);
+        }
+        affine_to_unit(c, v, p.a[j], p.b[j]);
+        int lp = v.level - dj;
+        DCt lam = poly_eval(c, v, p.inv_c[j], lp, delta);
+        bool lam_bts = c->bootstrap && lp - 1 < ly;
+        int llam = lam_bts ? ut : lp - 1;
+        int lz = std::min(llam, ly);
+        double tgt = y_target(c, p, j + 1, lz - 2);
+        double sz = sqrt(tgt * qd(c, lz - 1));
+        double slam = (sz * qd(c, lz)) / ys[0].scale;
+        std::vector<double2> mk(n0, make_double2(0.0, 0.0));
+        double mval = sqrt(p.gs[j]) * p.gl[j];
+        for (int i = 0; i < stride; i++) mk[i].x = mval;
+        double smk = lam_bts ? qd(c, lp) : ((slam * qd(c, lp)) / lam.scale) / p.gl[j];
+        DPtr pt = encode(c, mk, smk, lp);
+        ct_mul_plain(c, lam, pt.get());
+        lam.scale = lam.scale * smk;
+        lam = rescale(c, lam);
+        lam = rotsum(c, lam, stride, nrot);
+        if (lam_bts) lam = bts_boosted(c, p, lam, 1.0, slam / p.gl[j]);
+        lam.scale = lam.scale * p.gl[j];
+        for (auto &y : ys) {
+            DCt z = hmult(c, lam, y);
+            y = hmult(c, z, z);
+        }
+    }
+    return ys;
+}
+
+// ------------------------------------------------------------------------- context creation
+static void build_tables(he_ctx *c) {
+    int N = c->N, nm = c->nm;
+    c->modc.resize(nm);
+    for (int i = 0; i < nm; i++) {
+        uint64_t q = c->mods[i];
+        int s = 64 - __builtin_clzll(q);
+        REQUIRE(s <= 61 && s >= 20, HE_EINVAL, "modulus size");
+        REQUIRE((q - 1) % (2 * (uint64_t)N) == 0, HE_EINVAL, "modulus not 1 mod 2N");
+        ModC m;
+        m.q = q;
+        m.s = s;
+        m.pad = 0;
+        m.mu = (uint64_t)(((u128)1 << (s + 63)) / q);
+        c->modc[i] = m;
+    }
+    CK(cudaMalloc(&c->d_mods, sizeof(ModC) * nm));
+    CK(cudaMemcpy(c->d_mods, c->modc.data(), sizeof(ModC) * nm, cudaMemcpyHostToDevice));
+    // NTT tables: psi^{brv(k)} and psi^{-brv(k)} with Shoup companions
+    std::vector<uint64_t> tw((size_t)nm * 4 * N), ninv(2 * nm);
+    for (int t = 0; t < nm; t++) {
+        uint64_t q = c->mods[t], psi = h_root(q, N);
+        REQUIRE(psi, HE_EINVAL, "no 2N-th root");
+        uint64_t ipsi = h_inv(psi, q);
+        std::vector<uint64_t> pw(N), ipw(N);
+        pw[0] = ipw[0] = 1;
+        for (int i = 1; i < N; i++) {
+            pw[i] = h_mulmod(pw[i - 1], psi, q);
+            ipw[i] = h_mulmod(ipw[i - 1], ipsi, q);
+        }
+        uint64_t *T = tw.data() + (size_t)t * 4 * N;
+        for (int k = 0; k < N; k++) {
+            int r = 0;
+            for (int b = 0; b < c->logN; b++) r |= ((k >> b) & 1) << (c->logN - 1 - b);
+            T[k] = pw[r];
+            T[N + k] = h_shoup(pw[r], q);
+            T[2 * N + k] = ipw[r];
+            T[3 * N + k] = h_shoup(ipw[r], q);
+        }
+        uint64_t ni = h_inv((uint64_t)N % q, q);
+        ninv[2 * t] = ni;
+        ninv[2 * t + 1] = h_shoup(ni, q);
+    }
+    CK(cudaMalloc(&c->d_tw, tw.size() * 8));
+    CK(cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_ninv, ninv.size() * 8));
+    CK(cudaMemcpy(c->d_ninv, ninv.data(), ninv.size() * 8, cudaMemcpyHostToDevice));
+    // ModUp constants per (level, digit)
+    int al = c->alpha;
+    std::vector<uint64_t> cv;
+    c->cv_off.assign(c->nq, {});
+    for (int Lm1 = 0; Lm1 < c->nq; Lm1++) {
+        int L = Lm1 + 1, nl = L + al, nd = (L + al - 1) / al;
+        for (int j = 0; j < nd; j++) {
+            int lo = j * al, hi = std::min(L, lo + al), ds = hi - lo;
+            c->cv_off[Lm1].push_back(cv.size());
+            std::vector<uint64_t> qhinv(ds), qhinvs(ds), qh((size_t)ds * nl);
+            for (int i = lo; i < hi; i++) {
+                uint64_t qi = c->mods[i], prod = 1 % qi;
+                for (int i2 = lo; i2 < hi; i2++)
+                    if (i2 != i) prod = h_mulmod(prod, c->mods[i2] % qi, qi);
+                qhinv[i - lo] = h_inv(prod, qi);
+                qhinvs[i - lo] = h_shoup(qhinv[i - lo], qi);
+                for (int t = 0; t < nl; t++) {
+                    uint64_t mt = c->mods[t < L ? t : c->nq + (t - L)], pr = 1 % mt;
+                    for (int i2 = lo; i2 < hi; i2++)
+                        if (i2 != i) pr = h_mulmod(pr, c->mods[i2] % mt, mt);
+                    qh[(size_t)(i - lo) * nl + t] = pr;
+                }
+            }
+            cv.insert(cv.end(), qhinv.begin(), qhinv.end());
+            cv.insert(cv.end(), qhinvs.begin(), qhinvs.end());
+            cv.insert(cv.end(), qh.begin(), qh.end());
+        }
+    }
+    CK(cudaMalloc(&c->d_cv, cv.size() * 8));
+    CK(cudaMemcpy(c->d_cv, cv.data(), cv.size() * 8, cudaMemcpyHostToDevice));
+    // ModDown constants
+    std::vector<uint64_t> md(2 * al + (size_t)al * c->nq), pinv(2 * c->nq);
+    std::vector<int> pidx(al);
+    for (int k = 0; k < al; k++) {
+        uint64_t pk = c->mods[c->nq + k], prod = 1 % pk;
+        for (int k2 = 0; k2 < al; k2++)
+            if (k2 != k) prod = h_mulmod(prod, c->mods[c->nq + k2] % pk, pk);
+        md[k] = h_inv(prod, pk);
+        md[al + k] = h_shoup(md[k], pk);
+        pidx[k] = c->nq + k;
+        for (int i = 0; i < c->nq; i++) {
+            uint64_t q = c->mods[i], pr = 1 % q;
+            for (int k2 = 0; k2 < al; k2++)
+                if (k2 != k) pr = h_mulmod(pr, c->mods[c->nq + k2] % q, q);
+            md[2 * al + (size_t)k * c->nq + i] = pr;
+        }
+    }
+    for (int i = 0; i < c->nq; i++) {
+        uint64_t q = c->mods[i], pm = 1 % q;
+        for (int k = 0; k < al; k++) pm = h_mulmod(pm, c->mods[c->nq + k] % q, q);
+        pinv[2 * i] = h_inv(pm, q);
+        pinv[2 * i + 1] = h_shoup(pinv[2 * i], q);
+    }
+    CK(cudaMalloc(&c->d_mdcv, md.size() * 8));
+    CK(cudaMemcpy(c->d_mdcv, md.data(), md.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_pinv, pinv.size() * 8));
+    CK(cudaMemcpy(c->d_pinv, pinv.data(), pinv.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_pidx, pidx.size() * sizeof(int)));
+    CK(cudaMemcpy(c->d_pidx, pidx.data(), pidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // rescale constants: q_l^{-1} mod q_i (i < l)
+    std::vector<uint64_t> ql((size_t)c->nq * 2 * c->nq, 0);
+    for (int l = 1; l < c->nq; l++)
+        for (int i = 0; i < l; i++) {
+            uint64_t q = c->mods[i], v = h_inv(c->mods[l] % q, q);
+            ql[(size_t)l * 2 * c->nq + 2 * i] = v;
+            ql[(size_t)l * 2 * c->nq + 2 * i + 1] = h_shoup(v, q);
+        }
+    CK(cudaMalloc(&c->d_qlinv, ql.size() * 8));
+    CK(cudaMemcpy(c->d_qlinv, ql.data(), ql.size() * 8, cudaMemcpyHostToDevice));
+    // canonical embedding tables: zeta^j = exp(2 pi i j / 2N), 5^j mod 2N
+    int m = 2 * N;
+    c->zeta.resize(m);
+    for (int j = 0; j < m; j++) {
+        double ang = (2.0 * HE_PI * (double)j) / (double)m;
+        c->zeta[j] = make_double2(cos(ang), sin(ang));
+    }
+    c->rg.resize(c->n0);
+    long g = 1;
+    for (int j = 0; j < c->n0; j++) {
+        c->rg[j] = (int)g;
+        g = (g * 5) % m;
+    }
+    CK(cudaMalloc(&c->d_zeta, sizeof(double2) * m));
+    CK(cudaMemcpy(c->d_zeta, c->zeta.data(), sizeof(double2) * m, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_rg, sizeof(int) * c->n0));
+    CK(cudaMemcpy(c->d_rg, c->rg.data(), sizeof(int) * c->n0, cudaMemcpyHostToDevice));
+    // Gaussian cumulative table: rho(k) = exp(-k^2 / (2 sigma^2)), k <= ceil(6 sigma)
+    int kmax = (int)ceil(6.0 * c->sigma);
+    double s2 = 2.0 * c->sigma * c->sigma;
+    double zsum = exp(-0.0 / s2);
+    for (int k = 1; k <= kmax; k++) zsum += 2.0 * exp(-(double)(k * k) / s2);
+    std::vector<uint64_t> cdt(kmax);
+    double acc = 0.0;
+    for (int k = 0; k < kmax; k++) {
+        double pk = (k == 0 ? exp(-0.0 / s2) : 2.0 * exp(-(double)(k * k) / s2)) / zsum;
+        acc += pk;
+        cdt[k] = (uint64_t)(acc * 9223372036854775808.0);
+    }
+    c->cdt_len = kmax;
+    CK(cudaMalloc(&c->d_cdt, sizeof(uint64_t) * kmax));
+    CK(cudaMemcpy(c->d_cdt, cdt.data(), sizeof(uint64_t) * kmax, cudaMemcpyHostToDevice));
+    // Garner constants for decoding
+    REQUIRE(c->nq <= HE_MAX_LIMBS, HE_EINVAL, "too many primes");
+    std::vector<uint64_t> radix((size_t)c->nq * HE_MAX_LIMBS, 0), radinv(c->nq);
+    std::vector<double> qdv(c->nq);
+    for (int i = 0; i < c->nq; i++) {
+        uint64_t q = c->mods[i], r = 1 % q;
+        for (int j = 0; j < i; j++) {
+            radix[(size_t)i * HE_MAX_LIMBS + j] = r;
+            r = h_mulmod(r, c->mods[j] % q, q);
+        }
+        radinv[i] = h_inv(r, q);
+        qdv[i] = (double)c->mods[i];
+    }
+    CK(cudaMalloc(&c->d_radix, radix.size() * 8));
+    CK(cudaMemcpy(c->d_radix, radix.data(), radix.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_radinv, radinv.size() * 8));
+    CK(cudaMemcpy(c->d_radinv, radinv.data(), radinv.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_qd, qdv.size() * 8));
+    CK(cudaMemcpy(c->d_qd, qdv.data(), qdv.size() * 8, cudaMemcpyHostToDevice));
+    c->ndig_top = (c->nq + al - 1) / al;
+    // dynamic shared memory of the column pass (N1 * 16 words)
+    int logN1 = c->logN / 2;
+    size_t sm1 = (size_t)(1 << logN1) * std::min(16, N >> logN1) * 8;
+    if (sm1 > 48 * 1024) {
+        CK(cudaFuncSetAttribute(k_ntt_cols_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+        CK(cudaFuncSetAttribute(k_ntt_cols_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    }
+}
+
+// ------------------------------------------------------------------------- C ABI
+#define API_BEGIN try {
+#define API_END                                      \
+    }                                                \
+    catch (const HeErr &e) {                         \
+        ctx->err = e.msg;                            \
+        return e.code;                               \
+    }                                                \
+    catch (const std::exception &e) {                \
+        ctx->err = e.what();                         \
+        return HE_EINVAL;                            \
+    }                                                \
+    return HE_OK;
+
+extern "C" {
+
+int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out) {
+    if (!p || !out) return HE_EINVAL;
+    *out = nullptr;
+    if (p->log_n < 4 || p->log_n > 17 || p->n_q < 1 || p->n_p < 1 || p->n_q + p->n_p > HE_MAX_MODS ||
+        p->n_q > HE_MAX_LIMBS - p->n_p || !p->q || !p->p || p->h < 1 || p->h > (1 << p->log_n))
+        return HE_EINVAL;
+    he_ctx *c = new he_ctx();
+    c->logN = p->log_n;
+    c->N = 1 << p->log_n;
+    c->n0 = c->N / 2;
+    c->nq = p->n_q;
+    c->np = p->n_p;
+    c->alpha = p->n_p;
+    c->nm = c->nq + c->np;
+    c->h = p->h;
+    c->sigma = p->sigma;
+    c->log_scale = p->log_scale;
+    c->user_top = p->user_top_level;
+    c->bootstrap = p->bootstrap;
+    c->stc_levels = p->stc_levels;
+    c->cts_levels = p->cts_levels;
+    c->bts_min = p->bts_min_level;
+    c->em_K = p->em_K;
+    c->em_r = p->em_r;
+    c->em_deg = p->em_deg;
+    if (p->bootstrap && p->em_coeffs) c->em_c.assign(p->em_coeffs, p->em_coeffs + p->em_deg + 1);
+    c->st = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < p->n_q; i++) c->mods.push_back(p->q[i]);
+    for (int i = 0; i < p->n_p; i++) c->mods.push_back(p->p[i]);
+    he_ctx *ctx = c;
+    try {
+        if (p->bootstrap) {
+            REQUIRE(p->em_coeffs && p->em_deg >= 1, HE_EINVAL, "EvalMod coefficients missing");
+            REQUIRE(p->user_top_level + p->em_r + ilog2c(p->em_deg + 1) + p->cts_levels == p->n_q - 1, HE_EINVAL,
+                    "level map: user_top + EvalMod + CtS levels must reach the top");
+        }
+        REQUIRE(p->user_top_level < p->n_q, HE_EINVAL, "user_top_level");
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        int nsm = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        c->max_grid = nsm * 16;
+        build_tables(c);
+    } catch (const HeErr &e) {
+        fprintf(stderr, "he_context_create: %s\n", e.msg.c_str());
+        delete c;
+        return e.code;
+    }
+    *out = c;
+    return HE_OK;
+}
+
+void he_context_destroy(he_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    c->lt_cache.clear();
+    for (auto &kv : c->keys) cudaFree(kv.second);
+    void *ptrs[] = {c->d_mods, c->d_tw, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx, c->d_zeta,
+                    c->d_rg, c->d_cdt, c->d_radix, c->d_radinv, c->d_qd, c->d_s, c->d_pk};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete c;
+}
+
+const char *he_last_error(const he_ctx *c) { return c ? c->err.c_str() : "null context"; }
+int he_ring_degree(const he_ctx *c) { return c ? c->N : 0; }
+
+int he_keygen(he_ctx *ctx, uint64_t seed, const int *rot_steps, int n_rot) {
+    if (!ctx || n_rot < 0 || (n_rot > 0 && !rot_steps)) return HE_EINVAL;
+    API_BEGIN
+    keygen(ctx, seed);
+    make_key(ctx, 0);
+    make_key(ctx, 2 * ctx->N - 1);
+    for (int i = 0; i < n_rot; i++) make_key(ctx, galois_for_rot(ctx, rot_steps[i]));
+    if (ctx->bootstrap) {
+        for (int inv = 0; inv < 2; inv++) {
+            int nl = inv ? ctx->cts_levels : ctx->stc_levels;
+            for (const LtDesc &lv : lt_levels(ctx, nl, inv))
+                for (int r : lt_rotation_steps(ctx, lv)) make_key(ctx, galois_for_rot(ctx, r));
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    API_END
+}
+
+int he_keygen_softmax(he_ctx *ctx, int n, int m) {
+    if (!ctx || n < 1 || m < 1 || (n & (n - 1)) || n % m || ctx->n0 % n) return HE_EINVAL;
+    API_BEGIN
+    REQUIRE(ctx->have_keys, HE_ENOKEY, "keygen first");
+    int stride = (int)((long)m * ctx->n0 / n);
+    for (int i = 0; (1 << i) < n / m; i++) make_key(ctx, galois_for_rot(ctx, (long)stride << i));
+    CK(cudaStreamSynchronize(ctx->st));
+    API_END
+}
+
+int he_encrypt(he_ctx *ctx, const double *x, size_t count, int n, int m, double M, uint64_t seed, he_ct *out) {
+    if (!ctx || !x || !out || !out->data || n < 1 || m < 1 || (n & (n - 1)) || n % m || ctx->n0 % n || !(M > 0))
+        return HE_EINVAL;
+    size_t L = (size_t)m * ctx->n0 / n;
+    if (count != L * (size_t)n) {
+        ctx->err = "count must be L n with L = m N0 / n";
+        return HE_EINVAL;
+    }
+    for (size_t i = 0; i < count; i++)
+        if (!(x[i] <= 0.0 && x[i] >= -M)) {
+            ctx->err = "inputs must lie in [-M, 0] (Assumption 3.5)";
+            return HE_EINVAL;
+        }
+    API_BEGIN
+    int top = ctx->user_top, per = n / m;
+    double scale = (2.0 / M) * (double)ctx->mods[top];
+    long cs = 2L * (top + 1) * ctx->N;
+    for (int c = 0; c < m; c++) {
+        std::vector<double2> z(ctx->n0, make_double2(0.0, 0.0));
+        for (int t = 0; t < per; t++)
+            for (size_t l = 0; l < L; l++) z[t * L + l].x = x[l * n + (size_t)c * per + t];
+        encrypt_into(ctx, z, top, scale, seed, c, out->data + c * cs);
+    }
+    out->level = top;
+    out->scale = scale;
+    out->n_ct = m;
+    CK(cudaStreamSynchronize(ctx->st));
+    API_END
+}
+
+int he_decrypt(he_ctx *ctx, const he_ct *cts, int n, double *y, size_t count) {
+    if (!ctx || !cts || !y || n < 1 || cts->n_ct < 1 || n % cts->n_ct || ctx->n0 % n) return HE_EINVAL;
+    int m = cts->n_ct, per = n / m;
+    size_t L = (size_t)m * ctx->n0 / n;
+    if (count != L * (size_t)n) return HE_EINVAL;
+    API_BEGIN
+    DCt x = ct_view(cts);
+    for (int c = 0; c < m; c++) {
+        std::vector<double2> z = decrypt_slots(ctx, x, c);
+        for (int t = 0; t < per; t++)
+            for (size_t l = 0; l < L; l++) y[l * n + (size_t)c * per + t] = z[t * L + l].x;
+    }
+    API_END
+}
+
+int he_decrypt_slots(he_ctx *ctx, const he_ct *cts, int ct, double *slots) {
+    if (!ctx || !cts || !slots || ct < 0 || ct >= cts->n_ct) return HE_EINVAL;
+    API_BEGIN
+    std::vector<double2> z = decrypt_slots(ctx, ct_view(cts), ct);
+    memcpy(slots, z.data(), sizeof(double2) * ctx->n0);
+    API_END
+}
+
+int he_encrypt_slots(he_ctx *ctx, const double *slots, int level, double scale, uint64_t seed, int ct_index, he_ct *out,
+                     int ct) {
+    if (!ctx || !slots || !out || !out->data || level < 0 || level >= ctx->nq || ct < 0 || ct >= out->n_ct)
+        return HE_EINVAL;
+    API_BEGIN
+    std::vector<double2> z(ctx->n0);
+    memcpy(z.data(), slots, sizeof(double2) * ctx->n0);
+    encrypt_into(ctx, z, level, scale, seed, ct_index, out->data + (long)ct * 2 * (level + 1) * ctx->N);
+    out->level = level;
+    out->scale = scale;
+    CK(cudaStreamSynchronize(ctx->st));
+    API_END
+}
+
+static Plan plan_of(he_ctx *c, const he_softmax_plan *hp) {
+    Plan p;
+    p.n = hp->n;
+    p.k = hp->k;
+    p.M = hp->M;
+    p.boost = hp->bts_boost > 0 ? hp->bts_boost : 1.0;
+    p.exp_deg = hp->exp_deg;
+    p.exp_c.assign(hp->exp_coeffs, hp->exp_coeffs + hp->exp_deg + 1);
+    const double *cp = hp->inv_coeffs;
+    for (int j = 0; j < p.k; j++) {
+        p.inv_deg.push_back(hp->inv_deg[j]);
+        p.inv_c.emplace_back(cp, cp + hp->inv_deg[j] + 1);
+        cp += hp->inv_deg[j] + 1;
+        p.a.push_back(hp->inv_a[j]);
+        p.b.push_back(hp->inv_b[j]);
+        p.gs.push_back(hp->gain_s[j]);
+        p.gl.push_back(hp->gain_l[j]);
+    }
+    (void)c;
+    return p;
+}
+
+int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched) {
+    if (!ctx || !plan || !cts || !cts->data || cts->n_ct < 1 || plan->k < 1 || plan->k > 16) return HE_EINVAL;
+    int m = cts->n_ct, n = plan->n;
+    if (n < 1 || (n & (n - 1)) || n % m || ctx->n0 % n) {
+        ctx->err = "n must be a power of two dividing N/2, and m must divide n";
+        return HE_EINVAL;
+    }
+    API_BEGIN
+    Plan p = plan_of(ctx, plan);
+    DCt in = ct_view(cts);
+    std::vector<DCt> ys;
+    if (batched) {
+        ys.push_back(ct_copy(ctx, in));
+    } else {
+        for (int i = 0; i < m; i++) ys.push_back(ct_copy(ctx, ct_sub(ctx, in, i)));
+    }
+    ys = softmax_run(ctx, p, ys, m);
+    int lo = ys[0].level;
+    long cs = 2L * (lo + 1) * ctx->N;
+    if (batched) {
+        CK(cudaMemcpyAsync(cts->data, ys[0].d, (size_t)m * cs * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    } else {
+        for (int i = 0; i < m; i++)
+            CK(cudaMemcpyAsync(cts->data + i * cs, ys[i].d, (size_t)cs * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    }
+    cts->level = lo;
+    cts->scale = ys[0].scale;
+    ys.clear();
+    API_END
+}
+
+int he_ntt(he_ctx *ctx, uint64_t *data, int n_poly, int n_limb, int inverse) {
+    if (!ctx || !data || n_poly < 1 || n_limb < 1 || n_limb > ctx->nq) return HE_EINVAL;
+    API_BEGIN
+    ntt(ctx, data, n_poly * n_limb, qmap(n_limb), (long)n_limb * ctx->N, inverse != 0);
+    API_END
+}
+
+int he_ct_to_coeff(he_ctx *ctx, const he_ct *x, uint64_t *host) {
+    if (!ctx || !x || !x->data || !host || x->level < 0 || x->level >= ctx->nq) return HE_EINVAL;
+    API_BEGIN
+    int L = x->level + 1;
+    size_t words = (size_t)x->n_ct * 2 * L * ctx->N;
+    DPtr t = dalloc(ctx, words);
+    CK(cudaMemcpyAsync(t.get(), x->data, words * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    ntt(ctx, t.get(), x->n_ct * 2 * L, qmap(L), (long)L * ctx->N, true);
+    CK(cudaMemcpyAsync(host, t.get(), words * 8, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    API_END
+}
+
+int he_ct_from_coeff(he_ctx *ctx, const uint64_t *host, he_ct *x) {
+    if (!ctx || !x || !x->data || !host || x->level < 0 || x->level >= ctx->nq || x->n_ct < 1) return HE_EINVAL;
+    API_BEGIN
+    int L = x->level + 1;
+    size_t words = (size_t)x->n_ct * 2 * L * ctx->N;
+    CK(cudaMemcpyAsync(x->data, host, words * 8, cudaMemcpyHostToDevice, ctx->st));
+    ntt(ctx, x->data, x->n_ct * 2 * L, qmap(L), (long)L * ctx->N, false);
+    CK(cudaStreamSynchronize(ctx->st));
+    API_END
+}
+
+int he_encode(he_ctx *ctx, const double *slots, double scale, int level, uint64_t *pt) {
+    if (!ctx || !slots || !pt || level < 0 || level >= ctx->nq) return HE_EINVAL;
+    API_BEGIN
+    std::vector<double2> z(ctx->n0);
+    memcpy(z.data(), slots, sizeof(double2) * ctx->n0);
+    DPtr d = encode(ctx, z, scale, level);
+    CK(cudaMemcpyAsync(pt, d.get(), (size_t)(level + 1) * ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    API_END
+}
+
+int he_add(he_ctx *ctx, he_ct *a, const he_ct *b) {
+    if (!ctx || !a || !b) return HE_EINVAL;
+    API_BEGIN
+    DCt x = ct_view(a);
+    ct_add_inplace(ctx, x, ct_view(b));
+    API_END
+}
+
+int he_mul_plain(he_ctx *ctx, he_ct *a, const uint64_t *pt) {
+    if (!ctx || !a || !pt) return HE_EINVAL;
+    API_BEGIN
+    DCt x = ct_view(a);
+    ct_mul_plain(ctx, x, pt);
+    API_END
+}
+
+static void put_out(he_ctx *ctx, const DCt &y, he_ct *out) {
+    REQUIRE(out->data, HE_EINVAL, "output buffer");
+    CK(cudaMemcpyAsync(out->data, y.d, (size_t)y.nct * y.cs(ctx) * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    out->level = y.level;
+    out->scale = y.scale;
+    out->n_ct = y.nct;
+}
+
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out) {
+    if (!ctx || !a || !out) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, rescale(ctx, ct_view(a)), out);
+    API_END
+}
+
+int he_hmult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out) {
+    if (!ctx || !a || !b || !out) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, hmult(ctx, ct_view(a), ct_view(b)), out);
+    API_END
+}
+
+int he_relinearize(he_ctx *ctx, const uint64_t *d, int level, int n_ct, he_ct *out) {
+    if (!ctx || !d || !out || level < 0 || level >= ctx->nq || n_ct < 1) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, relinearize(ctx, d, level, n_ct, 1.0), out);
+    API_END
+}
+
+int he_rotate(he_ctx *ctx, const he_ct *a, int r, he_ct *out) {
+    if (!ctx || !a || !out) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, rotate(ctx, ct_view(a), galois_for_rot(ctx, r)), out);
+    API_END
+}
+
+int he_conjugate(he_ctx *ctx, const he_ct *a, he_ct *out) {
+    if (!ctx || !a || !out) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, rotate(ctx, ct_view(a), 2 * ctx->N - 1), out);
+    API_END
+}
+
+int he_poly_eval(he_ctx *ctx, const he_ct *u, const double *coeffs, int deg, int level_out, double scale_out, he_ct *out) {
+    if (!ctx || !u || !coeffs || !out || deg < 1 || level_out < 0) return HE_EINVAL;
+    API_BEGIN
+    std::vector<double> cf(coeffs, coeffs + deg + 1);
+    put_out(ctx, poly_eval(ctx, ct_view(u), cf, level_out, scale_out), out);
+    API_END
+}
+
+int he_lintrans(he_ctx *ctx, const he_ct *a, int nlev, int inverse, int which, double gain, double pt_scale, he_ct *out) {
+    if (!ctx || !a || !out || nlev < 1 || which < 0 || which >= nlev) return HE_EINVAL;
+    API_BEGIN
+    std::vector<LtDesc> lv = lt_levels(ctx, nlev, inverse);
+    put_out(ctx, lt_eval_level(ctx, ct_view(a), lv[which], gain, pt_scale), out);
+    API_END
+}
+
+int he_bootstrap(he_ctx *ctx, const he_ct *a, double gain, double out_scale, he_ct *out) {
+    if (!ctx || !a || !out) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, bootstrap(ctx, ct_view(a), gain, out_scale), out);
+    API_END
+}
+
+int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out) {
+    if (!ctx || !a || !out || top < 0 || top >= ctx->nq) return HE_EINVAL;
+    API_BEGIN
+    put_out(ctx, mod_raise(ctx, ct_view(a), top), out);
+    API_END
+}
+
+int he_counters(const he_ctx *ctx, long *out5) {
+    if (!ctx || !out5) return HE_EINVAL;
+    for (int i = 0; i < 5; i++) out5[i] = ctx->cnt[i];
+    return HE_OK;
+}
+
+int he_selftest_bounded_wait(he_ctx *ctx, long max_iter) {
+    if (!ctx || max_iter < 1) return HE_EINVAL;
+    API_BEGIN
+    DPtr b = dalloc(ctx, 1);
+    int *flag = (int *)b.get(), *status = flag + 1;
+    CK(cudaMemsetAsync(b.get(), 0, 8, ctx->st));
+    k_bounded_wait<<<1, 32, 0, ctx->st>>>(flag, status, max_iter);
+    LAUNCH_CHECK();
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (hs == 2) {
+        ctx->err = "bounded wait gave up";
+        return HE_ETIMEOUT;
+    }
+    API_END
+}
+
+}  // extern "C"

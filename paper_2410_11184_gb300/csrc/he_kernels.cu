@@ -1,0 +1,588 @@
+// CUDA kernels for RNS-CKKS on sm_103a.  Every step of the ciphertext arithmetic runs here;
+// the host code in he_host.cu only sequences launches.
+//
+// Polynomial batches are addressed as (base, count, nper, poly_stride): limb l of the batch
+// lives at base + (l / nper) * poly_stride + (l % nper) * N and uses modulus prime[l % nper].
+#include "he_kernels.cuh"
+
+// ------------------------------------------------------------------------------------------
+// Negacyclic NTT (Cooley-Tukey with merged psi twist; output in bit-reversed order:
+// a_hat[k] = a(psi^(2 brv(k) + 1))) and its Gentleman-Sande inverse.  N = N1 * N2: the first
+// log2(N1) stages act on the N2 columns {c + N2 r}, the rest on the N1 rows of N2 contiguous
+// coefficients; each pass stages one tile in shared memory.
+// tw layout per modulus: [psi_rev | psi_rev_shoup | ipsi_rev | ipsi_rev_shoup], each N long.
+
+__global__ void k_ntt_cols_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, int logN, int logN1, int C) {
+    extern __shared__ uint64_t sm[];
+    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
+    const int c0 = blockIdx.x * C;
+    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
+        int r = idx / C, c = idx % C;
+        sm[idx] = a[(long)r * N2 + c0 + c];
+    }
+    __syncthreads();
+    for (int m = 1, t = N1 >> 1; m < N1; m <<= 1, t >>= 1) {
+        for (int b = threadIdx.x; b < (N1 >> 1) * C; b += blockDim.x) {
+            int c = b % C, j = b / C;
+            int i = j / t, r = 2 * i * t + (j % t);
+            uint64_t w = psi[m + i], wp = psip[m + i];
+            uint64_t u = sm[r * C + c], v = mul_shoup(sm[(r + t) * C + c], w, wp, q);
+            sm[r * C + c] = add_mod(u, v, q);
+            sm[(r + t) * C + c] = sub_mod(u, v, q);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
+        int r = idx / C, c = idx % C;
+        a[(long)r * N2 + c0 + c] = sm[idx];
+    }
+}
+
+__global__ void k_ntt_rows_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, int logN, int logN1, int R) {
+    extern __shared__ uint64_t sm[];
+    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1, h2 = N2 >> 1;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
+    const int row0 = blockIdx.x * R;
+    uint64_t *g = a + (long)row0 * N2;
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = g[idx];
+    __syncthreads();
+    for (int m = N1, t = h2; m < N; m <<= 1, t >>= 1) {
+        for (int b = threadIdx.x; b < R * h2; b += blockDim.x) {
+            int rr = b / h2, j = b % h2;
+            int il = j / t, ci = 2 * il * t + (j % t);
+            int ig = (row0 + rr) * (m >> logN1) + il;
+            uint64_t w = psi[m + ig], wp = psip[m + ig];
+            uint64_t *s = sm + rr * N2;
+            uint64_t u = s[ci], v = mul_shoup(s[ci + t], w, wp, q);
+            s[ci] = add_mod(u, v, q);
+            s[ci + t] = sub_mod(u, v, q);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) g[idx] = sm[idx];
+}
+
+__global__ void k_ntt_rows_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, int logN, int logN1, int R) {
+    extern __shared__ uint64_t sm[];
+    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1, h2 = N2 >> 1;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
+    const int row0 = blockIdx.x * R;
+    uint64_t *g = a + (long)row0 * N2;
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = g[idx];
+    __syncthreads();
+    for (int t = 1, h = N >> 1; t < N2; t <<= 1, h >>= 1) {
+        for (int b = threadIdx.x; b < R * h2; b += blockDim.x) {
+            int rr = b / h2, j = b % h2;
+            int il = j / t, ci = 2 * il * t + (j % t);
+            int ig = (row0 + rr) * (h >> logN1) + il;
+            uint64_t w = ipsi[h + ig], wp = ipsip[h + ig];
+            uint64_t *s = sm + rr * N2;
+            uint64_t u = s[ci], v = s[ci + t];
+            s[ci] = add_mod(u, v, q);
+            s[ci + t] = mul_shoup(sub_mod(u, v, q), w, wp, q);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) g[idx] = sm[idx];
+}
+
+__global__ void k_ntt_cols_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, const uint64_t *ninv, int logN, int logN1, int C) {
+    extern __shared__ uint64_t sm[];
+    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
+    const int c0 = blockIdx.x * C;
+    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
+        int r = idx / C, c = idx % C;
+        sm[idx] = a[(long)r * N2 + c0 + c];
+    }
+    __syncthreads();
+    for (int t = 1, h = N1 >> 1; h >= 1; t <<= 1, h >>= 1) {
+        for (int b = threadIdx.x; b < (N1 >> 1) * C; b += blockDim.x) {
+            int c = b % C, j = b / C;
+            int i = j / t, r = 2 * i * t + (j % t);
+            uint64_t w = ipsi[h + i], wp = ipsip[h + i];
+            uint64_t u = sm[r * C + c], v = sm[(r + t) * C + c];
+            sm[r * C + c] = add_mod(u, v, q);
+            sm[(r + t) * C + c] = mul_shoup(sub_mod(u, v, q), w, wp, q);
+        }
+        __syncthreads();
+    }
+    const uint64_t ni = ninv[2 * p], nip = ninv[2 * p + 1];
+    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
+        int r = idx / C, c = idx % C;
+        a[(long)r * N2 + c0 + c] = mul_shoup(sm[idx], ni, nip, q);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Elementwise kernels over a batch (count limbs, addressing as above).
+#define EW_PROLOGUE                                                                           \
+    const int N = 1 << logN;                                                                  \
+    long total = (long)count << logN;                                                         \
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) { \
+        int l = (int)(x >> logN), k = (int)(x & (N - 1));                                     \
+        int li = l % nper;                                                                    \
+        long po = (long)(l / nper);                                                           \
+        const ModC m = mods[map.prime[li]];
+
+__global__ void k_add(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
+                      int count, int nper, LimbMap map, const ModC *mods, int logN, int sub) {
+    EW_PROLOGUE
+    long off = (long)li * N + k;
+    uint64_t u = a[po * sa + off], v = b[po * sb + off];
+    out[po * so + off] = sub ? sub_mod(u, v, m.q) : add_mod(u, v, m.q);
+    }
+}
+
+__global__ void k_mul(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
+                      int count, int nper, LimbMap map, const ModC *mods, int logN, int accumulate) {
+    EW_PROLOGUE
+    long off = (long)li * N + k;
+    uint64_t r = mul_mod(a[po * sa + off], b[po * sb + off], m);
+    if (accumulate) r = add_mod(out[po * so + off], r, m.q);
+    out[po * so + off] = r;
+    }
+}
+
+// out = a * s_l with a per-limb scalar (residue of the scalar mod each modulus, by limb index)
+__global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal,
+                             int count, int nper, LimbMap map, const ModC *mods, int logN) {
+    EW_PROLOGUE
+    long off = (long)li * N + k;
+    out[po * so + off] = mul_mod(a[po * sa + off], scal.v[li], m);
+    }
+}
+
+// adds scal[li] to every evaluation point of the selected polynomials (a constant polynomial
+// has the same value at every root)
+__global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int nper, LimbMap map,
+                             const ModC *mods, int logN) {
+    EW_PROLOGUE
+    long off = (long)li * N + k;
+    a[po * sa + off] = add_mod(a[po * sa + off], scal.v[li], m.q);
+    }
+}
+
+// tensor of ciphertext batches a, b (each [ct][2][nper][N] with their own strides) into
+// d [ct][3][nper][N]; accumulate adds into d
+__global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
+                         int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate) {
+    const int N = 1 << logN;
+    long total = (long)nct * nper << logN;
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
+        int l = (int)(x >> logN), k = (int)(x & (N - 1));
+        int li = l % nper, c = l / nper;
+        const ModC m = mods[map.prime[li]];
+        long off = (long)li * N + k;
+        // each ciphertext holds 2 (inputs) or 3 (output) polynomials: poly stride = ct stride / #polys
+        const uint64_t *pa = a + c * sa, *pb = b + c * sb;
+        long psa = sa / 2, psb = sb / 2, ps = sd / 3;
+        uint64_t a0 = pa[off], a1 = pa[psa + off], b0 = pb[off], b1 = pb[psb + off];
+        uint64_t d0 = mul_mod(a0, b0, m);
+        uint64_t d1 = add_mod(mul_mod(a0, b1, m), mul_mod(a1, b0, m), m.q);
+        uint64_t d2 = mul_mod(a1, b1, m);
+        uint64_t *pd = d + c * sd;
+        if (accumulate) {
+            d0 = add_mod(d0, pd[off], m.q);
+            d1 = add_mod(d1, pd[ps + off], m.q);
+            d2 = add_mod(d2, pd[2 * ps + off], m.q);
+        }
+        pd[off] = d0;
+        pd[ps + off] = d1;
+        pd[2 * ps + off] = d2;
+    }
+}
+
+// NTT-domain automorphism X -> X^g: out[k] = in[pi(k)], e_k = 2 brv(k) + 1,
+// pi(k) = brv((e_k g mod 2N - 1) / 2)
+__device__ __forceinline__ int auto_index(int k, int g, int logN) {
+    int e = 2 * brev_bits(k, logN) + 1;
+    int e2 = (int)(((long)e * g) & ((2L << logN) - 1));
+    return brev_bits((e2 - 1) >> 1, logN);
+}
+
+__global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN) {
+    const int N = 1 << logN;
+    long total = (long)count << logN;
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
+        int l = (int)(x >> logN), k = (int)(x & (N - 1));
+        int li = l % nper;
+        long po = l / nper;
+        out[po * so + (long)li * N + k] = a[po * sa + (long)li * N + auto_index(k, g, logN)];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Basis conversion (coefficient domain).  ModUp for one digit D of a batch of polynomials:
+// for every target modulus t of the extended basis,
+//   out_t = sum_{i in D} [x_i * qhinv_i]_{q_i} * (qh_{i,t}) mod m_t.
+// For t in D this reproduces x_t.  cv layout per (level, digit): qhinv[a], qhinv_shoup[a],
+// then qh[a][ntarget].
+__global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
+                        int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
+                        int logN) {
+    const int N = 1 << logN;
+    long total = (long)nct * ntarget << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        int t = l % ntarget, c = l / ntarget;
+        const ModC mt = mods[tmap.prime[t]];
+        uint64_t acc = 0;
+        for (int i = 0; i < dsize; i++) {
+            const int pi = tmap.prime[digit_lo + i];
+            uint64_t qi = mods[pi].q;
+            uint64_t y = mul_shoup(x[c * sx + (long)(digit_lo + i) * N + k], cv[i], cv[dsize + i], qi);
+            acc = add_mod(acc, mul_mod(reduce_u64(y, mt), cv[2 * dsize + i * ntarget + t], mt), mt.q);
+        }
+        out[c * so_ct + so_digit + (long)t * N + k] = acc;
+    }
+}
+
+// ModDown conversion: conv_i = sum_k [y_k * phinv_k]_{p_k} (phat_k mod q_i); writes conv into
+// out (coefficient domain) for the Q limbs.  x: [nct][2][L + alpha][N] coefficient-domain P limbs
+// at offset L.  cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][L_all] (by Q index).
+__global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
+                               const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN) {
+    const int N = 1 << logN;
+    long total = (long)npoly * L << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        int i = l % L, pl = l / L;
+        const ModC mi = mods[qmap.prime[i]];
+        const uint64_t *xp = x + (long)pl * (L + alpha) * N + (long)L * N;
+        uint64_t acc = 0;
+        for (int j = 0; j < alpha; j++) {
+            uint64_t pj = mods[pidx[j]].q;
+            uint64_t y = mul_shoup(xp[(long)j * N + k], cv[j], cv[alpha + j], pj);
+            acc = add_mod(acc, mul_mod(reduce_u64(y, mi), cv[2 * alpha + j * nqall + qmap.prime[i]], mi), mi.q);
+        }
+        out[(long)pl * L * N + (long)i * N + k] = acc;
+    }
+}
+
+// out_i = (x_i - conv_i) * pinv_i for the Q limbs of every polynomial; accumulate adds to out
+__global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
+                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN, int accumulate) {
+    const int N = 1 << logN;
+    long total = (long)npoly * L << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        int i = l % L, pl = l / L;
+        const ModC mi = mods[qmap.prime[i]];
+        uint64_t v = sub_mod(x[(long)pl * (L + alpha) * N + (long)i * N + k], conv[(long)pl * L * N + (long)i * N + k], mi.q);
+        v = mul_shoup(v, pinv[2 * qmap.prime[i]], pinv[2 * qmap.prime[i] + 1], mi.q);
+        long o = (long)(pl / 2) * so + (long)(pl % 2) * L * N + (long)i * N + k;
+        if (accumulate) v = add_mod(out[o], v, mi.q);
+        out[o] = v;
+    }
+}
+
+// Key-switching inner product: for each ciphertext c and extended limb t,
+//   acc_{0,1}[t] = sum_j d~_j[t][pi_g(k)] * key_j^{b,a}[kt][k],
+// with the key limb kt = t for Q limbs and nq_all + (t - L) for P limbs.  The key is read once
+// per (t, k) for all ciphertexts of the batch.
+__global__ void k_ks_inner(uint64_t *acc, const uint64_t *dig, int nct, int ndig, int L, int alpha,
+                           LimbMap tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all,
+                           int g, int logN) {
+    const int N = 1 << logN;
+    const int nl = L + alpha;
+    long total = (long)nl << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int t = (int)(id >> logN), k = (int)(id & (N - 1));
+        const ModC m = mods[tmap.prime[t]];
+        int kt = t < L ? t : nq_all + (t - L);
+        int src = g > 1 ? auto_index(k, g, logN) : k;
+        uint64_t kb[8], ka[8];
+        for (int j = 0; j < ndig; j++) {
+            kb[j] = key[((long)(2 * j) * key_nlimb + kt) * N + k];
+            ka[j] = key[((long)(2 * j + 1) * key_nlimb + kt) * N + k];
+        }
+        for (int c = 0; c < nct; c++) {
+            uint64_t s0 = 0, s1 = 0;
+            for (int j = 0; j < ndig; j++) {
+                uint64_t d = dig[(((long)c * ndig + j) * nl + t) * N + src];
+                s0 = add_mod(s0, mul_mod(d, kb[j], m), m.q);
+                s1 = add_mod(s1, mul_mod(d, ka[j], m), m.q);
+            }
+            acc[((long)(2 * c) * nl + t) * N + k] = s0;
+            acc[((long)(2 * c + 1) * nl + t) * N + k] = s1;
+        }
+    }
+}
+
+// Rescale, step 1: r = centred last limb (coefficient form, [npoly][N]); writes r mod q_i for
+// the remaining L-1 limbs into tmp [npoly][L-1][N].
+__global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,
+                                 const ModC *mods, uint64_t ql, int logN) {
+    const int N = 1 << logN;
+    long total = (long)npoly * Lm1 << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        int i = l % Lm1, pl = l / Lm1;
+        const ModC mi = mods[qmap.prime[i]];
+        uint64_t r = last[(long)pl * N + k];
+        uint64_t v = r <= (ql - 1) / 2 ? reduce_u64(r, mi) : reduce_i64((int64_t)r - (int64_t)ql, mi);
+        tmp[(long)pl * Lm1 * N + (long)i * N + k] = v;
+    }
+}
+
+// Rescale, step 2: out_i = (x_i - t_i) * qlinv_i (x: [nct][2][L][N], out: [nct][2][L-1][N])
+__global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *t, int npoly, int L, LimbMap qmap,
+                              const ModC *mods, const uint64_t *qlinv, int logN) {
+    const int N = 1 << logN;
+    const int Lm1 = L - 1;
+    long total = (long)npoly * Lm1 << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        int i = l % Lm1, pl = l / Lm1;
+        const ModC mi = mods[qmap.prime[i]];
+        uint64_t v = sub_mod(x[(long)pl * L * N + (long)i * N + k], t[(long)pl * Lm1 * N + (long)i * N + k], mi.q);
+        out[(long)pl * Lm1 * N + (long)i * N + k] = mul_shoup(v, qlinv[2 * i], qlinv[2 * i + 1], mi.q);
+    }
+}
+
+// ModRaise: level-0 coefficients (centred mod q0) reduced into L limbs (coefficient form)
+__global__ void k_modraise(uint64_t *out, const uint64_t *x0, int npoly, int L, LimbMap qmap, const ModC *mods,
+                           uint64_t q0, int logN) {
+    const int N = 1 << logN;
+    long total = (long)npoly * L << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        int i = l % L, pl = l / L;
+        const ModC mi = mods[qmap.prime[i]];
+        uint64_t r = x0[(long)pl * N + k];
+        uint64_t v = r <= (q0 - 1) / 2 ? reduce_u64(r, mi) : reduce_i64((int64_t)r - (int64_t)q0, mi);
+        out[(long)pl * L * N + (long)i * N + k] = v;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Counter-based randomness (SplitMix64 output function, Steele-Lea-Flood 2014):
+//   key = mix(seed + G (2 dom + 1)), draw = mix(key + G (ctr + 1)), G = 0x9e3779b97f4a7c15.
+__device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xbf58476d1ce4e5b9ULL;
+    z ^= z >> 27;
+    z *= 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return z;
+}
+
+__device__ __forceinline__ uint64_t rng64(uint64_t seed, uint64_t dom, uint64_t ctr) {
+    const uint64_t G = 0x9e3779b97f4a7c15ULL;
+    return sm_mix(sm_mix(seed + G * (2 * dom + 1)) + G * (ctr + 1));
+}
+
+// uniform residues: limb l (modulus index p = prime[l % nper]) coefficient k from counter
+// p * N + k of domain dom; value (w0 2^64 + w1) mod q_p
+__global__ void k_sample_uniform(uint64_t *out, long so, int count, int nper, LimbMap map,
+                                 const ModC *mods, uint64_t seed, uint64_t dom, int logN) {
+    const int N = 1 << logN;
+    long total = (long)count << logN;
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
+        int l = (int)(x >> logN), k = (int)(x & (N - 1));
+        int li = l % nper;
+        uint64_t q = mods[map.prime[li]].q;
+        uint64_t c = ((uint64_t)map.prime[li] << logN) + k;
+        unsigned __int128 w = ((unsigned __int128)rng64(seed, dom, 2 * c) << 64) | rng64(seed, dom, 2 * c + 1);
+        out[(long)(l / nper) * so + (long)li * N + k] = (uint64_t)(w % q);
+    }
+}
+
+// small signed samples: kind 0 = Gaussian from the cumulative table, 1 = ternary {0,0,+1,-1}
+__global__ void k_sample_small(int64_t *out, int n, uint64_t seed, uint64_t dom, uint64_t ctr0,
+                               const uint64_t *cdt, int cdt_len, int kind) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        uint64_t r = rng64(seed, dom, ctr0 + k);
+        int64_t v;
+        if (kind == 0) {
+            uint64_t u = r >> 1;
+            int mag = 0;
+            for (int j = 0; j < cdt_len; j++) mag += u >= cdt[j];
+            v = (r & 1) ? -mag : mag;
+        } else {
+            uint64_t b = r & 3;
+            v = b < 2 ? 0 : (b == 2 ? 1 : -1);
+        }
+        out[k] = v;
+    }
+}
+
+// secret with exactly h nonzeros: coefficient k is nonzero iff fewer than h pairs
+// (draw_j, j) are smaller than (draw_k, k); sign from a second domain
+__global__ void k_sample_hwt(int64_t *out, int n, int h, uint64_t seed, uint64_t dom, uint64_t dom_sign) {
+    extern __shared__ uint64_t keys[];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t mine = k < n ? rng64(seed, dom, k) : 0;
+    int rank = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        int j = base + threadIdx.x;
+        keys[threadIdx.x] = j < n ? rng64(seed, dom, j) : ~0ULL;
+        __syncthreads();
+        int lim = min((int)blockDim.x, n - base);
+        for (int jj = 0; jj < lim; jj++) {
+            uint64_t o = keys[jj];
+            int j2 = base + jj;
+            rank += (o < mine) || (o == mine && j2 < k);
+        }
+        __syncthreads();
+    }
+    if (k < n) out[k] = rank < h ? ((rng64(seed, dom_sign, k) & 1) ? -1 : 1) : 0;
+}
+
+// signed small coefficients into residues for every limb
+__global__ void k_small_to_limbs(uint64_t *out, long so, const int64_t *v, int count, int nper, LimbMap map,
+                                 const ModC *mods, int logN) {
+    EW_PROLOGUE
+    out[po * so + (long)li * N + k] = reduce_i64(v[k], m);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Canonical embedding: special FFT stages on complex doubles (re, im interleaved).
+// Forward (coefficients -> slots) stage of length len on the bit-reversed array,
+// inverse stage undoes one forward stage (the 1/2 factors are applied at the end).
+// Built with --fmad=false: every double operation is a single IEEE operation, in the
+// order the definition writes it.
+__global__ void k_bitrev_c(double2 *v, int n0, int logn0) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
+        int j = brev_bits(i, logn0);
+        if (i < j) {
+            double2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
+}
+
+__global__ void k_sfft_fwd_stage(double2 *v, int n0, int len, const double2 *zeta, const int *rg, int m2n) {
+    int lenh = len >> 1, lenq = len << 2, gap = m2n / lenq;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < (n0 >> 1); b += gridDim.x * blockDim.x) {
+        int i = (b / lenh) * len, j = b % lenh;
+        double2 z = zeta[(rg[j] % lenq) * gap];
+        double2 u = v[i + j], x = v[i + j + lenh], t;
+        t.x = x.x * z.x - x.y * z.y;
+        t.y = x.x * z.y + x.y * z.x;
+        v[i + j] = make_double2(u.x + t.x, u.y + t.y);
+        v[i + j + lenh] = make_double2(u.x - t.x, u.y - t.y);
+    }
+}
+
+__global__ void k_sfft_inv_stage(double2 *v, int n0, int len, const double2 *zeta, const int *rg, int m2n) {
+    int lenh = len >> 1, lenq = len << 2, gap = m2n / lenq;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < (n0 >> 1); b += gridDim.x * blockDim.x) {
+        int i = (b / lenh) * len, j = b % lenh;
+        double2 z = zeta[(lenq - (rg[j] % lenq)) * gap];
+        double2 a = v[i + j], c = v[i + j + lenh], s, d, t;
+        s.x = a.x + c.x;
+        s.y = a.y + c.y;
+        d.x = a.x - c.x;
+        d.y = a.y - c.y;
+        t.x = d.x * z.x - d.y * z.y;
+        t.y = d.x * z.y + d.y * z.x;
+        v[i + j] = s;
+        v[i + j + lenh] = t;
+    }
+}
+
+__global__ void k_scale_c(double2 *v, int n0, double div) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
+        v[i].x = v[i].x / div;
+        v[i].y = v[i].y / div;
+    }
+}
+
+// nearest integer (ties to even) of a double, as a signed 128-bit value, reduced mod q
+__device__ __forceinline__ uint64_t round_reduce(double x, const ModC &m) {
+    double r = rint(x);
+    if (fabs(r) < 9.2e18) return reduce_i64((int64_t)r, m);
+    // |r| >= 2^63: r is an integer m 2^e with a 53-bit m
+    unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+    int e = (int)((bits >> 52) & 0x7ff) - 1075;
+    unsigned long long man = (bits & ((1ULL << 52) - 1)) | (1ULL << 52);
+    unsigned __int128 mag = (unsigned __int128)man << e;
+    uint64_t v = (uint64_t)(mag % m.q);
+    return (bits >> 63) ? neg_mod(v, m.q) : v;
+}
+
+// coefficient k of round(scale * t): t_k = Re w_k (k < N0), Im w_{k-N0} (k >= N0)
+__global__ void k_round_to_limbs(uint64_t *out, long so, const double2 *w, double scale, int count, int nper,
+                                 LimbMap map, const ModC *mods, int logN) {
+    EW_PROLOGUE
+    int n0 = N >> 1;
+    double t = k < n0 ? w[k].x : w[k - n0].y;
+    out[po * so + (long)li * N + k] = round_reduce(scale * t, m);
+    }
+}
+
+// Garner: centred value of each coefficient from L residues, as a double divided by scale,
+// written as w_k = t_k + i t_{k+N0}.  gc: per level constants [L][L] of (prod_{j<i} q_j mod q_i)
+// and inverses; computed on the host.
+__global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qmap, const ModC *mods,
+                                const uint64_t *radix, const uint64_t *radinv, const double *qd, double scale, int logN) {
+    const int N = 1 << logN, n0 = N >> 1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        uint64_t a[HE_MAX_LIMBS], b[HE_MAX_LIMBS];
+        for (int pass = 0; pass < 2; pass++) {
+            uint64_t *dg = pass ? b : a;
+            for (int i = 0; i < L; i++) {
+                const ModC mi = mods[qmap.prime[i]];
+                uint64_t xi = x[(long)i * N + k];
+                if (pass) xi = neg_mod(xi, mi.q);
+                uint64_t acc = 0;
+                for (int j = 0; j < i; j++) acc = add_mod(acc, mul_mod(reduce_u64(dg[j], mi), radix[i * HE_MAX_LIMBS + j], mi), mi.q);
+                dg[i] = mul_mod(sub_mod(xi, acc, mi.q), radinv[i], mi);
+            }
+        }
+        int neg = 0;
+        for (int i = L - 1; i >= 0; i--)
+            if (a[i] != b[i]) { neg = a[i] > b[i]; break; }
+        const uint64_t *d = neg ? b : a;
+        double v = 0.0;
+        for (int i = L - 1; i >= 0; i--) v = v * qd[i] + (double)d[i];
+        v = (neg ? -v : v) / scale;
+        if (k < n0) w[k].x = v;
+        else w[k - n0].y = v;
+    }
+}
+
+// switching-key rows: b = e - a s + [limb in digit] pmod_t s'  (all NTT form, limbs of Q u P)
+__global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
+                              Scal pm, int nl, int dlo, int dhi, LimbMap map, const ModC *mods, int logN) {
+    const int N = 1 << logN;
+    long total = (long)nl << logN;
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
+        int t = (int)(x >> logN);
+        const ModC m = mods[map.prime[t]];
+        uint64_t v = sub_mod(e[x], mul_mod(a[x], s[x], m), m.q);
+        if (t >= dlo && t < dhi && sp) v = add_mod(v, mul_mod(pm.v[t], sp[x], m), m.q);
+        b[x] = v;
+    }
+}
+
+// bounded spin used only by the device-wait self test: waits for *flag != 0 at most max_iter
+// polls, then records a timeout in *status (1 = flag seen, 2 = gave up) and returns
+__global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter) {
+    if (threadIdx.x || blockIdx.x) return;
+    for (long i = 0; i < max_iter; i++) {
+        if (*flag) { *status = 1; return; }
+    }
+    *status = 2;
+}

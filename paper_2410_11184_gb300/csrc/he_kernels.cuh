@@ -1,0 +1,61 @@
+// Kernel declarations shared by the host orchestration (he_host.cu).
+#pragma once
+#include "he_common.cuh"
+
+struct Scal {
+    uint64_t v[HE_MAX_LIMBS];
+};
+
+__global__ void k_ntt_cols_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, int logN, int logN1, int C);
+__global__ void k_ntt_rows_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, int logN, int logN1, int R);
+__global__ void k_ntt_rows_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, int logN, int logN1, int R);
+__global__ void k_ntt_cols_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
+                               const uint64_t *tw, const uint64_t *ninv, int logN, int logN1, int C);
+__global__ void k_add(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
+                      int count, int nper, LimbMap map, const ModC *mods, int logN, int sub);
+__global__ void k_mul(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
+                      int count, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
+__global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal,
+                             int count, int nper, LimbMap map, const ModC *mods, int logN);
+__global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int nper, LimbMap map,
+                             const ModC *mods, int logN);
+__global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
+                         int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
+__global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN);
+__global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
+                        int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
+                        int logN);
+__global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
+                               const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN);
+__global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
+                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN, int accumulate);
+__global__ void k_ks_inner(uint64_t *acc, const uint64_t *dig, int nct, int ndig, int L, int alpha,
+                           LimbMap tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all,
+                           int g, int logN);
+__global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,
+                                 const ModC *mods, uint64_t ql, int logN);
+__global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *t, int npoly, int L, LimbMap qmap,
+                              const ModC *mods, const uint64_t *qlinv, int logN);
+__global__ void k_modraise(uint64_t *out, const uint64_t *x0, int npoly, int L, LimbMap qmap, const ModC *mods,
+                           uint64_t q0, int logN);
+__global__ void k_sample_uniform(uint64_t *out, long so, int count, int nper, LimbMap map,
+                                 const ModC *mods, uint64_t seed, uint64_t dom, int logN);
+__global__ void k_sample_small(int64_t *out, int n, uint64_t seed, uint64_t dom, uint64_t ctr0,
+                               const uint64_t *cdt, int cdt_len, int kind);
+__global__ void k_sample_hwt(int64_t *out, int n, int h, uint64_t seed, uint64_t dom, uint64_t dom_sign);
+__global__ void k_small_to_limbs(uint64_t *out, long so, const int64_t *v, int count, int nper, LimbMap map,
+                                 const ModC *mods, int logN);
+__global__ void k_bitrev_c(double2 *v, int n0, int logn0);
+__global__ void k_sfft_fwd_stage(double2 *v, int n0, int len, const double2 *zeta, const int *rg, int m2n);
+__global__ void k_sfft_inv_stage(double2 *v, int n0, int len, const double2 *zeta, const int *rg, int m2n);
+__global__ void k_scale_c(double2 *v, int n0, double div);
+__global__ void k_round_to_limbs(uint64_t *out, long so, const double2 *w, double scale, int count, int nper,
+                                 LimbMap map, const ModC *mods, int logN);
+__global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qmap, const ModC *mods,
+                                const uint64_t *radix, const uint64_t *radinv, const double *qd, double scale, int logN);
+__global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
+                              Scal pm, int nl, int dlo, int dhi, LimbMap map, const ModC *mods, int logN);
+__global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter);

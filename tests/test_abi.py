@@ -1,0 +1,41 @@
+"""The C ABI library loads and exports every entry point include/he_gb300.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "he_gb300.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(he_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("he_context_create", "he_keygen", "he_encrypt", "he_softmax", "he_decrypt", "he_bootstrap",
+                 "he_hmult", "he_rotate", "he_rescale", "he_ntt"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2410_11184_gb300 import build
+
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2410_11184_gb300 import he
+
+    monkeypatch.setattr(he, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(he, "_lib", None)
+    try:
+        he.lib()
+    except RuntimeError as e:
+        assert "no CPU fallback" in str(e)
+    else:
+        raise AssertionError("expected a failure")

@@ -1,0 +1,210 @@
+"""GPU path (C ABI through the thin binding) against the CPU oracle.
+
+Ciphertexts are compared limb by limb in coefficient form, bit for bit: the two sides use
+different NTT orderings and roots, so equality in coefficient form is independent of them.
+Decrypted values are compared with the FP64 references within the stated tolerances."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_2410_11184_gb300 import he  # noqa: E402
+
+SEED = 7
+
+
+def _rand_ct(o, level, rng, nct=1):
+    d = np.zeros((nct, 2, level + 1, o.n), dtype=np.uint64)
+    for t in range(level + 1):
+        d[:, :, t] = rng.integers(0, o.q[t], (nct, 2, o.n), dtype=np.uint64)
+    return d
+
+
+@pytest.fixture(scope="module")
+def toy(params):
+    ch = params[0]["toy"]
+    g = he.Context(ch)
+    g.keygen(SEED, rot_steps=[1, 3, 5, 64])
+    o = O.Oracle(ch)
+    o.keygen(SEED)
+    return g, o
+
+
+@pytest.fixture(scope="module")
+def toybts(params):
+    ch = params[0]["toybts"]
+    em = params[2]["toybts"]
+    g = he.Context(ch, em)
+    g.keygen(SEED, rot_steps=[1])
+    o = O.Oracle(ch)
+    o.keygen(SEED)
+    return g, o, em
+
+
+def test_library_exports_and_bounded_wait(toy):
+    g, _ = toy
+    assert he.lib().he_ring_degree(g.h) == 4096
+    assert g.selftest_bounded_wait(1000) == -6  # HE_ETIMEOUT, context still usable
+    assert g.counters()["ks"] >= 0
+
+
+def test_ntt_product_matches_oracle(toy):
+    g, o = toy
+    rng = np.random.default_rng(1)
+    lv = 4
+    a = _rand_ct(o, lv, rng)
+    a[:, 1] = 0
+    b = np.stack([rng.integers(0, o.q[t], o.n, dtype=np.uint64) for t in range(lv + 1)])
+    ga = g.from_coeff(a, lv, 1.0)
+    pt = torch.from_numpy(b.view(np.int64).reshape(-1).copy()).to(g.device)
+    g.ntt(pt, 1, lv + 1)
+    g.mul_plain(ga, pt)
+    out = g.to_coeff(ga)
+    for t in range(lv + 1):
+        assert np.array_equal(out[0, 0, t], o.polymul(t, a[0, 0, t], b[t]))
+    # inverse . forward = identity
+    assert np.array_equal(g.to_coeff(g.from_coeff(a, lv, 1.0)), a)
+
+
+def test_encode_bit_exact(toy):
+    g, o = toy
+    rng = np.random.default_rng(2)
+    z = rng.uniform(-1, 1, o.n0) + 1j * rng.uniform(-1, 1, o.n0)
+    for scale in (2.0 ** 40, float(o.q[7]) * 3.5, 2.0 ** 70):
+        pt = g.encode(z, scale, 7)
+        g.ntt(pt, 1, 8, inverse=True)
+        got = pt.cpu().numpy().view(np.uint64).reshape(8, o.n)
+        assert np.array_equal(got, o.encode(z, scale, 7))
+
+
+def test_encrypt_bit_exact_and_decrypt(toy):
+    g, o = toy
+    rng = np.random.default_rng(3)
+    z = rng.uniform(-1, 1, o.n0)
+    for idx in (0, 5):
+        gc = g.encrypt_slots(z, 20, 2.0 ** 40, 99, ct_index=idx)
+        oc = o.encrypt(z, 20, 2.0 ** 40, 99, idx)
+        assert np.array_equal(g.to_coeff(gc)[0], oc.data)
+        assert np.abs(g.decrypt_slots(gc).real - z).max() < 2 ** -20
+
+
+def test_rescale_hmult_relin_bit_exact(toy):
+    g, o = toy
+    rng = np.random.default_rng(4)
+    x, y = rng.uniform(-1, 1, o.n0), rng.uniform(-1, 1, o.n0)
+    a, b = o.encrypt(x, 12, 2.0 ** 40, 5, 0), o.encrypt(y, 11, 2.0 ** 40, 5, 1)
+    ga, gb = g.from_coeff(a.data, 12, a.scale), g.from_coeff(b.data, 11, b.scale)
+    r = o.rescale(a)
+    gr = g.rescale(ga)
+    assert np.array_equal(g.to_coeff(gr)[0], r.data) and gr.scale == r.scale
+    p = o.hmult(a, b)
+    gp = g.hmult(ga, gb)
+    assert gp.level == p.level and gp.scale == p.scale
+    assert np.array_equal(g.to_coeff(gp)[0], p.data)
+    d = np.stack([rng.integers(0, o.q[t], (3, o.n), dtype=np.uint64) for t in range(6)], axis=1)
+    dt = torch.from_numpy(d.view(np.int64).reshape(-1).copy()).to(g.device)
+    g.ntt(dt, 3, 6)
+    gk = g.relinearize(dt, 5, 1)
+    assert np.array_equal(g.to_coeff(gk)[0], o.relin(d, 5))
+
+
+def test_rotations_bit_exact(toy):
+    g, o = toy
+    rng = np.random.default_rng(5)
+    a = o.encrypt(rng.uniform(-1, 1, o.n0) + 1j * rng.uniform(-1, 1, o.n0), 9, 2.0 ** 40, 6)
+    ga = g.from_coeff(a.data, 9, a.scale)
+    for r in (1, 3, 64):
+        assert np.array_equal(g.to_coeff(g.rotate(ga, r))[0], o.rotate(a, r).data)
+    assert np.array_equal(g.to_coeff(g.conjugate(ga))[0], o.conjugate(a).data)
+
+
+@pytest.mark.parametrize("deg", [7, 15, 63])
+def test_poly_eval_bit_exact(toy, deg):
+    g, o = toy
+    rng = np.random.default_rng(deg)
+    c = rng.normal(size=deg + 1) / (1 + np.arange(deg + 1)) ** 1.5
+    a = o.encrypt(rng.uniform(-1, 1, o.n0), 20, float(o.q[20]), 8)
+    d = math.ceil(math.log2(deg + 1))
+    r = o.poly_eval(a, c, 20 - d, 2.0 ** 40)
+    gr = g.poly_eval(g.from_coeff(a.data, 20, a.scale), c, 20 - d, 2.0 ** 40)
+    assert gr.scale == r.scale
+    assert np.array_equal(g.to_coeff(gr)[0], r.data)
+
+
+def test_lintrans_and_modraise_bit_exact(toybts):
+    g, o, em = toybts
+    rng = np.random.default_rng(6)
+    a = o.encrypt(rng.uniform(-1, 1, o.n0), 3, 2.0 ** 42, 9)
+    ga = g.from_coeff(a.data, 3, a.scale)
+    for which in range(3):
+        r = o.lintrans(a, 3, False, which, 16.0 if which == 0 else 1.0, float(o.q[a.level]))
+        gr = g.lintrans(ga, 3, False, which, 16.0 if which == 0 else 1.0, float(o.q[a.level]))
+        assert np.array_equal(g.to_coeff(gr)[0], r.data), which
+        a, ga = r, gr
+    top = len(o.q) - 1
+    mr = o.mod_raise(a, top)
+    assert np.array_equal(g.to_coeff(g.mod_raise(ga, top))[0], mr.data)
+    r = o.lintrans(mr, 3, True, 0, 1.0, float(o.q[top]))
+    gr = g.lintrans(g.from_coeff(mr.data, top, mr.scale), 3, True, 0, 1.0, float(o.q[top]))
+    assert np.array_equal(g.to_coeff(gr)[0], r.data)
+
+
+def test_bootstrap_bit_exact(toybts):
+    g, o, em = toybts
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1, 1, o.n0)
+    a = o.encrypt(x, 3, 2.0 ** 42, 10)
+    r = o.bootstrap(a, em, gain=16.0)
+    gr = g.bootstrap(g.from_coeff(a.data, 3, a.scale), 16.0, 2.0 ** 42)
+    assert gr.level == r.level and gr.scale == r.scale
+    assert np.array_equal(g.to_coeff(gr)[0], r.data)
+    assert np.abs(g.decrypt_slots(gr).real / 16.0 - x).max() < 2 ** -22
+
+
+def test_softmax_toy_bit_exact(toy, params):
+    g, o = toy
+    pl = params[1]["cfg1_n16_M8"]
+    n = pl["n"]
+    g.keygen_softmax(n, 1)
+    rng = np.random.default_rng(8)
+    L = o.n0 // n
+    x = rng.uniform(-pl["M"], 0, (L, n))
+    gc = g.encrypt(x, n, 1, pl["M"], 31)
+    top = o.chain["user_top_level"]
+    oc = o.encrypt(O.pack(x, 1, o.n0)[0], top, (2 / pl["M"]) * o.q[top], 31, 0)
+    assert np.array_equal(g.to_coeff(gc)[0], oc.data)
+    g.softmax(gc, pl)
+    out = o.softmax([oc], pl)[0]
+    assert gc.level == out.level and gc.scale == out.scale
+    assert np.array_equal(g.to_coeff(gc)[0], out.data)
+    y = g.decrypt(gc, n)
+    assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_softmax_bootstrapped_bit_exact(toybts, params, batched):
+    g, o, em = toybts
+    pl = params[1]["toybts_n16_M32"]
+    n, m = pl["n"], 2
+    g.keygen_softmax(n, m)
+    rng = np.random.default_rng(9)
+    L = m * o.n0 // n
+    x = rng.uniform(-pl["M"], 0, (L, n))
+    gc = g.encrypt(x, n, m, pl["M"], 32)
+    top = o.chain["user_top_level"]
+    slots = O.pack(x, m, o.n0)
+    ocs = [o.encrypt(slots[i], top, (2 / pl["M"]) * o.q[top], 32, i) for i in range(m)]
+    g.softmax(gc, pl, batched=batched)
+    outs = o.softmax(ocs, pl, em)
+    assert gc.level == outs[0].level and gc.scale == outs[0].scale
+    got = g.to_coeff(gc)
+    for i in range(m):
+        assert np.array_equal(got[i], outs[i].data), i
+    assert np.abs(g.decrypt(gc, n) - O.softmax_fp64(x)).max() < 2 ** -15
