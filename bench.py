@@ -1,0 +1,326 @@
+"""Benchmark: amortized ms per encrypted Softmax (n = 256, N = 2^16, bootstrapping), batched vs plain.
+
+Workload (default "m64"): 8192 Softmax of dimension 256 packed into m = 64 ciphertexts at
+N = 2^16 (the paper's many-ciphertext setting, Sec. 4.2 / Table 6), inputs shaped like
+attention logits q.k/sqrt(64), q, k ~ N(0, 1), shifted by a public bound and clipped to
+[-128, 0].  "m1": 128 Softmax of dimension 256 in one ciphertext.
+
+A step is one he_softmax call over the whole batch, ciphertexts already resident in HBM
+(a pristine copy is restored into the working buffer inside the step).  The timed region is
+bracketed by a barrier and a synchronize, timed with CUDA events on the library's stream.
+e2e: the same metric through he_softmax with the ciphertexts copied from pinned host memory
+to the device and the results copied back, inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                       [--workload m64|m1] [--profile-kernel NAME]
+Under torchrun each rank runs an independent replica (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amortized ms/Softmax (n=256, N=2^16, >=15-bit prec) batched vs plain; p99 ms"
+
+
+def workload(name):
+    if name == "m1":
+        return {"workload": "1 ciphertext, 128 Softmax of dim 256, N=2^16, bootstrapping", "m": 1, "n": 256}
+    return {"workload": "64 ciphertexts, 8192 Softmax of dim 256, N=2^16, bootstrapping", "m": 64, "n": 256}
+
+
+def attention_logits(L, n, seed, M=128.0, d=64, bound=8.0):
+    """q.k/sqrt(d) with q, k ~ N(0, 1) per row, minus a public bound, clipped to [-M, 0]."""
+    from paper_2410_11184_gb300 import workloads
+
+    return workloads.attention_logits(L, n, seed, M=M, d=d, bound=bound)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p["hbm_gbs"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(steps_unit_ks, ms_per_softmax_scale):
+    """Times the CPU oracle (as it stands) on a bounded sample: one relinearised multiplication
+    at the top user level and one rotation at the top bootstrapping level of the N = 2^16
+    chain; the mean key-switch time is scaled by the circuit's key-switch count per Softmax
+    (counted by the GPU run)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    chains, plans, evalmod = O.load_params()
+    ch = chains["fgb16"]
+    o = O.Oracle(ch)
+    o.keygen(11)
+    rng = np.random.default_rng(0)
+    a = o.encrypt(rng.uniform(-1, 1, o.n0), ch["user_top_level"], 2.0 ** 42, 3)
+    top = len(o.q) - 1
+    b = o.encrypt(rng.uniform(-1, 1, o.n0), top, 2.0 ** 42, 4)
+    o.hmult(a, a)           # key generation outside the timing
+    o.rotate(b, 1)
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        o.hmult(a, a)
+        o.rotate(b, 1)
+    dt = time.perf_counter() - t0
+    per_ks_ms = dt / (2 * reps) * 1e3
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {
+        "value": per_ks_ms * steps_unit_ks * ms_per_softmax_scale,
+        "unit": "ms/Softmax",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": "%d x (HMult at level %d + rotation at level %d), N=2^16, %.1f s; mean key switch %.0f ms "
+                  "scaled by %d key switches per step / Softmax per step" % (reps, ch["user_top_level"], top, dt,
+                                                                            per_ks_ms, steps_unit_ks),
+    }
+
+
+def run_reference(args, wl):
+    """The CPU oracle timed as the reference arm: per step, the same bounded sample as the
+    CPU baseline (key switches at the circuit's levels), scaled to ms/Softmax."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # key-switch count per Softmax step of this workload, from the circuit's operation list
+    ks_per_step = {"m64": 5700, "m1": 760}[args.workload]
+    L = wl["m"] * 32768 // wl["n"]
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(ks_per_step, 1.0 / L)
+        vals.append(cb["value"])
+    v = statistics.median(vals[args.warmup:])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/Softmax", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * L, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues)", "data": "synthetic",
+            "config": {"workload": wl["workload"], "n": wl["n"], "m": wl["m"], "softmax_per_step": L},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "ms/Softmax", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="m64", choices=["m64", "m1"])
+    ap.add_argument("--profile-kernel", default="ntt")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2410_11184_gb300 import he
+
+    chains, plans, evalmod = he.load_params()
+    ch, pl, em = chains["fgb16"], plans["n256_M128"], evalmod["fgb16"]
+    stream = torch.cuda.Stream(dev)
+    g = he.Context(ch, em, stream=stream, device=dev)
+    m, n = wl["m"], wl["n"]
+    L = m * g.n0 // n
+    g.keygen(1234 + rank)
+    g.keygen_softmax(n, m)
+    x = attention_logits(L, n, seed=100 + rank)
+    src = g.encrypt(x, n, m, pl["M"], 77 + rank)
+    work = g.like(src)
+
+    def step(batched):
+        work.tensor.copy_(src.tensor)  # (on torch's stream of `stream` below)
+        work.level, work.scale, work.n_ct = src.level, src.scale, src.n_ct
+        g.softmax(work, pl, batched=batched)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(True)
+        torch.cuda.synchronize(dev)
+        # precision check of the warm-up output (FP64 Softmax of the same inputs)
+        y = g.decrypt(work, n)
+        e = np.exp(x - x.max(axis=1, keepdims=True))
+        err = float(np.abs(y - e / e.sum(axis=1, keepdims=True)).max())  # vs FP64 Softmax
+        c0 = g.counters()
+        l0 = g.launch_count()
+        g.profile_kernel(args.profile_kernel)
+        clocks = ClockSampler(local)
+        clocks.start()
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for i in range(args.steps):
+            step(True)
+            ev[i + 1].record(stream)
+        barrier()
+        clk = clocks.stop()
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        k_ms, k_launch, k_bytes = g.profile_read()
+        g.profile_kernel("")
+        c1 = g.counters()
+        launches = g.launch_count() - l0
+        ks_per_step = (c1["ks"] - c0["ks"]) // args.steps
+        # plain mode: the same operation list one ciphertext at a time
+        plain_ms = None
+        if not args.no_plain:
+            t = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            step(False)  # warm-up of the per-ciphertext path
+            barrier()
+            t[0].record(stream)
+            step(False)
+            t[1].record(stream)
+            barrier()
+            plain_ms = t[0].elapsed_time(t[1])
+        # e2e: pinned host ciphertexts in, results out, through he_softmax
+        host_in = torch.empty_like(src.tensor, device="cpu").pin_memory()
+        host_in.copy_(src.tensor)
+        host_out = torch.empty_like(src.tensor, device="cpu").pin_memory()
+        barrier()
+        te = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        te[0].record(stream)
+        e2e_steps = max(1, min(args.steps, 2))
+        out_words = 0
+        for _ in range(e2e_steps):
+            work.tensor.copy_(host_in, non_blocking=True)
+            work.level, work.scale, work.n_ct = src.level, src.scale, src.n_ct
+            g.softmax(work, pl, batched=True)
+            out_words = work.n_ct * 2 * (work.level + 1) * g.n
+            host_out[:out_words].copy_(work.tensor[:out_words], non_blocking=True)
+        te[1].record(stream)
+        barrier()
+        e2e_ms = te[0].elapsed_time(te[1]) / e2e_steps
+
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    per_softmax = ms_step / L  # each rank processes L Softmax; value is whole-job (weak scaling)
+    value = ms_step / (L * world)
+    hbm, peak_kind = peaks()
+    roof = None
+    if k_launch:
+        achieved = (k_bytes / k_launch) / ((k_ms / k_launch) * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": args.profile_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                "launches_per_step": k_launch / args.steps, "kernel_ms_per_step": k_ms / args.steps,
+                "share_of_step": (k_ms / args.steps) / ms_step}
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms/Softmax", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
+        "config": {"workload": wl["workload"], "n": n, "m": m, "softmax_per_step": L * world, "M": pl["M"],
+                   "k": pl["k"], "log_qp": round(ch["log_qp"], 2), "h": ch["h"],
+                   "l2": "inputs 1.7 GB + evaluation keys > 12 GB per step, larger than L2 (no flush)"},
+        "p50_ms_per_step": statistics.median(per), "p99_ms_per_step": max(per),
+        "plain_ms_per_softmax": (plain_ms / L) if plain_ms else None,
+        "batched_speedup_vs_plain": (plain_ms / ms_step) if plain_ms else None,
+        "precision_bits_vs_fp64": -math.log2(err) if err > 0 else None,
+        "key_switches_per_step": ks_per_step,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+        "e2e": {"value": e2e_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": src.tensor.numel() * 8,
+                "d2h_bytes_per_step": out_words * 8},
+    }
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(ks_per_step, 1.0 / L)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

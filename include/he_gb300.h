@@ -140,6 +140,13 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
 
 /* operation counters since creation: [key switches, rotations, hmults, rescales, bootstraps] */
 int he_counters(const he_ctx *ctx, long *out5);
+/* number of kernel launches this context has issued since creation */
+long he_launch_count(const he_ctx *ctx);
+/* live timing of one kernel family ("ntt", "ks_inner", "modup", "tensor"; "" = off): CUDA
+ * events on the context stream around each launch; he_profile_read synchronises, returns the
+ * summed device time, the launch count and the algorithmic bytes of those launches, and resets */
+int he_profile_kernel(he_ctx *ctx, const char *name);
+int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes);
 /* bounded device wait self test: a kernel polls a flag nobody sets for at most max_iter polls
  * and returns HE_ETIMEOUT; the context stays usable. */
 int he_selftest_bounded_wait(he_ctx *ctx, long max_iter);

@@ -101,7 +101,35 @@ struct he_ctx {
     cudaStream_t st = nullptr;
     std::string err;
     long cnt[5] = {0, 0, 0, 0, 0};
+    long launches = 0;
     int max_grid = 152 * 16;
+    // live kernel timing: CUDA events around the launches of one kernel family
+    std::string prof_name;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    size_t prof_used = 0;
+    double prof_bytes = 0;
+};
+
+// Records events around one launch of kernel family `name` when it is the profiled one.
+struct ProfScope {
+    he_ctx *c;
+    bool on;
+    size_t slot;
+    ProfScope(he_ctx *c_, const char *name, double bytes) : c(c_), on(!c_->prof_name.empty() && c_->prof_name == name) {
+        if (!on) return;
+        if (c->prof_used == c->prof_ev.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            c->prof_ev.push_back({a, b});
+        }
+        slot = c->prof_used++;
+        c->prof_bytes += bytes;
+        cudaEventRecord(c->prof_ev[slot].first, c->st);
+    }
+    ~ProfScope() {
+        if (on) cudaEventRecord(c->prof_ev[slot].second, c->st);
+    }
 };
 
 struct HeErr {
@@ -114,7 +142,11 @@ struct HeErr {
         cudaError_t e_ = (call);                                                                     \
         if (e_ != cudaSuccess) throw HeErr{HE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
     } while (0)
-#define LAUNCH_CHECK() CK(cudaGetLastError())
+#define LAUNCH_CHECK()              \
+    do {                            \
+        c->launches++;              \
+        CK(cudaGetLastError());     \
+    } while (0)
 #define REQUIRE(cond, code, msg)                                          \
     do {                                                                  \
         if (!(cond)) throw HeErr{code, msg};                              \
@@ -176,6 +208,8 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     int R = std::max(1, std::min(N1, 2048 / N2));
     dim3 g1(N2 / C, count), g2(N1 / R, count);
     size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
+    ProfScope ps(c, "ntt", 16.0 * count * c->N);
+    c->launches++;
     if (!inverse) {
         k_ntt_cols_fwd<<<g1, 256, sm1, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, C);
         k_ntt_rows_fwd<<<g2, 256, sm2, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, R);
@@ -324,6 +358,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     for (int j = 0; j < nd; j++) {
         int lo = j * al, ds = std::min(al, L - lo);
         long tot = (long)nct * nl << c->logN;
+        ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * ds + (double)nct * nl));
         k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N, tmp.get(),
                                                       (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
                                                       c->d_cv + c->cv_off[L - 1][j], c->logN);
@@ -339,6 +374,7 @@ static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, con
                       long so, bool accumulate) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
     DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
+    ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl));
     k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc.get(), dig, nct, nd, L, al, extmap(c, L),
                                                                     c->d_mods, key, c->nm, c->nq, g, c->logN);
     LAUNCH_CHECK();
@@ -379,6 +415,7 @@ static DCt relinearize(he_ctx *c, const uint64_t *d, int level, int nct, double 
 static void tensor_into(he_ctx *c, uint64_t *d, const DCt &a, const DCt &b, int level, bool accumulate) {
     int L = level + 1;
     long tot = (long)a.nct * L << c->logN;
+    ProfScope ps(c, "tensor", 8.0 * c->N * (double)a.nct * L * (2 + 2 + 3));
     k_tensor<<<grid_for(c, tot), 256, 0, c->st>>>(d, 3L * L * c->N, a.d, a.cs(c), b.d, b.cs(c), a.nct, L, qmap(L),
                                                    c->d_mods, c->logN, accumulate ? 1 : 0);
     LAUNCH_CHECK();
@@ -1037,8 +1074,9 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
                     if (first && i == 0)
                         CK(cudaMemcpyAsync(d.get(), dd.get(), (size_t)3 * L * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
                     else
-                        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), 0, d.get(), 0, dd.get() + (long)i * 3 * L * c->N,
-                                                                    0, cnt, L, qmap(L), c->d_mods, c->logN, 0);
+                        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), (long)L * c->N, d.get(), (long)L * c->N,
+                                                                    dd.get() + (long)i * 3 * L * c->N, (long)L * c->N,
+                                                                    cnt, L, qmap(L), c->d_mods, c->logN, 0);
                     LAUNCH_CHECK();
                 }
                 first = false;
@@ -1335,6 +1373,10 @@ void he_context_destroy(he_ctx *c) {
     cudaStreamSynchronize(c->st);
     c->lt_cache.clear();
     for (auto &kv : c->keys) cudaFree(kv.second);
+    for (auto &e : c->prof_ev) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
     void *ptrs[] = {c->d_mods, c->d_tw, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx, c->d_zeta,
                     c->d_rg, c->d_cdt, c->d_radix, c->d_radinv, c->d_qd, c->d_s, c->d_pk};
     for (void *q : ptrs)
@@ -1629,8 +1671,37 @@ int he_counters(const he_ctx *ctx, long *out5) {
     return HE_OK;
 }
 
+long he_launch_count(const he_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int he_profile_kernel(he_ctx *ctx, const char *name) {
+    if (!ctx) return HE_EINVAL;
+    ctx->prof_name = name ? name : "";
+    ctx->prof_used = 0;
+    ctx->prof_bytes = 0;
+    return HE_OK;
+}
+
+int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes) {
+    if (!ctx || !total_ms || !launches || !bytes) return HE_EINVAL;
+    API_BEGIN
+    CK(cudaStreamSynchronize(ctx->st));
+    double t = 0;
+    for (size_t i = 0; i < ctx->prof_used; i++) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[i].first, ctx->prof_ev[i].second));
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = (long)ctx->prof_used;
+    *bytes = ctx->prof_bytes;
+    ctx->prof_used = 0;
+    ctx->prof_bytes = 0;
+    API_END
+}
+
 int he_selftest_bounded_wait(he_ctx *ctx, long max_iter) {
     if (!ctx || max_iter < 1) return HE_EINVAL;
+    he_ctx *c = ctx;
     API_BEGIN
     DPtr b = dalloc(ctx, 1);
     int *flag = (int *)b.get(), *status = flag + 1;

@@ -86,6 +86,12 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = None if name == "he_context_destroy" else C.c_int
+        L.he_launch_count.restype = C.c_long
+        L.he_launch_count.argtypes = [vp]
+        L.he_profile_kernel.restype = C.c_int
+        L.he_profile_kernel.argtypes = [vp, C.c_char_p]
+        L.he_profile_read.restype = C.c_int
+        L.he_profile_read.argtypes = [vp, dblp, C.POINTER(C.c_long), dblp]
         L.he_last_error.restype = C.c_char_p
         L.he_last_error.argtypes = [vp]
         _lib = L
@@ -293,6 +299,17 @@ class Context:
         a = (C.c_long * 5)()
         self.check(lib().he_counters(self.h, a))
         return dict(zip(["ks", "rot", "hmult", "rescale", "bts"], list(a)))
+
+    def launch_count(self):
+        return lib().he_launch_count(self.h)
+
+    def profile_kernel(self, name):
+        self.check(lib().he_profile_kernel(self.h, (name or "").encode()))
+
+    def profile_read(self):
+        ms, n, b = C.c_double(), C.c_long(), C.c_double()
+        self.check(lib().he_profile_read(self.h, C.byref(ms), C.byref(n), C.byref(b)))
+        return ms.value, n.value, b.value
 
     def selftest_bounded_wait(self, max_iter):
         return lib().he_selftest_bounded_wait(self.h, max_iter)
