@@ -11,9 +11,14 @@
  *      mod the other Q primes.)  Relinearisation: s' = s^2; rotation: s' = s(X^g).
  * Key switching of d at level l (hybrid):
  *   ModUp   : for digit D, limbs t not in D get sum_{i in D} [d_i (Q_D/q_i)^{-1}]_{q_i} (Q_D/q_i)
- *             mod m_t (input representatives in [0, q_i), no correction);
+ *             mod m_t, each [.]_{q_i} taken as its centred representative (no further
+ *             correction; the result is d + u Q_D with |u| <= |D|/2, zero mean);
  *   product : c_0 = sum_j d~_j b_j, c_1 = sum_j d~_j a_j over Q_l u P;
- *   ModDown : c_t <- (c_t - sum_k [c_{p_k} (P/p_k)^{-1}]_{p_k} (P/p_k)) P^{-1} mod q_t.
+ *   ModDown : c_t <- (c_t - sum_k [c_{p_k} (P/p_k)^{-1}]_{p_k} (P/p_k)) P^{-1} mod q_t, with the
+ *             centred representative of each [.]_{p_k} in (-p_k/2, p_k/2]: the conversion error
+ *             v P (|v| <= alpha/2) then has zero mean.  With [0, p_k) representatives v has mean
+ *             about alpha/2, a constant on every coefficient, whose slot values 2v/(1 - zeta_j)
+ *             are large at the slots with zeta_j near 1 and cost several bits there.
  * Rotation by galois element g: ModUp of c1 first, then X -> X^g on every extended digit and
  *   on c0, then the product with swk(s(X^g) -> s) and ModDown.  The result does not depend on
  *   whether the ModUp is shared among several rotations (hoisting).
@@ -342,8 +347,11 @@ uint64_t *modup(orc_ctx *c, const uint64_t *d, int level) {
             for (int k = 0; k < N_; k++) {
                 uint64_t acc = 0;
                 for (int i = lo; i < hi; i++) {
-                    uint64_t y = mulmod(d[(size_t)i * N_ + k], qhat_inv[i], c->mod[i]);
-                    acc = addmod(acc, mulmod(y % mt, qhat_t[i], mt), mt);
+                    uint64_t qi = c->mod[i];
+                    uint64_t y = mulmod(d[(size_t)i * N_ + k], qhat_inv[i], qi);
+                    /* centred representative in (-q_i/2, q_i/2] */
+                    i128 yc = y <= (qi - 1) / 2 ? (i128)y : (i128)y - (i128)qi;
+                    acc = addmod(acc, mulmod(reduce_i128(yc, mt), qhat_t[i], mt), mt);
                 }
                 o[k] = acc;
             }
@@ -413,7 +421,9 @@ int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_ke
                 for (int k = 0; k < np; k++) {
                     uint64_t pk = c->mod[c->nq + k];
                     uint64_t y = mulmod(acc[(size_t)(L + k) * N_ + kk], phat_inv[k], pk);
-                    conv = addmod(conv, mulmod(y % q, phat_t[k], q), q);
+                    /* centred representative of y in (-p_k/2, p_k/2] */
+                    i128 yc = y <= (pk - 1) / 2 ? (i128)y : (i128)y - (i128)pk;
+                    conv = addmod(conv, mulmod(reduce_i128(yc, q), phat_t[k], q), q);
                 }
                 out[(size_t)t * N_ + kk] = mulmod(submod(acc[(size_t)t * N_ + kk], conv, q), pinv, q);
             }

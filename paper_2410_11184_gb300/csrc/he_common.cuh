@@ -46,6 +46,7 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
     return r >= q ? r - q : r;
 }
 
+// valid for a < 2^62 and b < q (the quotient estimate stays within 2 of the true one)
 __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const ModC &m) {
     uint64_t lo = a * b, hi = he_mulhi(a, b);
     uint64_t x1 = (lo >> (m.s - 2)) | (hi << (66 - m.s));

@@ -357,7 +357,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     LimbMap em = extmap(c, L);
     for (int j = 0; j < nd; j++) {
         int lo = j * al, ds = std::min(al, L - lo);
-        long tot = (long)nct * nl << c->logN;
+        long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)
         ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * ds + (double)nct * nl));
         k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N, tmp.get(),
                                                       (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
@@ -381,7 +381,7 @@ static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, con
     ntt(c, acc.get() + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true);
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
     long tot = (long)2 * nct * L << c->logN;
-    k_moddown_conv<<<grid_for(c, tot), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
+    k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
                                                          c->d_mods, c->d_mdcv, c->nq, c->logN);
     LAUNCH_CHECK();
     ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false);

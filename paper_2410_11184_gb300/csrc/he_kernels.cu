@@ -238,42 +238,73 @@ __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, 
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN) {
+    // one thread per (ciphertext, coefficient): the digit's limbs are read once, then every
+    // target limb is produced (y_i < 2^61 is multiplied mod m_t directly, no pre-reduction)
     const int N = 1 << logN;
-    long total = (long)nct * ntarget << logN;
+    long total = (long)nct << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
-        int l = (int)(id >> logN), k = (int)(id & (N - 1));
-        int t = l % ntarget, c = l / ntarget;
-        const ModC mt = mods[tmap.prime[t]];
-        uint64_t acc = 0;
+        int c = (int)(id >> logN), k = (int)(id & (N - 1));
+        // centred representatives (-q_i/2, q_i/2] (|y_i| and a sign bit): the result is
+        // d + u Q_D with zero-mean u
+        uint64_t y[8];
+        unsigned negmask = 0;
         for (int i = 0; i < dsize; i++) {
-            const int pi = tmap.prime[digit_lo + i];
-            uint64_t qi = mods[pi].q;
-            uint64_t y = mul_shoup(x[c * sx + (long)(digit_lo + i) * N + k], cv[i], cv[dsize + i], qi);
-            acc = add_mod(acc, mul_mod(reduce_u64(y, mt), cv[2 * dsize + i * ntarget + t], mt), mt.q);
+            uint64_t qi = mods[tmap.prime[digit_lo + i]].q;
+            uint64_t v = mul_shoup(x[c * sx + (long)(digit_lo + i) * N + k], cv[i], cv[dsize + i], qi);
+            if (v > (qi - 1) / 2) {
+                v = qi - v;
+                negmask |= 1u << i;
+            }
+            y[i] = v;
         }
-        out[c * so_ct + so_digit + (long)t * N + k] = acc;
+        uint64_t *o = out + c * so_ct + so_digit + k;
+        for (int t = 0; t < ntarget; t++) {
+            const ModC mt = mods[tmap.prime[t]];
+            uint64_t acc = 0;
+            for (int i = 0; i < dsize; i++) {
+                uint64_t v = mul_mod(y[i], cv[2 * dsize + i * ntarget + t], mt);
+                acc = (negmask >> i) & 1 ? sub_mod(acc, v, mt.q) : add_mod(acc, v, mt.q);
+            }
+            o[(long)t * N] = acc;
+        }
     }
 }
 
 // ModDown conversion: conv_i = sum_k [y_k * phinv_k]_{p_k} (phat_k mod q_i); writes conv into
-// out (coefficient domain) for the Q limbs.  x: [nct][2][L + alpha][N] coefficient-domain P limbs
-// at offset L.  cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][L_all] (by Q index).
+// out (coefficient domain) for the Q limbs.  x: [npoly][L + alpha][N] with the coefficient-domain
+// P limbs at offset L.  cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][nqall] (by Q index).
+// One thread per (polynomial, coefficient): the alpha P limbs are read once.
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN) {
     const int N = 1 << logN;
-    long total = (long)npoly * L << logN;
+    long total = (long)npoly << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
-        int l = (int)(id >> logN), k = (int)(id & (N - 1));
-        int i = l % L, pl = l / L;
-        const ModC mi = mods[qmap.prime[i]];
-        const uint64_t *xp = x + (long)pl * (L + alpha) * N + (long)L * N;
-        uint64_t acc = 0;
+        int pl = (int)(id >> logN), k = (int)(id & (N - 1));
+        const uint64_t *xp = x + (long)pl * (L + alpha) * N + (long)L * N + k;
+        // y_j in centred form (-p_j/2, p_j/2]: keep |y_j| and its sign, so that the conversion
+        // error v P has zero mean (a biased v is a constant on every coefficient, whose slot
+        // values concentrate where the evaluation point is near 1)
+        uint64_t y[16];
+        unsigned negmask = 0;
         for (int j = 0; j < alpha; j++) {
             uint64_t pj = mods[pidx[j]].q;
-            uint64_t y = mul_shoup(xp[(long)j * N + k], cv[j], cv[alpha + j], pj);
-            acc = add_mod(acc, mul_mod(reduce_u64(y, mi), cv[2 * alpha + j * nqall + qmap.prime[i]], mi), mi.q);
+            uint64_t v = mul_shoup(xp[(long)j * N], cv[j], cv[alpha + j], pj);
+            if (v > (pj - 1) / 2) {
+                v = pj - v;
+                negmask |= 1u << j;
+            }
+            y[j] = v;
         }
-        out[(long)pl * L * N + (long)i * N + k] = acc;
+        uint64_t *o = out + (long)pl * L * N + k;
+        for (int i = 0; i < L; i++) {
+            const ModC mi = mods[qmap.prime[i]];
+            uint64_t acc = 0;
+            for (int j = 0; j < alpha; j++) {
+                uint64_t t = mul_mod(y[j], cv[2 * alpha + j * nqall + qmap.prime[i]], mi);
+                acc = (negmask >> j) & 1 ? sub_mod(acc, t, mi.q) : add_mod(acc, t, mi.q);
+            }
+            o[(long)i * N] = acc;
+        }
     }
 }
 
@@ -338,7 +369,7 @@ __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly,
         int i = l % Lm1, pl = l / Lm1;
         const ModC mi = mods[qmap.prime[i]];
         uint64_t r = last[(long)pl * N + k];
-        uint64_t v = r <= (ql - 1) / 2 ? reduce_u64(r, mi) : reduce_i64((int64_t)r - (int64_t)ql, mi);
+        uint64_t v = r <= (ql - 1) / 2 ? mul_mod(r, 1, mi) : neg_mod(mul_mod(ql - r, 1, mi), mi.q);
         tmp[(long)pl * Lm1 * N + (long)i * N + k] = v;
     }
 }
@@ -368,7 +399,7 @@ __global__ void k_modraise(uint64_t *out, const uint64_t *x0, int npoly, int L, 
         int i = l % L, pl = l / L;
         const ModC mi = mods[qmap.prime[i]];
         uint64_t r = x0[(long)pl * N + k];
-        uint64_t v = r <= (q0 - 1) / 2 ? reduce_u64(r, mi) : reduce_i64((int64_t)r - (int64_t)q0, mi);
+        uint64_t v = r <= (q0 - 1) / 2 ? mul_mod(r, 1, mi) : neg_mod(mul_mod(q0 - r, 1, mi), mi.q);
         out[(long)pl * L * N + (long)i * N + k] = v;
     }
 }
