@@ -210,6 +210,13 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
     ProfScope ps(c, "ntt", 16.0 * count * c->N);
     c->launches++;
+    if (c->logN == 16 || c->logN == 12) {
+        // register-blocked passes: 16 (N = 2^16) or 8 (N = 2^12) coefficients per thread
+        launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw,
+                      c->d_ninv, c->logN, c->st);
+        LAUNCH_CHECK();
+        return;
+    }
     if (!inverse) {
         k_ntt_cols_fwd<<<g1, 256, sm1, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, C);
         k_ntt_rows_fwd<<<g2, 256, sm2, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, R);
@@ -1037,6 +1044,20 @@ static DCt rotsum(he_ctx *c, DCt x, int stride, int nrot) {
     return x;
 }
 
+// Diagnostics: with HE_DEBUG_DIR set, the decrypted slots of the first ciphertext of each
+// intermediate are written to <dir>/<round>_<name>.bin (N/2 complex doubles).
+static void dbg_dump(he_ctx *c, const char *what, int j, const DCt &x) {
+    const char *dir = getenv("HE_DEBUG_DIR");
+    if (!dir) return;
+    std::vector<double2> z = decrypt_slots(c, x, 0);
+    char fn[512];
+    snprintf(fn, sizeof fn, "%s/%d_%s.bin", dir, j, what);
+    FILE *f = fopen(fn, "wb");
+    if (!f) return;
+    fwrite(z.data(), sizeof(double2), z.size(), f);
+    fclose(f);
+}
+
 // ys: the m main-thread ciphertexts, as one batch (batched) or m batches of one
 static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> ys, int m) {
     int n0 = c->n0, n = p.n;
@@ -1049,12 +1070,14 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         int lvl = y.level - ilog2c(p.exp_deg + 1);
         y = poly_eval(c, y, p.exp_c, lvl, y_target(c, p, 0, lvl));
     }
+    dbg_dump(c, "y0", 0, ys[0]);
     for (int j = 0; j < p.k; j++) {
         int ly = ys[0].level;
         if (main_bts(c, p, j, ly)) {
             double so = y_target(c, p, j, ut);
             for (auto &y : ys) y = bts_boosted(c, p, y, 1.0, so);
             ly = ys[0].level;
+            dbg_dump(c, "ybts", j, ys[0]);
         }
         // S = Relin(sum_c y_c (x) y_c)
         int L = ly + 1;
@@ -1086,6 +1109,7 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         c->cnt[2]++;
         S = rescale(c, S);
         S = rotsum(c, S, stride, nrot);
+        dbg_dump(c, "S", j, S);
         int dj = ilog2c(p.inv_deg[j] + 1);
         DCt v;
         if (!s_bts(c, p, j, ly)) {
@@ -1095,9 +1119,11 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
             double so = (2.0 / (p.b[j] - p.a[j])) * qd(c, ut);
             v = bts_boosted(c, p, S, p.gs[j], so);
         }
+        dbg_dump(c, "v", j, v);
         affine_to_unit(c, v, p.a[j], p.b[j]);
         int lp = v.level - dj;
         DCt lam = poly_eval(c, v, p.inv_c[j], lp, delta);
+        dbg_dump(c, "lam", j, lam);
         bool lam_bts = c->bootstrap && lp - 1 < ly;
         int llam = lam_bts ? ut : lp - 1;
         int lz = std::min(llam, ly);
@@ -1115,10 +1141,12 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         lam = rotsum(c, lam, stride, nrot);
         if (lam_bts) lam = bts_boosted(c, p, lam, 1.0, slam / p.gl[j]);
         lam.scale = lam.scale * p.gl[j];
+        dbg_dump(c, "lamf", j, lam);
         for (auto &y : ys) {
             DCt z = hmult(c, lam, y);
             y = hmult(c, z, z);
         }
+        dbg_dump(c, "y", j, ys[0]);
     }
     return ys;
 }

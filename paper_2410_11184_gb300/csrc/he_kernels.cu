@@ -617,3 +617,200 @@ __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_i
     }
     *status = 2;
 }
+
+// ------------------------------------------------------------------------------------------
+// Register-blocked NTT passes.  A pass runs LOGS = 2*LOGE stages on sub-transforms of size
+// S = 2^LOGS; each thread holds E = 2^LOGE elements of one sub-transform in registers.
+// First LOGE stages: thread lane k holds elements k + E*j (pairs (j, j + 2^p) are its own);
+// one exchange through shared memory; last LOGE stages: lane k holds E*k + j.
+// "cols" passes act on the N2 columns {c + N2 r} (first log2(N1) stages of the transform),
+// "rows" passes on rows of N2 contiguous coefficients (the remaining stages).  The twiddle of
+// the butterfly pair (j, j + t) in stage m is psi_rev[m + group] exactly as in the radix-2
+// definition, so the result equals the one-stage-at-a-time transform.
+template <int LOGE>
+__device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase, int gmul, const uint64_t *psi,
+                                                  const uint64_t *psip, uint64_t q) {
+    // elements j (index k + E j); stages with half-distance t = E/2, E/4, ..., 1 in units of j
+    constexpr int E = 1 << LOGE;
+#pragma unroll
+    for (int p = 0; p < LOGE; p++) {
+        const int t = E >> (p + 1);          // distance in j
+        const int m = m0 << p;               // stage parameter
+#pragma unroll
+        for (int b = 0; b < E / 2; b++) {
+            const int grp = b / t, jj = 2 * grp * t + (b % t);
+            const int idx = m + gbase * (m / m0) * gmul + grp;
+            const uint64_t w = psi[idx], wp = psip[idx];
+            uint64_t u = v[jj], x = mul_shoup(v[jj + t], w, wp, q);
+            v[jj] = add_mod(u, x, q);
+            v[jj + t] = sub_mod(u, x, q);
+        }
+    }
+}
+
+template <int LOGE>
+__device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase, int gmul, const uint64_t *ipsi,
+                                                  const uint64_t *ipsip, uint64_t q) {
+    // inverse of ct_stages_strided: stages in reverse order (t = 1, 2, ..., E/2 in units of j)
+    constexpr int E = 1 << LOGE;
+#pragma unroll
+    for (int p = LOGE - 1; p >= 0; p--) {
+        const int t = E >> (p + 1);
+        const int m = m0 << p;
+#pragma unroll
+        for (int b = 0; b < E / 2; b++) {
+            const int grp = b / t, jj = 2 * grp * t + (b % t);
+            const int idx = m + gbase * (m / m0) * gmul + grp;
+            const uint64_t w = ipsi[idx], wp = ipsip[idx];
+            uint64_t u = v[jj], x = v[jj + t];
+            v[jj] = add_mod(u, x, q);
+            v[jj + t] = mul_shoup(sub_mod(u, x, q), w, wp, q);
+        }
+    }
+}
+
+// Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
+template <int LOGE>
+__global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+                                                         const ModC *mods, const uint64_t *tw, int logN) {
+    constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
+    constexpr int SUB = 256 / TPS;                         // columns per CTA
+    __shared__ uint64_t sm[S * SUB];
+    const int N = 1 << logN, N2 = N / S;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
+    const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = blockIdx.x * SUB + c;
+    uint64_t v[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = a[(long)(k + E * j) * N2 + col];
+    // stages m = 1 .. E/2: element index r = k + E j, group = j / (2t) (independent of k)
+    ct_stages_strided<LOGE>(v, 1, 0, 0, psi, psip, q);
+#pragma unroll
+    for (int j = 0; j < E; j++) sm[(k + E * j) * SUB + c] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = sm[(E * k + j) * SUB + c];
+    // stages m = E .. S/2 on r = E k + j: group = (E k + j) / (2t) = k * (m / E) + j / (2t)
+    ct_stages_strided<LOGE>(v, E, k, 1, psi, psip, q);
+#pragma unroll
+    for (int j = 0; j < E; j++) a[(long)(E * k + j) * N2 + col] = v[j];
+}
+
+// Forward row pass: stages m = N1 .. N/2 on rows of S = N2 contiguous coefficients.
+template <int LOGE>
+__global__ void __launch_bounds__(256) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+                                                         const ModC *mods, const uint64_t *tw, int logN) {
+    constexpr int E = 1 << LOGE, S = E * E, TPS = E;
+    constexpr int SUB = 256 / TPS;                         // rows per CTA
+    __shared__ uint64_t sm[S * SUB];
+    const int N = 1 << logN, N1 = N / S;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
+    const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
+    uint64_t *g = a + (long)row * S;
+    uint64_t v[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = g[k + E * j];
+    // stages m = N1 .. N1 E/2: group = row (m / N1) + j / (2t)
+    ct_stages_strided<LOGE>(v, N1, row, 1, psi, psip, q);
+#pragma unroll
+    for (int j = 0; j < E; j++) sm[rr * S + k + E * j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = sm[rr * S + E * k + j];
+    // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
+    ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, psip, q);
+    // back to the k + E j layout through shared memory so the store is coalesced
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) sm[rr * S + E * k + j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * S + k + E * j];
+}
+
+// Inverse row pass: stages h = N/2 .. N1 (t = 1 .. N2/2).
+template <int LOGE>
+__global__ void __launch_bounds__(256) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+                                                         const ModC *mods, const uint64_t *tw, int logN) {
+    constexpr int E = 1 << LOGE, S = E * E, TPS = E;
+    constexpr int SUB = 256 / TPS;
+    __shared__ uint64_t sm[S * SUB];
+    const int N = 1 << logN, N1 = N / S;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
+    const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
+    uint64_t *g = a + (long)row * S;
+    uint64_t v[E];
+    // coalesced load, then regroup to the E k + j layout through shared memory
+#pragma unroll
+    for (int j = 0; j < E; j++) sm[rr * S + k + E * j] = g[k + E * j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = sm[rr * S + E * k + j];
+    __syncthreads();
+    gs_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, ipsi, ipsip, q);
+#pragma unroll
+    for (int j = 0; j < E; j++) sm[rr * S + E * k + j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = sm[rr * S + k + E * j];
+    gs_stages_strided<LOGE>(v, N1, row, 1, ipsi, ipsip, q);
+#pragma unroll
+    for (int j = 0; j < E; j++) g[k + E * j] = v[j];
+}
+
+// Inverse column pass: stages h = N1/2 .. 1, then the N^{-1} factor.
+template <int LOGE>
+__global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+                                                         const ModC *mods, const uint64_t *tw, const uint64_t *ninv,
+                                                         int logN) {
+    constexpr int E = 1 << LOGE, S = E * E, TPS = E;
+    constexpr int SUB = 256 / TPS;
+    __shared__ uint64_t sm[S * SUB];
+    const int N = 1 << logN, N2 = N / S;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t q = mods[p].q;
+    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
+    const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = blockIdx.x * SUB + c;
+    uint64_t v[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = a[(long)(E * k + j) * N2 + col];
+    gs_stages_strided<LOGE>(v, E, k, 1, ipsi, ipsip, q);
+#pragma unroll
+    for (int j = 0; j < E; j++) sm[(E * k + j) * SUB + c] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; j++) v[j] = sm[(k + E * j) * SUB + c];
+    gs_stages_strided<LOGE>(v, 1, 0, 0, ipsi, ipsip, q);
+    const uint64_t ni = ninv[2 * p], nip = ninv[2 * p + 1];
+#pragma unroll
+    for (int j = 0; j < E; j++) a[(long)(k + E * j) * N2 + col] = mul_shoup(v[j], ni, nip, q);
+}
+
+template <int LOGE>
+static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
+                      const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st) {
+    constexpr int E = 1 << LOGE, S = E * E, SUB = 256 / E;
+    dim3 g(((1 << logN) / S) / SUB, count);
+    if (!inverse) {
+        k_ntt_cols_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
+        k_ntt_rows_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
+    } else {
+        k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
+        k_ntt_cols_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, ninv, logN);
+    }
+}
+
+void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
+                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st) {
+    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st);
+    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st);
+}

@@ -59,3 +59,8 @@ __global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qm
 __global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
                               Scal pm, int nl, int dlo, int dhi, LimbMap map, const ModC *mods, int logN);
 __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter);
+
+// register-blocked NTT of `count` limbs (N = 2^12: logE = 3, N = 2^16: logE = 4); launches
+// the column and row passes on stream st
+void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
+                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st);
