@@ -10,8 +10,7 @@
  *
  *   y_c   = P_exp(u_c)                                     (exp(x/2^k))
  *   for j = 1..k:
- *     main bootstrapping of every y_c if level(y) < bts_min + 1, or if j < k and
- *       level(y) - 2 < bts_min + 1
+ *     (fallback: bootstrapping of every y_c if level(y) < bts_min + 1)
  *     S    = Relin(sum_c y_c (x) y_c), rescaled           (Step 1 of Alg. 3, one key switch)
  *     S    = RotSum(S, L, log2(n/m))                      (Steps 3-5)
  *     if level(S) - depth_j - 1 >= bts_min: v = gain_s S by scale bookkeeping
@@ -19,9 +18,12 @@
  *     lam  = P_j(u), u = (2v - a_j - b_j)/(b_j - a_j)      (Step 6)
  *     lam  = lam (.) mask, mask = sqrt(gain_s) gain_l on slots [0, L), rescaled   (Step 7)
  *     lam  = RotSum(lam, L, log2(n/m))                    (Steps 8-10)
- *     if level(lam) < level(y): lam = Bootstrap(lam, 1)
+ *     if level(lam) < level(y) (and, in the last round, fewer than 2 levels remain):
+ *         lam = Bootstrap(lam, 1)
  *     lam carries lam_j gain_l; its scale is multiplied by gain_l (bookkeeping)
- *     z_c  = lam * y_c ; y_c = z_c * z_c                  (normalize, square)
+ *     z_c  = lam * y_c                                     (normalize)
+ *     if another round follows and z_c^2 would sit below bts_min + 1: z_c = Bootstrap(z_c)
+ *     y_c  = z_c * z_c                                     (square)
  *   return y
  *
  * Scales.  A Chebyshev evaluation needs its input at the scale of the prime at its level,
@@ -31,7 +33,8 @@
  *   y entering round j must have  sqrt(a'_j q_{l-1} q_l)   (l its level, a'_j =
  *     2 gain_s / (b_j - a_j)) when S_j is not bootstrapped, else Delta;
  *   lam must have (sqrt(T q_{lz - 1}) q_{lz}) / scale(y), lz = min(level(lam), level(y)),
- *     T the target of the next y;
+ *     T the target of the next y, or (Delta q_{lz}) / scale(y) when z is bootstrapped, whose
+ *     output scale is then sqrt(T q_{user_top});
  *   a bootstrapped S gets output scale (2/(b_j - a_j)) q_{user_top};
  *   inputs of bootstrapping are kept near Delta. */
 #include <math.h>
@@ -78,8 +81,16 @@ static int bts(orc_ctx *c, const orc_plan *p, const orc_bts *b, const orc_ct *x,
     return rc;
 }
 
+/* fallback: y cannot feed S = sum y^2 into a bootstrappable level */
 static int main_bts(const orc_plan *p, int j, int ly) {
-    return p->use_bts && (ly < p->bts_min + 1 || (j < p->k - 1 && ly - 2 < p->bts_min + 1));
+    (void)j;
+    return p->use_bts && ly < p->bts_min + 1;
+}
+
+/* z = lam y is computed at product level lz (z at lz - 1); it is bootstrapped when another round
+ * follows and y = z^2 (level lz - 2) would be too low for the next round's S */
+static int z_bts(const orc_plan *p, int j, int lz) {
+    return p->use_bts && j < p->k - 1 && lz - 2 < p->bts_min + 1;
 }
 
 static int s_bts(const orc_plan *p, int j, int ly) {
@@ -165,12 +176,20 @@ int softmax(orc_ctx *c, const orc_plan *p, const orc_bts *b, orc_ct *cts, int m)
         ct_free(&v);
         dbg(c, "lam", j, &lam);
         /* where lambda will meet y, and the scale it must have there */
-        int lam_bts = p->use_bts && lp - 1 < ly;
+        /* lambda is bootstrapped when it ends below y, except in the last round when two
+         * levels remain for z = lam y and y = z^2 */
+        int lam_bts = p->use_bts && lp - 1 < ly && !(j == p->k - 1 && lp - 1 >= 2);
         int llam = lam_bts ? ut : lp - 1;
         int lz = llam < ly ? llam : ly;
-        double tgt = y_target(c, p, j + 1, lz - 2);
-        double sz_ = sqrt(tgt * qd(c, lz - 1));
-        double slam = (sz_ * qd(c, lz)) / cts[0].scale;
+        int zb = z_bts(p, j, lz);
+        double slam;
+        if (zb) {
+            slam = (p->out_scale * qd(c, lz)) / cts[0].scale;
+        } else {
+            double tgt = y_target(c, p, j + 1, lz - 2);
+            double sz_ = sqrt(tgt * qd(c, lz - 1));
+            slam = (sz_ * qd(c, lz)) / cts[0].scale;
+        }
         /* mask */
         cplx *mk = calloc(n0, sizeof(cplx));
         double mval = sqrt(p->gain_s[j]) * p->gain_l[j];
@@ -192,9 +211,18 @@ int softmax(orc_ctx *c, const orc_plan *p, const orc_bts *b, orc_ct *cts, int m)
         }
         lam.scale = lam.scale * p->gain_l[j];
         dbg(c, "lam-fin", j, &lam);
+        double soz = zb ? sqrt(y_target(c, p, j + 1, ut - 1) * qd(c, ut)) : 0.0;
         for (int i = 0; i < m; i++) {
             orc_ct zc, yc;
             if (hmult(c, &lam, &cts[i], &zc)) return -1;
+            if (zb) {
+                /* z = lam y has its maximum in [n^{-1/2}, 1] (Sec. 3.2): bootstrapping it
+                 * instead of y keeps the relative error small for flat distributions */
+                orc_ct zz;
+                if (bts(c, p, b, &zc, 1.0, soz, &zz)) return -1;
+                ct_free(&zc);
+                zc = zz;
+            }
             if (hmult(c, &zc, &zc, &yc)) return -1;
             ct_free(&zc);
             ct_free(&cts[i]);

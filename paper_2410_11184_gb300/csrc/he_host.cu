@@ -370,8 +370,22 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
                                                       (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
                                                       c->d_cv + c->cv_off[L - 1][j], c->logN);
         LAUNCH_CHECK();
+        // the digit's own limbs are the input limbs: copy their NTT form instead of
+        // transforming the converted (identical) coefficients again
+        CK(cudaMemcpy2DAsync(dig.get() + (long)j * nl * c->N + (long)lo * c->N, (size_t)nd * nl * c->N * 8,
+                             x + (long)lo * c->N, (size_t)sx * 8, (size_t)ds * c->N * 8, nct,
+                             cudaMemcpyDeviceToDevice, c->st));
+        // forward NTT of the limbs outside the digit: [0, lo) and [lo + ds, L + alpha)
+        const int ranges[2][2] = {{0, lo}, {lo + ds, nl}};
+        for (const auto &r : ranges) {
+            int a = r[0], b = r[1];
+            if (b <= a) continue;
+            LimbMap sub;
+            sub.nper = b - a;
+            for (int t = a; t < b; t++) sub.prime[t - a] = em.prime[t];
+            ntt(c, dig.get() + (long)j * nl * c->N + (long)a * c->N, nct * (b - a), sub, (long)nd * nl * c->N, false);
+        }
     }
-    ntt(c, dig.get(), nct * nd * nl, em, (long)nl * c->N, false);
     return dig;
 }
 
@@ -1023,8 +1037,17 @@ static DCt bts_boosted(he_ctx *c, const Plan &p, const DCt &x, double gain, doub
     return y;
 }
 
+// fallback: y too low to feed S = sum y^2 into a bootstrappable level
 static bool main_bts(he_ctx *c, const Plan &p, int j, int ly) {
-    return c->bootstrap && (ly < c->bts_min + 1 || (j < p.k - 1 && ly - 2 < c->bts_min + 1));
+    (void)p;
+    (void)j;
+    return c->bootstrap && ly < c->bts_min + 1;
+}
+// z = lam y at product level lz is bootstrapped when another round follows and y = z^2 would
+// sit below bts_min + 1; z's maximum lies in [n^{-1/2}, 1] (Sec. 3.2), so its bootstrapping
+// error is small relative to the values, unlike y's for flat distributions
+static bool z_bts(he_ctx *c, const Plan &p, int j, int lz) {
+    return c->bootstrap && j < p.k - 1 && lz - 2 < c->bts_min + 1;
 }
 static bool s_bts(he_ctx *c, const Plan &p, int j, int ly) {
     return c->bootstrap && ((ly - 1) - ilog2c(p.inv_deg[j] + 1) - 1 < c->bts_min);
@@ -1124,12 +1147,20 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         int lp = v.level - dj;
         DCt lam = poly_eval(c, v, p.inv_c[j], lp, delta);
         dbg_dump(c, "lam", j, lam);
-        bool lam_bts = c->bootstrap && lp - 1 < ly;
+        // lambda is bootstrapped when it ends below y, except in the last round when two
+        // levels remain for z = lam y and y = z^2
+        bool lam_bts = c->bootstrap && lp - 1 < ly && !(j == p.k - 1 && lp - 1 >= 2);
         int llam = lam_bts ? ut : lp - 1;
         int lz = std::min(llam, ly);
-        double tgt = y_target(c, p, j + 1, lz - 2);
-        double sz = sqrt(tgt * qd(c, lz - 1));
-        double slam = (sz * qd(c, lz)) / ys[0].scale;
+        bool zb = z_bts(c, p, j, lz);
+        double slam;
+        if (zb) {
+            slam = (delta * qd(c, lz)) / ys[0].scale;
+        } else {
+            double tgt = y_target(c, p, j + 1, lz - 2);
+            double sz = sqrt(tgt * qd(c, lz - 1));
+            slam = (sz * qd(c, lz)) / ys[0].scale;
+        }
         std::vector<double2> mk(n0, make_double2(0.0, 0.0));
         double mval = sqrt(p.gs[j]) * p.gl[j];
         for (int i = 0; i < stride; i++) mk[i].x = mval;
@@ -1142,8 +1173,10 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         if (lam_bts) lam = bts_boosted(c, p, lam, 1.0, slam / p.gl[j]);
         lam.scale = lam.scale * p.gl[j];
         dbg_dump(c, "lamf", j, lam);
+        double soz = zb ? sqrt(y_target(c, p, j + 1, ut - 1) * qd(c, ut)) : 0.0;
         for (auto &y : ys) {
             DCt z = hmult(c, lam, y);
+            if (zb) z = bts_boosted(c, p, z, 1.0, soz);
             y = hmult(c, z, z);
         }
         dbg_dump(c, "y", j, ys[0]);
