@@ -16,11 +16,10 @@
  *     if level(S) - depth_j - 1 >= bts_min: v = gain_s S by scale bookkeeping
  *     else                                 : v = Bootstrap(S, gain_s)
  *     lam  = P_j(u), u = (2v - a_j - b_j)/(b_j - a_j)      (Step 6)
- *     lam  = lam (.) mask, mask = sqrt(gain_s) gain_l on slots [0, L), rescaled   (Step 7)
+ *     if lam would end below level(y) (and, in the last round, fewer than 2 levels remain):
+ *         lam = Bootstrap(lam, gain_l)                     (gain removed by bookkeeping)
+ *     lam  = lam (.) mask, mask = sqrt(gain_s) on slots [0, L), rescaled   (Step 7)
  *     lam  = RotSum(lam, L, log2(n/m))                    (Steps 8-10)
- *     if level(lam) < level(y) (and, in the last round, fewer than 2 levels remain):
- *         lam = Bootstrap(lam, 1)
- *     lam carries lam_j gain_l; its scale is multiplied by gain_l (bookkeeping)
  *     z_c  = lam * y_c                                     (normalize)
  *     if another round follows and z_c^2 would sit below bts_min + 1: z_c = Bootstrap(z_c)
  *     y_c  = z_c * z_c                                     (square)
@@ -176,10 +175,12 @@ int softmax(orc_ctx *c, const orc_plan *p, const orc_bts *b, orc_ct *cts, int m)
         ct_free(&v);
         dbg(c, "lam", j, &lam);
         /* where lambda will meet y, and the scale it must have there */
-        /* lambda is bootstrapped when it ends below y, except in the last round when two
-         * levels remain for z = lam y and y = z^2 */
+        /* lambda is bootstrapped right after the polynomial when it would end below y (except
+         * in the last round if two levels remain for z = lam y and y = z^2); masking and
+         * replication follow, so every slot of a Softmax carries the same value and the same
+         * error (Alg. 3, Steps 7-10), which the next normalisation removes */
         int lam_bts = p->use_bts && lp - 1 < ly && !(j == p->k - 1 && lp - 1 >= 2);
-        int llam = lam_bts ? ut : lp - 1;
+        int llam = lam_bts ? ut - 1 : lp - 1;
         int lz = llam < ly ? llam : ly;
         int zb = z_bts(p, j, lz);
         double slam;
@@ -190,26 +191,29 @@ int softmax(orc_ctx *c, const orc_plan *p, const orc_bts *b, orc_ct *cts, int m)
             double sz_ = sqrt(tgt * qd(c, lz - 1));
             slam = (sz_ * qd(c, lz)) / cts[0].scale;
         }
+        int lm = lp;
+        if (lam_bts) {
+            orc_ct lb;
+            if (bts(c, p, b, &lam, p->gain_l[j], p->out_scale, &lb)) return -1;
+            ct_free(&lam);
+            lam = lb;
+            lm = lam.level;
+        }
         /* mask */
         cplx *mk = calloc(n0, sizeof(cplx));
-        double mval = sqrt(p->gain_s[j]) * p->gain_l[j];
+        double mval = sqrt(p->gain_s[j]);
         for (int i = 0; i < stride; i++) mk[i].re = mval;
-        double sm = lam_bts ? qd(c, lp) : ((slam * qd(c, lp)) / lam.scale) / p->gain_l[j];
-        uint64_t *pt = malloc(sizeof(uint64_t) * (size_t)(lp + 1) * c->n);
-        encode(c, mk, sm, lp, pt);
-        ct_mul_plain(c, &lam, pt, lp);
+        double sm = (slam * qd(c, lm)) / lam.scale;
+        if (lam_bts) sm = sm / p->gain_l[j];
+        uint64_t *pt = malloc(sizeof(uint64_t) * (size_t)(lm + 1) * c->n);
+        encode(c, mk, sm, lm, pt);
+        ct_mul_plain(c, &lam, pt, lm);
         lam.scale = lam.scale * sm;
         free(pt);
         free(mk);
         if (rescale(c, &lam)) return -1;
         if (rotsum(c, &lam, stride, nrot)) return -1;
-        if (lam_bts) {
-            orc_ct lb;
-            if (bts(c, p, b, &lam, 1.0, slam / p->gain_l[j], &lb)) return -1;
-            ct_free(&lam);
-            lam = lb;
-        }
-        lam.scale = lam.scale * p->gain_l[j];
+        if (lam_bts) lam.scale = lam.scale * p->gain_l[j];
         dbg(c, "lam-fin", j, &lam);
         double soz = zb ? sqrt(y_target(c, p, j + 1, ut - 1) * qd(c, ut)) : 0.0;
         for (int i = 0; i < m; i++) {

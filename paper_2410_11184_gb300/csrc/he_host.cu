@@ -1147,10 +1147,11 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         int lp = v.level - dj;
         DCt lam = poly_eval(c, v, p.inv_c[j], lp, delta);
         dbg_dump(c, "lam", j, lam);
-        // lambda is bootstrapped when it ends below y, except in the last round when two
-        // levels remain for z = lam y and y = z^2
+        // lambda is bootstrapped right after the polynomial when it would end below y
+        // (except in the last round if two levels remain); masking and replication follow,
+        // so every slot of a Softmax carries the same value and error (Alg. 3, Steps 7-10)
         bool lam_bts = c->bootstrap && lp - 1 < ly && !(j == p.k - 1 && lp - 1 >= 2);
-        int llam = lam_bts ? ut : lp - 1;
+        int llam = lam_bts ? ut - 1 : lp - 1;
         int lz = std::min(llam, ly);
         bool zb = z_bts(c, p, j, lz);
         double slam;
@@ -1161,17 +1162,22 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
             double sz = sqrt(tgt * qd(c, lz - 1));
             slam = (sz * qd(c, lz)) / ys[0].scale;
         }
+        int lm = lp;
+        if (lam_bts) {
+            lam = bts_boosted(c, p, lam, p.gl[j], delta);
+            lm = lam.level;
+        }
         std::vector<double2> mk(n0, make_double2(0.0, 0.0));
-        double mval = sqrt(p.gs[j]) * p.gl[j];
+        double mval = sqrt(p.gs[j]);
         for (int i = 0; i < stride; i++) mk[i].x = mval;
-        double smk = lam_bts ? qd(c, lp) : ((slam * qd(c, lp)) / lam.scale) / p.gl[j];
-        DPtr pt = encode(c, mk, smk, lp);
+        double smk = (slam * qd(c, lm)) / lam.scale;
+        if (lam_bts) smk = smk / p.gl[j];
+        DPtr pt = encode(c, mk, smk, lm);
         ct_mul_plain(c, lam, pt.get());
         lam.scale = lam.scale * smk;
         lam = rescale(c, lam);
         lam = rotsum(c, lam, stride, nrot);
-        if (lam_bts) lam = bts_boosted(c, p, lam, 1.0, slam / p.gl[j]);
-        lam.scale = lam.scale * p.gl[j];
+        if (lam_bts) lam.scale = lam.scale * p.gl[j];
         dbg_dump(c, "lamf", j, lam);
         double soz = zb ? sqrt(y_target(c, p, j + 1, ut - 1) * qd(c, ut)) : 0.0;
         for (auto &y : ys) {

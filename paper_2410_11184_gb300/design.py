@@ -262,13 +262,15 @@ def design_softmax(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
         c, eps = weighted_minimax(lambda v: v ** -0.5, lambda v: v ** 0.5, a, b, d)
         alpha = 2.0 * eps + eps * eps
         gain_s = 1.0 / n if j == 1 else 1.0
+        uu = np.linspace(-1, 1, 20001)
+        pmax = float(np.max(np.abs(cheb_vander(uu, d) @ c)))
         iters.append({
             "deg": d, "a": a, "b": b, "coeffs": hexlist(c), "eps": eps, "alpha": alpha,
             # v = gain_s * S is the polynomial input; lambda = P(v) * sqrt(gain_s).
             "gain_s": gain_s,
-            # the mask carries sqrt(gain_s) * gain_l so that lambda * gain_l <= ~1 at
-            # bootstrapping; the factor gain_l is removed by scale bookkeeping.
-            "gain_l": 1.0 / math.sqrt(n),
+            # bootstrapping input gain of P(v) (1 / max |P| on [a, b]), removed afterwards by
+            # scale bookkeeping
+            "gain_l": 1.0 / pmax,
         })
     return {
         "name": name, "chain": chain_name, "n": n, "M": M, "k": k, "A": A,
