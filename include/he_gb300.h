@@ -138,7 +138,8 @@ int he_bootstrap(he_ctx *ctx, const he_ct *a, double gain, double out_scale, he_
 /* ModRaise of a level-0 batch to level top */
 int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
 
-/* operation counters since creation: [key switches, rotations, hmults, rescales, bootstraps] */
+/* operation counters since creation: [ciphertext key switches (a batched key switch over n
+ * ciphertexts counts n), rotation calls, hmult calls, rescale calls, bootstrapping calls] */
 int he_counters(const he_ctx *ctx, long *out5);
 /* number of kernel launches this context has issued since creation */
 long he_launch_count(const he_ctx *ctx);

@@ -409,7 +409,7 @@ static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, con
     k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc.get(), conv.get(), 2 * nct, L, al, qmap(L),
                                                         c->d_mods, c->d_pinv, c->logN, accumulate ? 1 : 0);
     LAUNCH_CHECK();
-    c->cnt[0]++;
+    c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
 }
 
 static const uint64_t *get_key(he_ctx *c, int galois) {

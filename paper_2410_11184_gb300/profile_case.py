@@ -1,0 +1,40 @@
+"""Small fixed workloads for Nsight Compute captures (profiles/ summaries name the command).
+
+  python -m paper_2410_11184_gb300.profile_case softmax   # one N=2^16 Softmax of dim 256 (1 ciphertext)
+  python -m paper_2410_11184_gb300.profile_case keyswitch # 4 HMults at level 12, 64 ciphertexts
+"""
+import sys
+
+import numpy as np
+import torch
+
+from paper_2410_11184_gb300 import he, workloads
+
+
+def main(which):
+    chains, plans, evalmod = he.load_params()
+    ch, pl, em = chains["fgb16"], plans["n256_M128"], evalmod["fgb16"]
+    g = he.Context(ch, em)
+    g.keygen(5)
+    if which == "softmax":
+        g.keygen_softmax(256, 1)
+        x = workloads.attention_logits(128, 256, 1)
+        cts = g.encrypt(x, 256, 1, pl["M"], 3)
+        g.softmax(cts, pl)
+    else:
+        m = 64
+        top = ch["user_top_level"]
+        rng = np.random.default_rng(0)
+        q = [int(v) for v in ch["q"]]
+        d = np.zeros((m, 2, top + 1, g.n), dtype=np.uint64)
+        for t in range(top + 1):
+            d[:, :, t] = rng.integers(0, q[t], (m, 2, g.n), dtype=np.uint64)
+        a = g.from_coeff(d, top, 2.0 ** 42)
+        for _ in range(4):
+            g.hmult(a, a)
+    torch.cuda.synchronize()
+    print("done", which, "launches", g.launch_count())
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "softmax")
