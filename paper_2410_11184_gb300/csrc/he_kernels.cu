@@ -638,12 +638,15 @@ __device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase
         const int m = m0 << p;               // stage parameter
 #pragma unroll
         for (int b = 0; b < E / 2; b++) {
+            // Harvey's lazy butterfly: values stay in [0, 4q); q < 2^61 keeps 4q < 2^63
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (m / m0) * gmul + grp;
             const uint64_t w = psi[idx], wp = psip[idx];
-            uint64_t u = v[jj], x = mul_shoup(v[jj + t], w, wp, q);
-            v[jj] = add_mod(u, x, q);
-            v[jj + t] = sub_mod(u, x, q);
+            uint64_t u = v[jj];
+            if (u >= 2 * q) u -= 2 * q;
+            const uint64_t x = v[jj + t] * w - he_mulhi(v[jj + t], wp) * q;   // in [0, 2q)
+            v[jj] = u + x;
+            v[jj + t] = u - x + 2 * q;
         }
     }
 }
@@ -659,12 +662,16 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
         const int m = m0 << p;
 #pragma unroll
         for (int b = 0; b < E / 2; b++) {
+            // lazy Gentleman-Sande butterfly: inputs and outputs in [0, 2q)
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (m / m0) * gmul + grp;
             const uint64_t w = ipsi[idx], wp = ipsip[idx];
-            uint64_t u = v[jj], x = v[jj + t];
-            v[jj] = add_mod(u, x, q);
-            v[jj + t] = mul_shoup(sub_mod(u, x, q), w, wp, q);
+            const uint64_t u = v[jj], x = v[jj + t];
+            uint64_t s = u + x;
+            if (s >= 2 * q) s -= 2 * q;
+            const uint64_t d = u - x + 2 * q;
+            v[jj] = s;
+            v[jj + t] = d * w - he_mulhi(d, wp) * q;
         }
     }
 }
@@ -724,10 +731,16 @@ __global__ void __launch_bounds__(256) k_ntt_rows_fwd_rb(uint64_t *base, int npe
     for (int j = 0; j < E; j++) v[j] = sm[rr * S + E * k + j];
     // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
     ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, psip, q);
-    // back to the k + E j layout through shared memory so the store is coalesced
+    // back to the k + E j layout through shared memory so the store is coalesced; the lazy
+    // butterflies left values in [0, 4q): reduce to [0, q)
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; j++) sm[rr * S + E * k + j] = v[j];
+    for (int j = 0; j < E; j++) {
+        uint64_t r = v[j];
+        if (r >= 2 * q) r -= 2 * q;
+        if (r >= q) r -= q;
+        sm[rr * S + E * k + j] = r;
+    }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * S + k + E * j];

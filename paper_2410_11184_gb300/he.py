@@ -260,7 +260,7 @@ class Context:
         return a
 
     def rescale(self, a):
-        return self._unary(lib().he_rescale, a)
+        return self._unary(lib().he_rescale, a, level=a.level - 1)
 
     def hmult(self, a, b):
         out = self.alloc(min(a.level, b.level), max(a.n_ct, b.n_ct))

@@ -14,6 +14,9 @@ from paper_2410_11184_gb300 import he, workloads
 def main(which):
     chains, plans, evalmod = he.load_params()
     ch, pl, em = chains["fgb16"], plans["n256_M128"], evalmod["fgb16"]
+    if which != "softmax":
+        ch = dict(ch, bootstrap=0)  # relinearisation key only: a few GB on the device
+        em = None
     g = he.Context(ch, em)
     g.keygen(5)
     if which == "softmax":
