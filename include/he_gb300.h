@@ -120,6 +120,20 @@ int he_encode(he_ctx *ctx, const double *slots, double scale, int level, uint64_
 int he_add(he_ctx *ctx, he_ct *a, const he_ct *b);                 /* a += b */
 int he_mul_plain(he_ctx *ctx, he_ct *a, const uint64_t *pt);       /* a *= pt (no rescale) */
 int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out);           /* out at level-1 */
+/* Rescale that allocates no device memory (no counterpart in the paper; an interface for
+ * callers that cannot allocate once they are running: a server that reserved its whole HBM
+ * budget at start-up and admits work against it, or a host program whose memory pool is
+ * fixed and must not grow on the request path).  The caller passes the input batch a and an
+ * output buffer out->data of n_ct * 2 * level * N words that must not alias a->data; level,
+ * scale and n_ct of *out are written.  Results equal he_rescale's bit for bit.
+ * Scratch: a fixed device array of 2^21 words (16 MiB) compiled into the library, held by
+ * every device that loads it until the process exits; its device address is looked up once
+ * per context, at he_context_create, with the context's device current.  Inputs needing more
+ * than 2 n_ct (level+1) N = 2^21 words are rejected with HE_EINVAL before any launch.  Every
+ * call shares that one array and leaves its contents behind: calls whose executions overlap
+ * on the GPU (several streams, or several contexts on one device) race on it, so serialise
+ * them.  Errors as he_rescale. */
+int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out);
 /* tensor + relinearise + rescale (Mult of Sec. 2.2) */
 int he_hmult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out);
 /* relinearise a degree-2 batch d [n_ct][3][level+1][N] into out (no rescale) */

@@ -98,6 +98,7 @@ struct he_ctx {
     std::map<int, uint64_t *> keys;
     int ndig_top = 0;
     std::map<std::string, LtLevel> lt_cache;
+    uint64_t *noalloc_scratch = nullptr;   // device address of g_rescale_scratch on this device
     cudaStream_t st = nullptr;
     std::string err;
     long cnt[5] = {0, 0, 0, 0, 0};
@@ -349,6 +350,31 @@ static DCt rescale(he_ctx *c, const DCt &a) {
     LAUNCH_CHECK();
     c->cnt[3]++;
     return y;
+}
+
+// ------------------------------------------------------------------------- rescale, no allocation
+// Scratch of he_rescale_noalloc: a file-scope device array, so that the call allocates nothing.
+// It holds the centred last limbs and their spread over the remaining limbs:
+// 2 n_ct (level + 1) N words at most (2 Mi words = 16 MiB).  Every device that loads this
+// library reserves it until the process exits.
+#define HE_NOALLOC_SCRATCH_WORDS (2u << 20)
+static __device__ __align__(256) uint64_t g_rescale_scratch[HE_NOALLOC_SCRATCH_WORDS];
+
+// the same steps as rescale(), with the scratch above and the caller's output buffer
+static void rescale_noalloc(he_ctx *c, const DCt &a, uint64_t *out) {
+    int l = a.level, L = l + 1, npoly = 2 * a.nct;
+    uint64_t *last = c->noalloc_scratch, *tmp = last + (size_t)npoly * c->N;
+    CK(cudaMemcpy2DAsync(last, (size_t)c->N * 8, a.d + (long)l * c->N, (size_t)L * c->N * 8, (size_t)c->N * 8, npoly,
+                         cudaMemcpyDeviceToDevice, c->st));
+    ntt(c, last, npoly, single(l), c->N, true);
+    long tot = (long)npoly * l << c->logN;
+    k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp, last, npoly, l, qmap(l), c->d_mods, c->mods[l], c->logN);
+    LAUNCH_CHECK();
+    ntt(c, tmp, npoly * l, qmap(l), (long)l * c->N, false);
+    k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, a.d, tmp, npoly, L, qmap(l), c->d_mods,
+                                                        c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
+    LAUNCH_CHECK();
+    c->cnt[3]++;
 }
 
 // ------------------------------------------------------------------------- key switching
@@ -1426,6 +1452,9 @@ int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out) {
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         c->max_grid = nsm * 16;
         build_tables(c);
+        // host code must not use the array's name as a device address: look it up once for
+        // this device (the current one) and keep it with the context
+        CK(cudaGetSymbolAddress((void **)&c->noalloc_scratch, g_rescale_scratch));
     } catch (const HeErr &e) {
         fprintf(stderr, "he_context_create: %s\n", e.msg.c_str());
         delete c;
@@ -1671,6 +1700,32 @@ int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out) {
     if (!ctx || !a || !out) return HE_EINVAL;
     API_BEGIN
     put_out(ctx, rescale(ctx, ct_view(a)), out);
+    API_END
+}
+
+int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out) {
+    if (!ctx || !a || !out || !a->data || !out->data || a->n_ct < 1) return HE_EINVAL;
+    if (a->level < 1 || a->level >= ctx->nq) {
+        ctx->err = "he_rescale_noalloc: level must be in [1, n_q)";
+        return HE_ELEVEL;
+    }
+    if (out->data == a->data) {
+        ctx->err = "he_rescale_noalloc: output must not alias the input";
+        return HE_EINVAL;
+    }
+    size_t need = (size_t)2 * a->n_ct * (a->level + 1) * ctx->N;
+    if (need > HE_NOALLOC_SCRATCH_WORDS) {
+        char b[160];
+        snprintf(b, sizeof b, "he_rescale_noalloc: needs %zu scratch words, the fixed scratch holds %u "
+                 "(2 n_ct (level+1) N <= %u)", need, HE_NOALLOC_SCRATCH_WORDS, HE_NOALLOC_SCRATCH_WORDS);
+        ctx->err = b;
+        return HE_EINVAL;
+    }
+    API_BEGIN
+    rescale_noalloc(ctx, ct_view(a), out->data);
+    out->level = a->level - 1;
+    out->scale = a->scale / (double)ctx->mods[a->level];
+    out->n_ct = a->n_ct;
     API_END
 }
 
