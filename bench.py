@@ -181,6 +181,7 @@ def main():
     ap.add_argument("--profile-kernel", default="ntt")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-breakdown", action="store_true")
     args = ap.parse_args()
     wl = workload(args.workload)
     if args.impl == "reference":
@@ -261,6 +262,13 @@ def main():
             t[1].record(stream)
             barrier()
             plain_ms = t[0].elapsed_time(t[1])
+        # per-family breakdown of one more (untimed) step: CUDA events around every launch
+        breakdown = None
+        if not args.no_breakdown:
+            g.profile_kernel("all")
+            step(True)
+            breakdown = {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in g.profile_breakdown().items()}
+            g.profile_kernel("")
         # e2e: pinned host ciphertexts in, results out, through he_softmax
         host_in = torch.empty_like(src.tensor, device="cpu").pin_memory()
         host_in.copy_(src.tensor)
@@ -312,6 +320,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
+        "breakdown_one_step": breakdown,
         "e2e": {"value": e2e_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": src.tensor.numel() * 8,
                 "d2h_bytes_per_step": out_words * 8},
     }

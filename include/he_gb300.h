@@ -162,6 +162,11 @@ long he_launch_count(const he_ctx *ctx);
  * summed device time, the launch count and the algorithmic bytes of those launches, and resets */
 int he_profile_kernel(he_ctx *ctx, const char *name);
 int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes);
+/* with he_profile_kernel(ctx, "all"): every launch and device copy is timed; this call
+ * synchronises and writes one text line "family launches total_ms" per kernel family (ntt,
+ * modup, ks_inner, moddown, tensor, rescale, lintrans, elementwise, automorph, modraise, encode, decode,
+ * keygen, copy) into buf (len bytes, NUL-terminated), then resets.  HE_EINVAL if buf is too small. */
+int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len);
 /* bounded device wait self test: a kernel polls a flag nobody sets for at most max_iter polls
  * and returns HE_ETIMEOUT; the context stays usable. */
 int he_selftest_bounded_wait(he_ctx *ctx, long max_iter);

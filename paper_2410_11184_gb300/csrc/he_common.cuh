@@ -4,6 +4,10 @@
 //  - mul_mod   : Barrett reduction of the 128-bit product with mu = floor(2^(s+63) / q),
 //                s = bitlen(q): the quotient estimate is at most 2 below the true one.
 //  - mul_shoup : Shoup's multiplication by a fixed w with w' = floor(w 2^64 / q).
+//  - mac_wide / redc : sums of products kept as 128-bit integers and reduced once by
+//                Montgomery's REDC (R = 2^64): redc(T) = T R^{-1} mod q for T < q 2^64, so
+//                a sum of products whose constant factors are stored as c R mod q comes out
+//                as the exact sum mod q.
 // Limb maps describe a batch of polynomials stored as [poly][limb][N]: limb l of the batch
 // uses modulus index prime[l % nper].
 #pragma once
@@ -16,6 +20,7 @@
 struct ModC {
     uint64_t q;
     uint64_t mu;   // floor(2^(s+63) / q)
+    uint64_t qinv; // -q^{-1} mod 2^64
     int s;         // bit length of q
     int pad;
 };
@@ -55,6 +60,20 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const ModC &
     if (r >= m.q) r -= m.q;
     if (r >= m.q) r -= m.q;
     return r;
+}
+
+// (hi:lo) += a b as one 128-bit integer
+__device__ __forceinline__ void mac_wide(uint64_t &lo, uint64_t &hi, uint64_t a, uint64_t b) {
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
+}
+
+// Montgomery reduction of T = (hi:lo) < q 2^64: returns T 2^{-64} mod q in [0, q).
+// u = lo (-q^{-1}) makes T + u q divisible by 2^64; its low word is 0 and carries out
+// exactly when lo != 0; the quotient is below 2q.
+__device__ __forceinline__ uint64_t redc(uint64_t lo, uint64_t hi, const ModC &m) {
+    uint64_t u = lo * m.qinv;
+    uint64_t t = hi + he_mulhi(u, m.q) + (lo != 0);
+    return t >= m.q ? t - m.q : t;
 }
 
 // x (any uint64) mod q

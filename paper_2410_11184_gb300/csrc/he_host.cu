@@ -37,6 +37,8 @@ static uint64_t h_pow(uint64_t a, uint64_t e, uint64_t q) {
 }
 static uint64_t h_inv(uint64_t a, uint64_t q) { return h_pow(a % q, q - 2, q); }
 static uint64_t h_shoup(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
+// Montgomery form w 2^64 mod q of the constant factors that redc() sums over
+static uint64_t h_mont(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) % q); }
 static uint64_t h_red128(i128 x, uint64_t q) {
     i128 r = x % (i128)q;
     if (r < 0) r += q;
@@ -105,26 +107,32 @@ struct he_ctx {
     long launches = 0;
     int max_grid = 152 * 16;
     // live kernel timing: CUDA events around the launches of one kernel family
-    std::string prof_name;
+    std::string prof_name;   // a family name, or "all"
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    std::vector<const char *> prof_fam;   // family of each recorded launch
     size_t prof_used = 0;
     double prof_bytes = 0;
 };
 
-// Records events around one launch of kernel family `name` when it is the profiled one.
+// Records events around one launch (or one copy) of kernel family `name` when that family,
+// or "all", is the profiled one.  Every scope brackets exactly one launch, so the families'
+// times add up to the stream's busy time.
 struct ProfScope {
     he_ctx *c;
     bool on;
     size_t slot;
-    ProfScope(he_ctx *c_, const char *name, double bytes) : c(c_), on(!c_->prof_name.empty() && c_->prof_name == name) {
+    ProfScope(he_ctx *c_, const char *name, double bytes)
+        : c(c_), on(!c_->prof_name.empty() && (c_->prof_name == name || c_->prof_name == "all")) {
         if (!on) return;
         if (c->prof_used == c->prof_ev.size()) {
             cudaEvent_t a, b;
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             c->prof_ev.push_back({a, b});
+            c->prof_fam.push_back(nullptr);
         }
         slot = c->prof_used++;
+        c->prof_fam[slot] = name;
         c->prof_bytes += bytes;
         cudaEventRecord(c->prof_ev[slot].first, c->st);
     }
@@ -261,7 +269,10 @@ static DCt ct_view(const he_ct *h) {
 
 static DCt ct_copy(he_ctx *c, const DCt &a) {
     DCt y = ct_new(c, a.level, a.nct, a.scale);
-    CK(cudaMemcpyAsync(y.d, a.d, (size_t)a.nct * a.cs(c) * 8, cudaMemcpyDeviceToDevice, c->st));
+    {
+        ProfScope ps_(c, "copy", 0);
+        CK(cudaMemcpyAsync(y.d, a.d, (size_t)a.nct * a.cs(c) * 8, cudaMemcpyDeviceToDevice, c->st));
+    }
     return y;
 }
 
@@ -270,8 +281,11 @@ static DCt ct_drop(he_ctx *c, const DCt &a, int level) {
     REQUIRE(level <= a.level && level >= 0, HE_ELEVEL, "drop: level");
     if (level == a.level) return ct_copy(c, a);
     DCt y = ct_new(c, level, a.nct, a.scale);
-    CK(cudaMemcpy2DAsync(y.d, (size_t)y.ps(c) * 8, a.d, (size_t)a.ps(c) * 8, (size_t)y.ps(c) * 8, 2 * a.nct,
-                         cudaMemcpyDeviceToDevice, c->st));
+    {
+        ProfScope ps_(c, "copy", 0);
+        CK(cudaMemcpy2DAsync(y.d, (size_t)y.ps(c) * 8, a.d, (size_t)a.ps(c) * 8, (size_t)y.ps(c) * 8, 2 * a.nct,
+                             cudaMemcpyDeviceToDevice, c->st));
+    }
     return y;
 }
 
@@ -294,8 +308,11 @@ static void ct_add_inplace(he_ctx *c, DCt &a, const DCt &b, bool sub = false) {
     int count = 2 * a.nct * (a.level + 1);
     LimbMap m = qmap(a.level + 1);
     long total = (long)count << c->logN;
-    k_add<<<grid_for(c, total), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), b.d, b.ps(c), count, a.level + 1, m,
-                                                  c->d_mods, c->logN, sub ? 1 : 0);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_add<<<grid_for(c, total), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), b.d, b.ps(c), count, a.level + 1, m,
+                                                      c->d_mods, c->logN, sub ? 1 : 0);
+    }
     LAUNCH_CHECK();
 }
 
@@ -308,8 +325,11 @@ static Scal scal_of(he_ctx *c, i128 k, int L) {
 static void ct_mul_int(he_ctx *c, DCt &a, i128 k) {
     int L = a.level + 1, count = 2 * a.nct * L;
     Scal s = scal_of(c, k, L);
-    k_mul_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), s, count, L,
-                                                                          qmap(L), c->d_mods, c->logN);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), s, count, L,
+                                                                              qmap(L), c->d_mods, c->logN);
+    }
     LAUNCH_CHECK();
 }
 
@@ -317,15 +337,21 @@ static void ct_mul_int(he_ctx *c, DCt &a, i128 k) {
 static void ct_add_const(he_ctx *c, DCt &a, i128 k) {
     int L = a.level + 1, count = a.nct * L;
     Scal s = scal_of(c, k, L);
-    k_add_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.cs(c), s, count, L, qmap(L),
-                                                                          c->d_mods, c->logN);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_add_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.cs(c), s, count, L, qmap(L),
+                                                                              c->d_mods, c->logN);
+    }
     LAUNCH_CHECK();
 }
 
 static void ct_mul_plain(he_ctx *c, DCt &a, const uint64_t *pt) {
     int L = a.level + 1, count = 2 * a.nct * L;
-    k_mul<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), pt, 0, count, L, qmap(L),
-                                                                   c->d_mods, c->logN, 0);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), pt, 0, count, L, qmap(L),
+                                                                       c->d_mods, c->logN, 0);
+    }
     LAUNCH_CHECK();
 }
 
@@ -335,18 +361,27 @@ static DCt rescale(he_ctx *c, const DCt &a) {
     REQUIRE(l >= 1, HE_ELEVEL, "rescale at level 0");
     int npoly = 2 * a.nct;
     DPtr last = dalloc(c, (size_t)npoly * c->N);
-    CK(cudaMemcpy2DAsync(last.get(), (size_t)c->N * 8, a.d + (long)l * c->N, (size_t)L * c->N * 8, (size_t)c->N * 8,
-                         npoly, cudaMemcpyDeviceToDevice, c->st));
+    {
+        ProfScope ps_(c, "copy", 0);
+        CK(cudaMemcpy2DAsync(last.get(), (size_t)c->N * 8, a.d + (long)l * c->N, (size_t)L * c->N * 8, (size_t)c->N * 8,
+                             npoly, cudaMemcpyDeviceToDevice, c->st));
+    }
     ntt(c, last.get(), npoly, single(l), c->N, true);
     DPtr tmp = dalloc(c, (size_t)npoly * l * c->N);
     long tot = (long)npoly * l << c->logN;
-    k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp.get(), last.get(), npoly, l, qmap(l), c->d_mods,
-                                                           c->mods[l], c->logN);
+    {
+        ProfScope ps_(c, "rescale", 0);
+        k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp.get(), last.get(), npoly, l, qmap(l), c->d_mods,
+                                                               c->mods[l], c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false);
     DCt y = ct_new(c, l - 1, a.nct, a.scale / (double)c->mods[l]);
-    k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, a.d, tmp.get(), npoly, L, qmap(l), c->d_mods,
-                                                        c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
+    {
+        ProfScope ps_(c, "rescale", 0);
+        k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, a.d, tmp.get(), npoly, L, qmap(l), c->d_mods,
+                                                            c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
+    }
     LAUNCH_CHECK();
     c->cnt[3]++;
     return y;
@@ -383,24 +418,32 @@ static void rescale_noalloc(he_ctx *c, const DCt &a, uint64_t *out) {
 static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
     DPtr tmp = dalloc(c, (size_t)nct * L * c->N);
-    CK(cudaMemcpy2DAsync(tmp.get(), (size_t)L * c->N * 8, x, (size_t)sx * 8, (size_t)L * c->N * 8, nct,
-                         cudaMemcpyDeviceToDevice, c->st));
+    {
+        ProfScope ps_(c, "copy", 0);
+        CK(cudaMemcpy2DAsync(tmp.get(), (size_t)L * c->N * 8, x, (size_t)sx * 8, (size_t)L * c->N * 8, nct,
+                             cudaMemcpyDeviceToDevice, c->st));
+    }
     ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true);
     DPtr dig = dalloc(c, (size_t)nct * nd * nl * c->N);
     LimbMap em = extmap(c, L);
     for (int j = 0; j < nd; j++) {
         int lo = j * al, ds = std::min(al, L - lo);
         long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)
-        ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * ds + (double)nct * nl));
-        k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N, tmp.get(),
-                                                      (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
-                                                      c->d_cv + c->cv_off[L - 1][j], c->logN);
+        {
+            ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * ds + (double)nct * nl));
+            k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
+                                                          tmp.get(), (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
+                                                          c->d_cv + c->cv_off[L - 1][j], c->logN);
+        }
         LAUNCH_CHECK();
         // the digit's own limbs are the input limbs: copy their NTT form instead of
         // transforming the converted (identical) coefficients again
-        CK(cudaMemcpy2DAsync(dig.get() + (long)j * nl * c->N + (long)lo * c->N, (size_t)nd * nl * c->N * 8,
-                             x + (long)lo * c->N, (size_t)sx * 8, (size_t)ds * c->N * 8, nct,
-                             cudaMemcpyDeviceToDevice, c->st));
+        {
+            ProfScope ps_(c, "copy", 0);
+            CK(cudaMemcpy2DAsync(dig.get() + (long)j * nl * c->N + (long)lo * c->N, (size_t)nd * nl * c->N * 8,
+                                 x + (long)lo * c->N, (size_t)sx * 8, (size_t)ds * c->N * 8, nct,
+                                 cudaMemcpyDeviceToDevice, c->st));
+        }
         // forward NTT of the limbs outside the digit: [0, lo) and [lo + ds, L + alpha)
         const int ranges[2][2] = {{0, lo}, {lo + ds, nl}};
         for (const auto &r : ranges) {
@@ -421,19 +464,27 @@ static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, con
                       long so, bool accumulate) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
     DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
-    ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl));
-    k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc.get(), dig, nct, nd, L, al, extmap(c, L),
-                                                                    c->d_mods, key, c->nm, c->nq, g, c->logN);
+    {
+        ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl));
+        k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc.get(), dig, nct, nd, L, al, extmap(c, L),
+                                                                        c->d_mods, key, c->nm, c->nq, g, c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, acc.get() + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true);
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
     long tot = (long)2 * nct * L << c->logN;
-    k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
-                                                         c->d_mods, c->d_mdcv, c->nq, c->logN);
+    {
+        ProfScope ps_(c, "moddown", 0);
+        k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
+                                                             c->d_mods, c->d_mdcv, c->nq, c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false);
-    k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc.get(), conv.get(), 2 * nct, L, al, qmap(L),
-                                                        c->d_mods, c->d_pinv, c->logN, accumulate ? 1 : 0);
+    {
+        ProfScope ps_(c, "moddown", 0);
+        k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc.get(), conv.get(), 2 * nct, L, al, qmap(L),
+                                                            c->d_mods, c->d_pinv, c->logN, accumulate ? 1 : 0);
+    }
     LAUNCH_CHECK();
     c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
 }
@@ -452,8 +503,11 @@ static const uint64_t *get_key(he_ctx *c, int galois) {
 static DCt relinearize(he_ctx *c, const uint64_t *d, int level, int nct, double scale) {
     int L = level + 1;
     DCt y = ct_new(c, level, nct, scale);
-    CK(cudaMemcpy2DAsync(y.d, (size_t)2 * L * c->N * 8, d, (size_t)3 * L * c->N * 8, (size_t)2 * L * c->N * 8, nct,
-                         cudaMemcpyDeviceToDevice, c->st));
+    {
+        ProfScope ps_(c, "copy", 0);
+        CK(cudaMemcpy2DAsync(y.d, (size_t)2 * L * c->N * 8, d, (size_t)3 * L * c->N * 8, (size_t)2 * L * c->N * 8, nct,
+                             cudaMemcpyDeviceToDevice, c->st));
+    }
     DPtr dig = ks_modup(c, d + 2L * L * c->N, 3L * L * c->N, nct, L);
     ks_finish(c, dig.get(), nct, L, 0, get_key(c, 0), y.d, y.cs(c), true);
     return y;
@@ -490,6 +544,18 @@ static DCt hmult(he_ctx *c, const DCt &a, const DCt &b) {
 
 // Rot by galois elements: ModUp(c1) once, then for every g: X -> X^g on the digits and c0,
 // inner product with swk(s(X^g) -> s), ModDown.
+// y.c0 += x.c0(X^g) for every ciphertext of the batch
+static void automorph_acc(he_ctx *c, DCt &y, const DCt &x, int g) {
+    int L = x.level + 1;
+    long tot = (long)x.nct * L << c->logN;
+    {
+        ProfScope ps_(c, "automorph", 0);
+        k_automorph_acc<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, y.cs(c), x.d, x.cs(c), x.nct * L, L, qmap(L),
+                                                              c->d_mods, g, c->logN);
+    }
+    LAUNCH_CHECK();
+}
+
 static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vector<int> &gal) {
     int L = x.level + 1;
     std::vector<DCt> out;
@@ -504,11 +570,9 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
         }
         const uint64_t *key = get_key(c, g);
         DCt y = ct_new(c, x.level, x.nct, x.scale);
-        CK(cudaMemsetAsync(y.d, 0, (size_t)y.nct * y.cs(c) * 8, c->st));
-        long tot = (long)x.nct * L << c->logN;
-        k_automorph<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, y.cs(c), x.d, x.cs(c), x.nct * L, L, g, c->logN);
-        LAUNCH_CHECK();
-        ks_finish(c, dig.get(), x.nct, L, g, key, y.d, y.cs(c), true);
+        // key switch of c1(X^g) written into y, then c0(X^g) added to its first polynomial
+        ks_finish(c, dig.get(), x.nct, L, g, key, y.d, y.cs(c), false);
+        automorph_acc(c, y, x, g);
         out.push_back(y);
         c->cnt[1]++;
     }
@@ -516,6 +580,17 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
 }
 
 static DCt rotate(he_ctx *c, const DCt &x, int g) { return rotate_hoisted(c, x, std::vector<int>{g})[0]; }
+
+// acc += Rot_g(x) (same level and count): the key switch accumulates into acc directly
+static void rotate_acc(he_ctx *c, const DCt &x, int g, DCt &acc) {
+    REQUIRE(acc.level == x.level && acc.nct == x.nct, HE_EINVAL, "rotate_acc: level/count mismatch");
+    int L = x.level + 1;
+    const uint64_t *key = get_key(c, g);
+    DPtr dig = ks_modup(c, x.d + (long)L * c->N, x.cs(c), x.nct, L);
+    automorph_acc(c, acc, x, g);
+    ks_finish(c, dig.get(), x.nct, L, g, key, acc.d, acc.cs(c), true);
+    c->cnt[1]++;
+}
 
 static int galois_for_rot(he_ctx *c, long r) {
     long n0 = c->n0, m = 2L * c->N;
@@ -530,11 +605,17 @@ static DCt mod_raise(he_ctx *c, const DCt &a, int top) {
     REQUIRE(a.level == 0, HE_EINVAL, "mod_raise needs level 0");
     int npoly = 2 * a.nct, L = top + 1;
     DPtr x0 = dalloc(c, (size_t)npoly * c->N);
-    CK(cudaMemcpyAsync(x0.get(), a.d, (size_t)npoly * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
+    {
+        ProfScope ps_(c, "copy", 0);
+        CK(cudaMemcpyAsync(x0.get(), a.d, (size_t)npoly * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
+    }
     ntt(c, x0.get(), npoly, single(0), c->N, true);
     DCt y = ct_new(c, top, a.nct, a.scale);
     long tot = (long)npoly * L << c->logN;
-    k_modraise<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, x0.get(), npoly, L, qmap(L), c->d_mods, c->mods[0], c->logN);
+    {
+        ProfScope ps_(c, "modraise", 0);
+        k_modraise<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, x0.get(), npoly, L, qmap(L), c->d_mods, c->mods[0], c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, y.d, npoly * L, qmap(L), (long)L * c->N, false);
     return y;
@@ -548,13 +629,20 @@ static DPtr encode(he_ctx *c, const std::vector<double2> &z, double scale, int l
     double2 *wd = (double2 *)w.get();
     CK(cudaMemcpyAsync(wd, z.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice, c->st));
     dim3 g = grid_for(c, n0 / 2);
-    for (int len = n0; len >= 2; len >>= 1) k_sfft_inv_stage<<<g, 256, 0, c->st>>>(wd, n0, len, c->d_zeta, c->d_rg, 2 * c->N);
-    k_bitrev_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, c->logN - 1);
-    k_scale_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, (double)n0);
+    {
+        ProfScope ps_(c, "encode", 0);
+        for (int len = n0; len >= 2; len >>= 1)
+            k_sfft_inv_stage<<<g, 256, 0, c->st>>>(wd, n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+        k_bitrev_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, c->logN - 1);
+        k_scale_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, (double)n0);
+    }
     LAUNCH_CHECK();
     DPtr pt = dalloc(c, (size_t)L * c->N);
-    k_round_to_limbs<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(pt.get(), 0, wd, scale, L, L, qmap(L),
-                                                                         c->d_mods, c->logN);
+    {
+        ProfScope ps_(c, "encode", 0);
+        k_round_to_limbs<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(pt.get(), 0, wd, scale, L, L, qmap(L),
+                                                                             c->d_mods, c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, pt.get(), L, qmap(L), (long)L * c->N, false);
     return pt;
@@ -562,8 +650,11 @@ static DPtr encode(he_ctx *c, const std::vector<double2> &z, double scale, int l
 
 // device small integers (signed) -> NTT-form residues for the limbs of map
 static void small_to_ntt(he_ctx *c, uint64_t *out, const int64_t *v, const LimbMap &m) {
-    k_small_to_limbs<<<grid_for(c, (long)m.nper << c->logN), 256, 0, c->st>>>(out, 0, v, m.nper, m.nper, m, c->d_mods,
-                                                                               c->logN);
+    {
+        ProfScope ps_(c, "encode", 0);
+        k_small_to_limbs<<<grid_for(c, (long)m.nper << c->logN), 256, 0, c->st>>>(out, 0, v, m.nper, m.nper, m, c->d_mods,
+                                                                                   c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, out, m.nper, m, (long)m.nper * c->N, false);
 }
@@ -574,7 +665,10 @@ static uint64_t dom_key(int key_id, int digit, int which) {
 }
 
 static void sample_small(he_ctx *c, int64_t *out, uint64_t seed, uint64_t dom, uint64_t ctr0, int kind) {
-    k_sample_small<<<grid_for(c, c->N), 256, 0, c->st>>>(out, c->N, seed, dom, ctr0, c->d_cdt, c->cdt_len, kind);
+    {
+        ProfScope ps_(c, "keygen", 0);
+        k_sample_small<<<grid_for(c, c->N), 256, 0, c->st>>>(out, c->N, seed, dom, ctr0, c->d_cdt, c->cdt_len, kind);
+    }
     LAUNCH_CHECK();
 }
 
@@ -598,11 +692,26 @@ static void encrypt_into(he_ctx *c, const std::vector<double2> &z, int level, do
     long tot = (long)L << c->logN;
     uint64_t *c0 = out, *c1 = out + (long)L * c->N;
     const uint64_t *pkb = c->d_pk, *pka = c->d_pk + (long)c->nq * c->N;
-    k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, vn, 0, pkb, 0, L, L, m, c->d_mods, c->logN, 0);
-    k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, vn, 0, pka, 0, L, L, m, c->d_mods, c->logN, 0);
-    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, e0n, 0, L, L, m, c->d_mods, c->logN, 0);
-    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, pt.get(), 0, L, L, m, c->d_mods, c->logN, 0);
-    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, c1, 0, e1n, 0, L, L, m, c->d_mods, c->logN, 0);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, vn, 0, pkb, 0, L, L, m, c->d_mods, c->logN, 0);
+    }
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, vn, 0, pka, 0, L, L, m, c->d_mods, c->logN, 0);
+    }
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, e0n, 0, L, L, m, c->d_mods, c->logN, 0);
+    }
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, pt.get(), 0, L, L, m, c->d_mods, c->logN, 0);
+    }
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, c1, 0, e1n, 0, L, L, m, c->d_mods, c->logN, 0);
+    }
     LAUNCH_CHECK();
 }
 
@@ -612,17 +721,29 @@ static std::vector<double2> decrypt_slots(he_ctx *c, const DCt &x, int i) {
     const uint64_t *c0 = x.d + (long)i * x.cs(c), *c1 = c0 + (long)L * c->N;
     DPtr m = dalloc(c, (size_t)L * c->N);
     long tot = (long)L << c->logN;
-    k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, c1, 0, c->d_s, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
-    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, m.get(), 0, c0, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, c1, 0, c->d_s, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+    }
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, m.get(), 0, c0, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+    }
     LAUNCH_CHECK();
     ntt(c, m.get(), L, qmap(L), (long)L * c->N, true);
     DPtr w = dalloc(c, (size_t)2 * c->n0);
     double2 *wd = (double2 *)w.get();
-    k_crt_to_double<<<grid_for(c, c->N), 128, 0, c->st>>>(wd, m.get(), L, qmap(L), c->d_mods, c->d_radix, c->d_radinv,
-                                                          c->d_qd, x.scale, c->logN);
-    k_bitrev_c<<<grid_for(c, c->n0), 256, 0, c->st>>>(wd, c->n0, c->logN - 1);
-    for (int len = 2; len <= c->n0; len <<= 1)
-        k_sfft_fwd_stage<<<grid_for(c, c->n0 / 2), 256, 0, c->st>>>(wd, c->n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+    {
+        ProfScope ps_(c, "decode", 0);
+        k_crt_to_double<<<grid_for(c, c->N), 128, 0, c->st>>>(wd, m.get(), L, qmap(L), c->d_mods, c->d_radix, c->d_radinv,
+                                                              c->d_qd, x.scale, c->logN);
+    }
+    {
+        ProfScope ps_(c, "decode", 0);
+        k_bitrev_c<<<grid_for(c, c->n0), 256, 0, c->st>>>(wd, c->n0, c->logN - 1);
+        for (int len = 2; len <= c->n0; len <<= 1)
+            k_sfft_fwd_stage<<<grid_for(c, c->n0 / 2), 256, 0, c->st>>>(wd, c->n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+    }
     LAUNCH_CHECK();
     std::vector<double2> z(c->n0);
     CK(cudaMemcpyAsync(z.data(), wd, sizeof(double2) * c->n0, cudaMemcpyDeviceToHost, c->st));
@@ -635,7 +756,10 @@ static void keygen(he_ctx *c, uint64_t seed) {
     c->seed = seed;
     int N = c->N, nm = c->nm;
     DPtr sint = dalloc(c, N);
-    k_sample_hwt<<<(N + 255) / 256, 256, 256 * 8, c->st>>>((int64_t *)sint.get(), N, c->h, seed, DOM_SK, DOM_SK_SIGN);
+    {
+        ProfScope ps_(c, "keygen", 0);
+        k_sample_hwt<<<(N + 255) / 256, 256, 256 * 8, c->st>>>((int64_t *)sint.get(), N, c->h, seed, DOM_SK, DOM_SK_SIGN);
+    }
     LAUNCH_CHECK();
     if (!c->d_s) CK(cudaMalloc(&c->d_s, (size_t)nm * N * 8));
     small_to_ntt(c, c->d_s, (int64_t *)sint.get(), allmap(c));
@@ -646,14 +770,20 @@ static void keygen(he_ctx *c, uint64_t seed) {
     sample_small(c, (int64_t *)e.get(), seed, DOM_PK_E, 0, 0);
     LimbMap qm = qmap(c->nq);
     small_to_ntt(c, el.get(), (int64_t *)e.get(), qm);
-    k_sample_uniform<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pka, 0, c->nq, c->nq, qm, c->d_mods, seed,
-                                                                              DOM_PK_A, c->logN);
+    {
+        ProfScope ps_(c, "keygen", 0);
+        k_sample_uniform<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pka, 0, c->nq, c->nq, qm, c->d_mods, seed,
+                                                                                  DOM_PK_A, c->logN);
+    }
     LAUNCH_CHECK();
     ntt(c, pka, c->nq, qm, (long)c->nq * N, false);
     Scal z0;
     memset(&z0, 0, sizeof z0);
-    k_key_combine<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pkb, pka, el.get(), c->d_s, nullptr, z0, c->nq,
-                                                                           0, 0, qm, c->d_mods, c->logN);
+    {
+        ProfScope ps_(c, "keygen", 0);
+        k_key_combine<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pkb, pka, el.get(), c->d_s, nullptr, z0, c->nq,
+                                                                               0, 0, qm, c->d_mods, c->logN);
+    }
     LAUNCH_CHECK();
     c->have_keys = true;
 }
@@ -667,9 +797,15 @@ static void make_key(he_ctx *c, int galois) {
     DPtr sp = dalloc(c, (size_t)nm * N), e = dalloc(c, N), el = dalloc(c, (size_t)nm * N);
     long tot = (long)nm << c->logN;
     if (galois == 0)
-        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, c->d_s, 0, nm, nm, am, c->d_mods, c->logN, 0);
+        {
+            ProfScope ps_(c, "elementwise", 0);
+            k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, c->d_s, 0, nm, nm, am, c->d_mods, c->logN, 0);
+        }
     else
-        k_automorph<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, nm, nm, galois, c->logN);
+        {
+            ProfScope ps_(c, "automorph", 0);
+            k_automorph<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, nm, nm, galois, c->logN);
+        }
     LAUNCH_CHECK();
     Scal pm;
     for (int t = 0; t < nm; t++) {
@@ -681,15 +817,31 @@ static void make_key(he_ctx *c, int galois) {
         uint64_t *b = key + (size_t)(2 * j) * nm * N, *a = key + (size_t)(2 * j + 1) * nm * N;
         sample_small(c, (int64_t *)e.get(), c->seed, dom_key(galois, j, 1), 0, 0);
         small_to_ntt(c, el.get(), (int64_t *)e.get(), am);
-        k_sample_uniform<<<grid_for(c, tot), 256, 0, c->st>>>(a, 0, nm, nm, am, c->d_mods, c->seed, dom_key(galois, j, 0),
-                                                               c->logN);
+        {
+            ProfScope ps_(c, "keygen", 0);
+            k_sample_uniform<<<grid_for(c, tot), 256, 0, c->st>>>(a, 0, nm, nm, am, c->d_mods, c->seed, dom_key(galois, j, 0),
+                                                                   c->logN);
+        }
         LAUNCH_CHECK();
         ntt(c, a, nm, am, (long)nm * N, false);
         int dlo = j * c->alpha, dhi = std::min((j + 1) * c->alpha, c->nq);
-        k_key_combine<<<grid_for(c, tot), 256, 0, c->st>>>(b, a, el.get(), c->d_s, sp.get(), pm, nm, dlo, dhi, am,
-                                                            c->d_mods, c->logN);
+        {
+            ProfScope ps_(c, "keygen", 0);
+            k_key_combine<<<grid_for(c, tot), 256, 0, c->st>>>(b, a, el.get(), c->d_s, sp.get(), pm, nm, dlo, dhi, am,
+                                                                c->d_mods, c->logN);
+        }
         LAUNCH_CHECK();
     }
+    // stored in Montgomery form (k 2^64 mod q): the inner product sums raw 128-bit products
+    // and reduces once
+    Scal rm;
+    for (int t = 0; t < nm; t++) rm.v[t] = h_mont(1, c->mods[t]);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul_scalar<<<grid_for(c, (long)2 * nd * nm << c->logN), 256, 0, c->st>>>(key, (long)nm * N, key, (long)nm * N, rm, 2 * nd * nm, nm, am,
+                                                                                  c->d_mods, c->logN);
+    }
+    LAUNCH_CHECK();
     c->keys[galois] = key;
 }
 
@@ -703,10 +855,17 @@ struct PolyEval {
 
     DCt adjust(const DCt &x, int lt, double st) {
         REQUIRE(x.level >= lt + 1, HE_ELEVEL, "adjust: level");
-        DCt y = ct_drop(c, x, lt + 1);
+        int L = lt + 2;
         double q = (double)c->mods[lt + 1];
-        ct_mul_int(c, y, h_round((st * q) / x.scale));
-        y.scale = st * q;
+        // drop to level lt + 1 and multiply by the integer in one pass
+        DCt y = ct_new(c, lt + 1, x.nct, st * q);
+        Scal s = scal_of(c, h_round((st * q) / x.scale), L);
+        {
+            ProfScope ps_(c, "elementwise", 0);
+            k_mul_scalar<<<grid_for(c, (long)2 * x.nct * L << c->logN), 256, 0, c->st>>>(
+                y.d, y.ps(c), x.d, x.ps(c), s, 2 * x.nct * L, L, qmap(L), c->d_mods, c->logN);
+        }
+        LAUNCH_CHECK();
         return rescale(c, y);
     }
 
@@ -741,25 +900,38 @@ struct PolyEval {
         return d;
     }
 
+    // sum_k round(cf_k st q / scale_k) T_k + round(cf_0 st q) at level lt + 1, then rescale:
+    // one pass over the T_k (drop, integer products, sum and constant fused)
     DCt lincomb(const std::vector<double> &cf, int d, int lt, double st) {
         double q = (double)c->mods[lt + 1];
-        DCt out;
-        bool have = false;
+        int L = lt + 2;
+        for (int k = 1; k <= d; k++)
+            if (cf[k] != 0.0) getT(k);
+        LcArgs A;
+        memset(&A, 0, sizeof A);
+        int nct = T[1].nct;
         for (int k = 1; k <= d; k++) {
             if (cf[k] == 0.0) continue;
-            const DCt &tk = getT(k);
-            DCt x = ct_drop(c, tk, lt + 1);
-            ct_mul_int(c, x, h_round(((cf[k] * st) * q) / tk.scale));
-            x.scale = st * q;
-            if (!have) {
-                out = x;
-                have = true;
-            } else {
-                ct_add_inplace(c, out, x);
-            }
+            const DCt &tk = T[k];
+            REQUIRE(tk.level >= lt + 1, HE_ELEVEL, "lincomb: level");
+            REQUIRE(A.nt < HE_LC_MAXT, HE_EINVAL, "lincomb: too many terms");
+            i128 kk = h_round(((cf[k] * st) * q) / tk.scale);
+            for (int l = 0; l < L; l++) A.w[A.nt][l] = h_mont(h_red128(kk, c->mods[l]), c->mods[l]);
+            A.x[A.nt] = tk.d;
+            A.cs[A.nt] = tk.cs(c);
+            A.ps[A.nt] = tk.ps(c);
+            A.nt++;
         }
-        REQUIRE(have, HE_EINVAL, "lincomb: constant polynomial");
-        ct_add_const(c, out, h_round((cf[0] * st) * q));
+        REQUIRE(A.nt >= 1, HE_EINVAL, "lincomb: constant polynomial");
+        i128 k0 = h_round((cf[0] * st) * q);
+        for (int l = 0; l < L; l++) A.w[A.nt][l] = h_red128(k0, c->mods[l]);
+        DCt out = ct_new(c, lt + 1, nct, st * q);
+        {
+            ProfScope ps_(c, "elementwise", 0);
+            k_lincomb<<<grid_for(c, (long)nct * 2 * L << c->logN), 256, 0, c->st>>>(out.d, A, nct, L, qmap(L),
+                                                                                     c->d_mods, c->logN);
+        }
+        LAUNCH_CHECK();
         return rescale(c, out);
     }
 
@@ -887,6 +1059,18 @@ static void lt_sources(he_ctx *c, int h, int inverse, int i, int *src, double2 *
     }
 }
 
+// plaintext [L][N] -> Montgomery form (x 2^64 mod q_l)
+static void to_mont(he_ctx *c, uint64_t *pt, int L) {
+    Scal rm;
+    for (int l = 0; l < L; l++) rm.v[l] = h_mont(1, c->mods[l]);
+    {
+        ProfScope ps_(c, "elementwise", 0);
+        k_mul_scalar<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(pt, 0, pt, 0, rm, L, L, qmap(L), c->d_mods,
+                                                                          c->logN);
+    }
+    LAUNCH_CHECK();
+}
+
 static int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 static int bsgs_g(int r) { return 1 << ((r + 2) / 2); }
 
@@ -947,6 +1131,7 @@ static const LtLevel &lt_prepare(he_ctx *c, const LtDesc &lv, double gain, doubl
             p.a = a;
             p.b = b;
             p.pt = encode(c, rd, pt_scale, level);
+            to_mont(c, p.pt.get(), level + 1);   // read only by the fused inner sums
             L.pts.push_back(p);
         }
     }
@@ -954,39 +1139,58 @@ static const LtLevel &lt_prepare(he_ctx *c, const LtDesc &lv, double gain, doubl
 }
 
 static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain, double pt_scale) {
-    const LtLevel &L = lt_prepare(c, lv, gain, pt_scale, x.level);
+    const LtLevel &Lv = lt_prepare(c, lv, gain, pt_scale, x.level);
+    int L = x.level + 1;
+    // baby steps Rot(x, b hmin), hoisted (one ModUp); b = 0 is x itself
     std::vector<int> gal;
-    for (int b : L.baby) gal.push_back(galois_for_rot(c, (long)b * L.hmin));
-    std::vector<DCt> baby = rotate_hoisted(c, x, gal);
+    for (int b : Lv.baby)
+        if (b != 0) gal.push_back(galois_for_rot(c, (long)b * Lv.hmin));
+    std::vector<DCt> rots = rotate_hoisted(c, x, gal);
+    LtArgs A;
+    memset(&A, 0, sizeof A);
     std::map<int, int> bidx;
-    for (size_t i = 0; i < L.baby.size(); i++) bidx[L.baby[i]] = (int)i;
-    DCt acc;
-    bool have_acc = false;
-    size_t pi = 0;
-    while (pi < L.pts.size()) {
-        int a = L.pts[pi].a;
-        DCt inner;
-        bool have = false;
-        for (; pi < L.pts.size() && L.pts[pi].a == a; pi++) {
-            DCt t = ct_copy(c, baby[bidx[L.pts[pi].b]]);
-            ct_mul_plain(c, t, L.pts[pi].pt.get());
-            if (!have) {
-                inner = t;
-                have = true;
-            } else {
-                inner.scale = t.scale;
-                ct_add_inplace(c, inner, t);
-            }
-        }
-        inner.scale = x.scale * pt_scale;
-        if (a != 0) inner = rotate(c, inner, galois_for_rot(c, (long)a * L.g * L.hmin));
-        if (!have_acc) {
-            acc = inner;
-            have_acc = true;
-        } else {
-            ct_add_inplace(c, acc, inner);
-        }
+    size_t ri = 0;
+    for (int b : Lv.baby) {
+        REQUIRE(A.nb < HE_LT_MAXB, HE_EINVAL, "lintrans: too many baby steps");
+        bidx[b] = A.nb;
+        A.baby[A.nb++] = b == 0 ? x.d : rots[ri++].d;
     }
+    // giant steps a (plaintexts are sorted by a): out_a = sum_b pt_{a,b} (.) baby_b in one pass
+    std::vector<int> gi;
+    std::vector<DCt> inner;
+    memset(A.ptix, -1, sizeof A.ptix);
+    REQUIRE(Lv.pts.size() <= HE_LT_MAXPT, HE_EINVAL, "lintrans: too many diagonals");
+    for (size_t pi = 0; pi < Lv.pts.size(); pi++) {
+        int a = Lv.pts[pi].a;
+        if (gi.empty() || gi.back() != a) {
+            REQUIRE(gi.size() < HE_LT_MAXA, HE_EINVAL, "lintrans: too many giant steps");
+            gi.push_back(a);
+            inner.push_back(ct_new(c, x.level, x.nct, x.scale * pt_scale));
+            A.out[A.na++] = inner.back().d;
+        }
+        A.ptix[A.na - 1][bidx.at(Lv.pts[pi].b)] = (signed char)A.npt;
+        A.pt[A.npt++] = Lv.pts[pi].pt.get();
+    }
+    {
+        int ntile = c->N / HE_LT_KT;
+        long tiles = (long)L * ntile;
+        dim3 grid((unsigned)std::min<long>(tiles, c->max_grid / 4), 1);
+        size_t smem = (size_t)A.npt * HE_LT_KT * 8;
+        ProfScope ps_(c, "lintrans", 8.0 * c->N * ((double)L * A.npt + (double)x.nct * 2 * L * (A.nb + A.na)));
+        k_lt_bsgs<<<grid, 256, smem, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
+    }
+    LAUNCH_CHECK();
+    // acc = sum_a Rot(out_a, a g hmin), the rotations accumulated into acc
+    int first = -1;
+    for (size_t i = 0; i < gi.size(); i++)
+        if (gi[i] == 0) first = (int)i;
+    DCt acc = first >= 0 ? inner[first] : rotate(c, inner[0], galois_for_rot(c, (long)gi[0] * Lv.g * Lv.hmin));
+    if (first < 0) first = 0;
+    for (size_t i = 0; i < gi.size(); i++) {
+        if ((int)i == first) continue;
+        rotate_acc(c, inner[i], galois_for_rot(c, (long)gi[i] * Lv.g * Lv.hmin), acc);
+    }
+    acc.scale = x.scale * pt_scale;
     return rescale(c, acc);
 }
 
@@ -1144,11 +1348,16 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
                     int cnt = 3 * L;
                     long tot = (long)cnt << c->logN;
                     if (first && i == 0)
-                        CK(cudaMemcpyAsync(d.get(), dd.get(), (size_t)3 * L * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
-                    else
+                        {
+                            ProfScope ps_(c, "copy", 0);
+                            CK(cudaMemcpyAsync(d.get(), dd.get(), (size_t)3 * L * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
+                        }
+                    else {
+                        ProfScope ps_(c, "elementwise", 0);
                         k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), (long)L * c->N, d.get(), (long)L * c->N,
                                                                     dd.get() + (long)i * 3 * L * c->N, (long)L * c->N,
                                                                     cnt, L, qmap(L), c->d_mods, c->logN, 0);
+                    }
                     LAUNCH_CHECK();
                 }
                 first = false;
@@ -1230,6 +1439,9 @@ static void build_tables(he_ctx *c) {
         m.s = s;
         m.pad = 0;
         m.mu = (uint64_t)(((u128)1 << (s + 63)) / q);
+        uint64_t inv = q;                          // q^{-1} mod 2^64 by Newton's iteration
+        for (int it = 0; it < 6; it++) inv *= 2 - q * inv;
+        m.qinv = 0 - inv;
         c->modc[i] = m;
     }
     CK(cudaMalloc(&c->d_mods, sizeof(ModC) * nm));
@@ -1283,7 +1495,7 @@ static void build_tables(he_ctx *c) {
                     uint64_t mt = c->mods[t < L ? t : c->nq + (t - L)], pr = 1 % mt;
                     for (int i2 = lo; i2 < hi; i2++)
                         if (i2 != i) pr = h_mulmod(pr, c->mods[i2] % mt, mt);
-                    qh[(size_t)(i - lo) * nl + t] = pr;
+                    qh[(size_t)(i - lo) * nl + t] = h_mont(pr, mt);
                 }
             }
             cv.insert(cv.end(), qhinv.begin(), qhinv.end());
@@ -1307,7 +1519,7 @@ static void build_tables(he_ctx *c) {
             uint64_t q = c->mods[i], pr = 1 % q;
             for (int k2 = 0; k2 < al; k2++)
                 if (k2 != k) pr = h_mulmod(pr, c->mods[c->nq + k2] % q, q);
-            md[2 * al + (size_t)k * c->nq + i] = pr;
+            md[2 * al + (size_t)k * c->nq + i] = h_mont(pr, q);
         }
     }
     for (int i = 0; i < c->nq; i++) {
@@ -1384,6 +1596,9 @@ static void build_tables(he_ctx *c) {
     CK(cudaMalloc(&c->d_qd, qdv.size() * 8));
     CK(cudaMemcpy(c->d_qd, qdv.data(), qdv.size() * 8, cudaMemcpyHostToDevice));
     c->ndig_top = (c->nq + al - 1) / al;
+    // the conversion and inner-product kernels hold alpha residues and ndig key words per
+    // thread, and their 128-bit sums must stay below q 2^64
+    REQUIRE(al >= 1 && al <= 8 && c->ndig_top <= 8, HE_EINVAL, "alpha and the digit count must be at most 8");
     // dynamic shared memory of the column pass (N1 * 16 words)
     int logN1 = c->logN / 2;
     size_t sm1 = (size_t)(1 << logN1) * std::min(16, N >> logN1) * 8;
@@ -1818,6 +2033,31 @@ int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes
     *bytes = ctx->prof_bytes;
     ctx->prof_used = 0;
     ctx->prof_bytes = 0;
+    API_END
+}
+
+int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len) {
+    if (!ctx || !buf || len == 0) return HE_EINVAL;
+    API_BEGIN
+    CK(cudaStreamSynchronize(ctx->st));
+    std::map<std::string, std::pair<long, double>> fam;
+    for (size_t i = 0; i < ctx->prof_used; i++) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[i].first, ctx->prof_ev[i].second));
+        auto &f = fam[ctx->prof_fam[i]];
+        f.first++;
+        f.second += ms;
+    }
+    std::string out;
+    for (const auto &kv : fam) {
+        char line[128];
+        snprintf(line, sizeof line, "%s %ld %.6f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+        out += line;
+    }
+    ctx->prof_used = 0;
+    ctx->prof_bytes = 0;
+    REQUIRE(out.size() < len, HE_EINVAL, "he_profile_breakdown: buffer too small");
+    memcpy(buf, out.c_str(), out.size() + 1);
     API_END
 }
 

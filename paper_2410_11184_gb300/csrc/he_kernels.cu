@@ -229,6 +229,71 @@ __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, 
     }
 }
 
+// out += a(X^g) on the selected limbs (the c0 part of a rotation, added to a key-switch result)
+__global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, LimbMap map,
+                                const ModC *mods, int g, int logN) {
+    EW_PROLOGUE
+    long o = po * so + (long)li * N + k;
+    out[o] = add_mod(out[o], a[po * sa + (long)li * N + auto_index(k, g, logN)], m.q);
+    }
+}
+
+// Baby-step/giant-step inner sums of a linear-transform level: every block stages the
+// plaintext diagonals of one (limb, 32-coefficient tile) in shared memory, then each row
+// (ciphertext polynomial) reads its nb baby-step values once and writes the na giant-step
+// sums once; the sums are 128-bit and reduced once (plaintexts in Montgomery form, at most 16
+// terms below 16 q^2 < q 2^64).  Dynamic shared memory: npt * HE_LT_KT words.
+__global__ void __launch_bounds__(256) k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods,
+                                                 int logN) {
+    extern __shared__ uint64_t spt[];
+    constexpr int KT = HE_LT_KT, RG = 256 / KT;
+    const int N = 1 << logN, ntile = N / KT;
+    const int kk = threadIdx.x % KT, rg = threadIdx.x / KT;
+    for (long t = blockIdx.x; t < (long)L * ntile; t += gridDim.x) {
+        const int l = (int)(t / ntile), k0 = (int)(t % ntile) * KT;
+        const ModC m = mods[qmap.prime[l]];
+        __syncthreads();   // the previous tile's readers are done
+        for (int i = threadIdx.x; i < A.npt * KT; i += blockDim.x) spt[i] = A.pt[i / KT][(long)l * N + k0 + i % KT];
+        __syncthreads();
+        for (int r = blockIdx.y * RG + rg; r < npoly; r += gridDim.y * RG) {
+            const long off = ((long)r * L + l) * N + k0 + kk;
+            uint64_t bv[HE_LT_MAXB];
+#pragma unroll
+            for (int b = 0; b < HE_LT_MAXB; b++) bv[b] = b < A.nb ? A.baby[b][off] : 0;
+            for (int a = 0; a < A.na; a++) {
+                uint64_t lo = 0, hi = 0;
+#pragma unroll
+                for (int b = 0; b < HE_LT_MAXB; b++) {
+                    const int pi = b < A.nb ? A.ptix[a][b] : -1;
+                    if (pi >= 0) mac_wide(lo, hi, bv[b], spt[pi * KT + kk]);
+                }
+                A.out[a][off] = redc(lo, hi, m);
+            }
+        }
+    }
+}
+
+// out[c][p][l] = sum_t x_t[c][p][l] w_t[l] (+ w_nt[l] when p = 0) for l < L: rows t < nt of w in
+// Montgomery form (sums of at most 8 products stay below q 2^64), row nt a plain residue.
+// Reads each input once (only its first L limbs).
+__global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap, const ModC *mods, int logN) {
+    const int N = 1 << logN;
+    long total = (long)nct * 2 * L << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(id & (N - 1));
+        const long row = id >> logN;                 // (c * 2 + p) * L + l
+        const int l = (int)(row % L), p = (int)((row / L) & 1);
+        const long c = row / L / 2;
+        const ModC m = mods[qmap.prime[l]];
+        uint64_t lo = 0, hi = 0;
+        for (int t = 0; t < A.nt; t++)
+            mac_wide(lo, hi, A.x[t][c * A.cs[t] + p * A.ps[t] + (long)l * N + k], A.w[t][l]);
+        uint64_t v = redc(lo, hi, m);
+        if (p == 0) v = add_mod(v, A.w[A.nt][l], m.q);
+        out[id] = v;
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Basis conversion (coefficient domain).  ModUp for one digit D of a batch of polynomials:
 // for every target modulus t of the extended basis,
@@ -239,7 +304,8 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN) {
     // one thread per (ciphertext, coefficient): the digit's limbs are read once, then every
-    // target limb is produced (y_i < 2^61 is multiplied mod m_t directly, no pre-reduction)
+    // target limb is produced as one 128-bit sum reduced once (cv holds the products of the
+    // other digit primes in Montgomery form, so redc returns the plain sum mod m_t)
     const int N = 1 << logN;
     long total = (long)nct << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -260,12 +326,13 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
         uint64_t *o = out + c * so_ct + so_digit + k;
         for (int t = 0; t < ntarget; t++) {
             const ModC mt = mods[tmap.prime[t]];
-            uint64_t acc = 0;
+            // sum of |y_i| (c or m_t - c): below dsize 2^60 m_t < m_t 2^64
+            uint64_t lo = 0, hi = 0;
             for (int i = 0; i < dsize; i++) {
-                uint64_t v = mul_mod(y[i], cv[2 * dsize + i * ntarget + t], mt);
-                acc = (negmask >> i) & 1 ? sub_mod(acc, v, mt.q) : add_mod(acc, v, mt.q);
+                uint64_t w = cv[2 * dsize + i * ntarget + t];
+                mac_wide(lo, hi, y[i], (negmask >> i) & 1 ? mt.q - w : w);
             }
-            o[(long)t * N] = acc;
+            o[(long)t * N] = redc(lo, hi, mt);
         }
     }
 }
@@ -298,12 +365,13 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
         uint64_t *o = out + (long)pl * L * N + k;
         for (int i = 0; i < L; i++) {
             const ModC mi = mods[qmap.prime[i]];
-            uint64_t acc = 0;
+            // one 128-bit sum, reduced once (phat_j mod q_i stored in Montgomery form)
+            uint64_t lo = 0, hi = 0;
             for (int j = 0; j < alpha; j++) {
-                uint64_t t = mul_mod(y[j], cv[2 * alpha + j * nqall + qmap.prime[i]], mi);
-                acc = (negmask >> j) & 1 ? sub_mod(acc, t, mi.q) : add_mod(acc, t, mi.q);
+                uint64_t w = cv[2 * alpha + j * nqall + qmap.prime[i]];
+                mac_wide(lo, hi, y[j], (negmask >> j) & 1 ? mi.q - w : w);
             }
-            o[(long)i * N] = acc;
+            o[(long)i * N] = redc(lo, hi, mi);
         }
     }
 }
@@ -346,14 +414,16 @@ __global__ void k_ks_inner(uint64_t *acc, const uint64_t *dig, int nct, int ndig
             ka[j] = key[((long)(2 * j + 1) * key_nlimb + kt) * N + k];
         }
         for (int c = 0; c < nct; c++) {
-            uint64_t s0 = 0, s1 = 0;
+            // the key is stored in Montgomery form: sum of d_j (k_j 2^64 mod m) < ndig m^2,
+            // below m 2^64, reduced once
+            uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
             for (int j = 0; j < ndig; j++) {
                 uint64_t d = dig[(((long)c * ndig + j) * nl + t) * N + src];
-                s0 = add_mod(s0, mul_mod(d, kb[j], m), m.q);
-                s1 = add_mod(s1, mul_mod(d, ka[j], m), m.q);
+                mac_wide(l0, h0, d, kb[j]);
+                mac_wide(l1, h1, d, ka[j]);
             }
-            acc[((long)(2 * c) * nl + t) * N + k] = s0;
-            acc[((long)(2 * c + 1) * nl + t) * N + k] = s1;
+            acc[((long)(2 * c) * nl + t) * N + k] = redc(l0, h0, m);
+            acc[((long)(2 * c + 1) * nl + t) * N + k] = redc(l1, h1, m);
         }
     }
 }
@@ -707,11 +777,13 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
 
 // Forward row pass: stages m = N1 .. N/2 on rows of S = N2 contiguous coefficients.
 template <int LOGE>
-__global__ void __launch_bounds__(256) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+__global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const uint64_t *tw, int logN) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;                         // rows per CTA
-    __shared__ uint64_t sm[S * SUB];
+    // one pad word per E: the E k + j accesses (stride E words) spread over all banks
+    constexpr int SP = S + S / E;
+    __shared__ uint64_t sm[SP * SUB];
     const int N = 1 << logN, N1 = N / S;
     const int l = blockIdx.y, p = map.prime[l % nper];
     uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
@@ -725,10 +797,10 @@ __global__ void __launch_bounds__(256) k_ntt_rows_fwd_rb(uint64_t *base, int npe
     // stages m = N1 .. N1 E/2: group = row (m / N1) + j / (2t)
     ct_stages_strided<LOGE>(v, N1, row, 1, psi, psip, q);
 #pragma unroll
-    for (int j = 0; j < E; j++) sm[rr * S + k + E * j] = v[j];
+    for (int j = 0; j < E; j++) sm[rr * SP + k + (E + 1) * j] = v[j];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; j++) v[j] = sm[rr * S + E * k + j];
+    for (int j = 0; j < E; j++) v[j] = sm[rr * SP + (E + 1) * k + j];
     // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
     ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, psip, q);
     // back to the k + E j layout through shared memory so the store is coalesced; the lazy
@@ -739,20 +811,22 @@ __global__ void __launch_bounds__(256) k_ntt_rows_fwd_rb(uint64_t *base, int npe
         uint64_t r = v[j];
         if (r >= 2 * q) r -= 2 * q;
         if (r >= q) r -= q;
-        sm[rr * S + E * k + j] = r;
+        sm[rr * SP + (E + 1) * k + j] = r;
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * S + k + E * j];
+    for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * SP + k + (E + 1) * j];
 }
 
 // Inverse row pass: stages h = N/2 .. N1 (t = 1 .. N2/2).
 template <int LOGE>
-__global__ void __launch_bounds__(256) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+__global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const uint64_t *tw, int logN) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;
-    __shared__ uint64_t sm[S * SUB];
+    // one pad word per E: the E k + j accesses (stride E words) spread over all banks
+    constexpr int SP = S + S / E;
+    __shared__ uint64_t sm[SP * SUB];
     const int N = 1 << logN, N1 = N / S;
     const int l = blockIdx.y, p = map.prime[l % nper];
     uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
@@ -763,17 +837,17 @@ __global__ void __launch_bounds__(256) k_ntt_rows_inv_rb(uint64_t *base, int npe
     uint64_t v[E];
     // coalesced load, then regroup to the E k + j layout through shared memory
 #pragma unroll
-    for (int j = 0; j < E; j++) sm[rr * S + k + E * j] = g[k + E * j];
+    for (int j = 0; j < E; j++) sm[rr * SP + k + (E + 1) * j] = g[k + E * j];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; j++) v[j] = sm[rr * S + E * k + j];
+    for (int j = 0; j < E; j++) v[j] = sm[rr * SP + (E + 1) * k + j];
     __syncthreads();
     gs_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, ipsi, ipsip, q);
 #pragma unroll
-    for (int j = 0; j < E; j++) sm[rr * S + E * k + j] = v[j];
+    for (int j = 0; j < E; j++) sm[rr * SP + (E + 1) * k + j] = v[j];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; j++) v[j] = sm[rr * S + k + E * j];
+    for (int j = 0; j < E; j++) v[j] = sm[rr * SP + k + (E + 1) * j];
     gs_stages_strided<LOGE>(v, N1, row, 1, ipsi, ipsip, q);
 #pragma unroll
     for (int j = 0; j < E; j++) g[k + E * j] = v[j];

@@ -6,6 +6,31 @@ struct Scal {
     uint64_t v[HE_MAX_LIMBS];
 };
 
+// Baby-step/giant-step inner sums of one linear-transform level (passed by value):
+//   out_a = sum_b pt_{a,b} (.) baby_b   for every giant index a,
+// over batches [nct][2][L][N] in NTT form; plaintexts [L][N] in Montgomery form.
+#define HE_LT_MAXB 16
+#define HE_LT_MAXA 16
+#define HE_LT_MAXPT 128
+#define HE_LT_KT 32   // coefficients per tile (plaintext tile staged in shared memory)
+struct LtArgs {
+    const uint64_t *baby[HE_LT_MAXB];
+    uint64_t *out[HE_LT_MAXA];
+    const uint64_t *pt[HE_LT_MAXPT];
+    signed char ptix[HE_LT_MAXA][HE_LT_MAXB];   // plaintext of (a, b), -1 if the diagonal is zero
+    int nb, na, npt;
+};
+
+// Linear combination sum_t w_t x_t (+ w0 on c0) of up to HE_LC_MAXT batches at any levels
+#define HE_LC_MAXT 8
+struct LcArgs {
+    const uint64_t *x[HE_LC_MAXT];
+    long cs[HE_LC_MAXT];   // ciphertext stride of input t (words)
+    long ps[HE_LC_MAXT];   // polynomial stride of input t (words)
+    uint64_t w[HE_LC_MAXT + 1][HE_MAX_LIMBS];   // weights (Montgomery form); row nt: constant on c0
+    int nt;
+};
+
 __global__ void k_ntt_cols_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
                                const uint64_t *tw, int logN, int logN1, int C);
 __global__ void k_ntt_rows_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
@@ -25,6 +50,10 @@ __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int npe
 __global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
                          int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
 __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN);
+__global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, LimbMap map,
+                                const ModC *mods, int g, int logN);
+__global__ void k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN);
+__global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap, const ModC *mods, int logN);
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN);

@@ -92,6 +92,8 @@ def lib():
         L.he_profile_kernel.argtypes = [vp, C.c_char_p]
         L.he_profile_read.restype = C.c_int
         L.he_profile_read.argtypes = [vp, dblp, C.POINTER(C.c_long), dblp]
+        L.he_profile_breakdown.restype = C.c_int
+        L.he_profile_breakdown.argtypes = [vp, C.c_char_p, C.c_size_t]
         L.he_last_error.restype = C.c_char_p
         L.he_last_error.argtypes = [vp]
         _lib = L
@@ -310,6 +312,16 @@ class Context:
         ms, n, b = C.c_double(), C.c_long(), C.c_double()
         self.check(lib().he_profile_read(self.h, C.byref(ms), C.byref(n), C.byref(b)))
         return ms.value, n.value, b.value
+
+    def profile_breakdown(self):
+        """{family: (launches, total_ms)} since he_profile_kernel("all") (then resets)."""
+        buf = C.create_string_buffer(1 << 14)
+        self.check(lib().he_profile_breakdown(self.h, buf, len(buf)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms = line.split()
+            out[name] = (int(n), float(ms))
+        return out
 
     def selftest_bounded_wait(self, max_iter):
         return lib().he_selftest_bounded_wait(self.h, max_iter)
