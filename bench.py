@@ -267,7 +267,11 @@ def main():
         if not args.no_breakdown:
             g.profile_kernel("all")
             step(True)
-            breakdown = {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in g.profile_breakdown().items()}
+            breakdown = {}
+            for k, (n, ms, b) in g.profile_breakdown().items():
+                breakdown[k] = {"launches": n, "ms": round(ms, 3)}
+                if b > 0 and ms > 0:
+                    breakdown[k]["gbs"] = round(b / (ms * 1e-3) / 1e9, 1)
             g.profile_kernel("")
         # e2e: pinned host ciphertexts in, results out, through he_softmax
         host_in = torch.empty_like(src.tensor, device="cpu").pin_memory()

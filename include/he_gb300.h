@@ -163,7 +163,8 @@ long he_launch_count(const he_ctx *ctx);
 int he_profile_kernel(he_ctx *ctx, const char *name);
 int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes);
 /* with he_profile_kernel(ctx, "all"): every launch and device copy is timed; this call
- * synchronises and writes one text line "family launches total_ms" per kernel family (ntt,
+ * synchronises and writes one text line "family launches total_ms bytes" (bytes: the
+ * algorithmic bytes of those launches, 0 where not stated) per kernel family (ntt,
  * modup, ks_inner, moddown, tensor, rescale, lintrans, elementwise, automorph, modraise, encode, decode,
  * keygen, copy) into buf (len bytes, NUL-terminated), then resets.  HE_EINVAL if buf is too small. */
 int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len);

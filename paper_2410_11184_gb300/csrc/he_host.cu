@@ -110,6 +110,7 @@ struct he_ctx {
     std::string prof_name;   // a family name, or "all"
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     std::vector<const char *> prof_fam;   // family of each recorded launch
+    std::vector<double> prof_b;           // its algorithmic bytes
     size_t prof_used = 0;
     double prof_bytes = 0;
 };
@@ -122,7 +123,7 @@ struct ProfScope {
     bool on;
     size_t slot;
     ProfScope(he_ctx *c_, const char *name, double bytes)
-        : c(c_), on(!c_->prof_name.empty() && (c_->prof_name == name || c_->prof_name == "all")) {
+        : c(c_), on(match(c_->prof_name, name)) {
         if (!on) return;
         if (c->prof_used == c->prof_ev.size()) {
             cudaEvent_t a, b;
@@ -130,11 +131,20 @@ struct ProfScope {
             cudaEventCreate(&b);
             c->prof_ev.push_back({a, b});
             c->prof_fam.push_back(nullptr);
+            c->prof_b.push_back(0);
         }
         slot = c->prof_used++;
         c->prof_fam[slot] = name;
+        c->prof_b[slot] = bytes;
         c->prof_bytes += bytes;
         cudaEventRecord(c->prof_ev[slot].first, c->st);
+    }
+    // "all", the family itself, or a family prefix ("ntt" covers "ntt_modup", ...)
+    static bool match(const std::string &want, const char *name) {
+        if (want.empty()) return false;
+        if (want == "all" || want == name) return true;
+        size_t n = want.size();
+        return strncmp(name, want.c_str(), n) == 0 && name[n] == '_';
     }
     ~ProfScope() {
         if (on) cudaEventRecord(c->prof_ev[slot].second, c->st);
@@ -209,20 +219,29 @@ static LimbMap single(int p) {
 }
 
 // ------------------------------------------------------------------------- NTT launches
-static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long poly_stride, bool inverse) {
+// NTT of `count` limbs in place, or out of place from src (limb l of polynomial i at
+// src + i src_stride + l N) when src is given
+static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long poly_stride, bool inverse,
+                const char *site = "ntt", const uint64_t *src = nullptr, long src_stride = 0) {
     if (count <= 0) return;
+    bool rb = c->logN == 16 || c->logN == 12;
+    if (src && !rb) {
+        CK(cudaMemcpy2DAsync(base, (size_t)poly_stride * 8, src, (size_t)src_stride * 8, (size_t)map.nper * c->N * 8,
+                             count / map.nper, cudaMemcpyDeviceToDevice, c->st));
+        src = nullptr;
+    }
     int logN1 = c->logN / 2;
     int N1 = 1 << logN1, N2 = c->N >> logN1;
     int C = std::min(16, N2);
     int R = std::max(1, std::min(N1, 2048 / N2));
     dim3 g1(N2 / C, count), g2(N1 / R, count);
     size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
-    ProfScope ps(c, "ntt", 16.0 * count * c->N);
+    ProfScope ps(c, site, 16.0 * count * c->N);
     c->launches++;
-    if (c->logN == 16 || c->logN == 12) {
+    if (rb) {
         // register-blocked passes: 16 (N = 2^16) or 8 (N = 2^12) coefficients per thread
         launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw,
-                      c->d_ninv, c->logN, c->st);
+                      c->d_ninv, c->logN, c->st, src, src_stride);
         LAUNCH_CHECK();
         return;
     }
@@ -361,24 +380,19 @@ static DCt rescale(he_ctx *c, const DCt &a) {
     REQUIRE(l >= 1, HE_ELEVEL, "rescale at level 0");
     int npoly = 2 * a.nct;
     DPtr last = dalloc(c, (size_t)npoly * c->N);
-    {
-        ProfScope ps_(c, "copy", 0);
-        CK(cudaMemcpy2DAsync(last.get(), (size_t)c->N * 8, a.d + (long)l * c->N, (size_t)L * c->N * 8, (size_t)c->N * 8,
-                             npoly, cudaMemcpyDeviceToDevice, c->st));
-    }
-    ntt(c, last.get(), npoly, single(l), c->N, true);
+    ntt(c, last.get(), npoly, single(l), c->N, true, "ntt_rescale", a.d + (long)l * c->N, (long)L * c->N);
     DPtr tmp = dalloc(c, (size_t)npoly * l * c->N);
     long tot = (long)npoly * l << c->logN;
     {
-        ProfScope ps_(c, "rescale", 0);
+        ProfScope ps_(c, "rescale", 8.0 * c->N * npoly * (1 + l));
         k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp.get(), last.get(), npoly, l, qmap(l), c->d_mods,
                                                                c->mods[l], c->logN);
     }
     LAUNCH_CHECK();
-    ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false);
+    ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false, "ntt_rescale");
     DCt y = ct_new(c, l - 1, a.nct, a.scale / (double)c->mods[l]);
     {
-        ProfScope ps_(c, "rescale", 0);
+        ProfScope ps_(c, "rescale", 8.0 * c->N * npoly * 3.0 * l);
         k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, a.d, tmp.get(), npoly, L, qmap(l), c->d_mods,
                                                             c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
     }
@@ -418,32 +432,19 @@ static void rescale_noalloc(he_ctx *c, const DCt &a, uint64_t *out) {
 static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
     DPtr tmp = dalloc(c, (size_t)nct * L * c->N);
-    {
-        ProfScope ps_(c, "copy", 0);
-        CK(cudaMemcpy2DAsync(tmp.get(), (size_t)L * c->N * 8, x, (size_t)sx * 8, (size_t)L * c->N * 8, nct,
-                             cudaMemcpyDeviceToDevice, c->st));
-    }
-    ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true);
+    ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true, "ntt_modup", x, sx);
     DPtr dig = dalloc(c, (size_t)nct * nd * nl * c->N);
     LimbMap em = extmap(c, L);
     for (int j = 0; j < nd; j++) {
         int lo = j * al, ds = std::min(al, L - lo);
         long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)
         {
-            ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * ds + (double)nct * nl));
+            ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * 2 * ds + (double)nct * nl));
             k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
                                                           tmp.get(), (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
-                                                          c->d_cv + c->cv_off[L - 1][j], c->logN);
+                                                          c->d_cv + c->cv_off[L - 1][j], c->logN, x, sx);
         }
         LAUNCH_CHECK();
-        // the digit's own limbs are the input limbs: copy their NTT form instead of
-        // transforming the converted (identical) coefficients again
-        {
-            ProfScope ps_(c, "copy", 0);
-            CK(cudaMemcpy2DAsync(dig.get() + (long)j * nl * c->N + (long)lo * c->N, (size_t)nd * nl * c->N * 8,
-                                 x + (long)lo * c->N, (size_t)sx * 8, (size_t)ds * c->N * 8, nct,
-                                 cudaMemcpyDeviceToDevice, c->st));
-        }
         // forward NTT of the limbs outside the digit: [0, lo) and [lo + ds, L + alpha)
         const int ranges[2][2] = {{0, lo}, {lo + ds, nl}};
         for (const auto &r : ranges) {
@@ -452,16 +453,18 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
             LimbMap sub;
             sub.nper = b - a;
             for (int t = a; t < b; t++) sub.prime[t - a] = em.prime[t];
-            ntt(c, dig.get() + (long)j * nl * c->N + (long)a * c->N, nct * (b - a), sub, (long)nd * nl * c->N, false);
+            ntt(c, dig.get() + (long)j * nl * c->N + (long)a * c->N, nct * (b - a), sub, (long)nd * nl * c->N, false,
+                "ntt_modup");
         }
     }
     return dig;
 }
 
-// inner product with key (automorphism g applied to the digits when g > 1), ModDown, and
-// accumulation into out (nct ciphertexts at level L-1, stride so)
+// inner product with key (automorphism g applied to the digits when g > 1) and ModDown into out
+// (nct ciphertexts at level L-1, stride so); when add is given (it may be out itself) its two
+// polynomials (ciphertext stride sadd) are added to the result
 static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, const uint64_t *key, uint64_t *out,
-                      long so, bool accumulate) {
+                      long so, const uint64_t *add, long sadd) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
     DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
     {
@@ -470,20 +473,20 @@ static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, con
                                                                         c->d_mods, key, c->nm, c->nq, g, c->logN);
     }
     LAUNCH_CHECK();
-    ntt(c, acc.get() + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true);
+    ntt(c, acc.get() + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true, "ntt_moddown");
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
     long tot = (long)2 * nct * L << c->logN;
     {
-        ProfScope ps_(c, "moddown", 0);
+        ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (al + L));
         k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
                                                              c->d_mods, c->d_mdcv, c->nq, c->logN);
     }
     LAUNCH_CHECK();
-    ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false);
+    ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown");
     {
-        ProfScope ps_(c, "moddown", 0);
+        ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * L * (add ? 4 : 3));
         k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc.get(), conv.get(), 2 * nct, L, al, qmap(L),
-                                                            c->d_mods, c->d_pinv, c->logN, accumulate ? 1 : 0);
+                                                            c->d_mods, c->d_pinv, c->logN, add, sadd);
     }
     LAUNCH_CHECK();
     c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
@@ -503,13 +506,9 @@ static const uint64_t *get_key(he_ctx *c, int galois) {
 static DCt relinearize(he_ctx *c, const uint64_t *d, int level, int nct, double scale) {
     int L = level + 1;
     DCt y = ct_new(c, level, nct, scale);
-    {
-        ProfScope ps_(c, "copy", 0);
-        CK(cudaMemcpy2DAsync(y.d, (size_t)2 * L * c->N * 8, d, (size_t)3 * L * c->N * 8, (size_t)2 * L * c->N * 8, nct,
-                             cudaMemcpyDeviceToDevice, c->st));
-    }
     DPtr dig = ks_modup(c, d + 2L * L * c->N, 3L * L * c->N, nct, L);
-    ks_finish(c, dig.get(), nct, L, 0, get_key(c, 0), y.d, y.cs(c), true);
+    // y = (d0, d1) + KS(d2): d0 and d1 are added by the ModDown epilogue
+    ks_finish(c, dig.get(), nct, L, 0, get_key(c, 0), y.d, y.cs(c), d, 3L * L * c->N);
     return y;
 }
 
@@ -571,7 +570,7 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
         const uint64_t *key = get_key(c, g);
         DCt y = ct_new(c, x.level, x.nct, x.scale);
         // key switch of c1(X^g) written into y, then c0(X^g) added to its first polynomial
-        ks_finish(c, dig.get(), x.nct, L, g, key, y.d, y.cs(c), false);
+        ks_finish(c, dig.get(), x.nct, L, g, key, y.d, y.cs(c), nullptr, 0);
         automorph_acc(c, y, x, g);
         out.push_back(y);
         c->cnt[1]++;
@@ -588,7 +587,7 @@ static void rotate_acc(he_ctx *c, const DCt &x, int g, DCt &acc) {
     const uint64_t *key = get_key(c, g);
     DPtr dig = ks_modup(c, x.d + (long)L * c->N, x.cs(c), x.nct, L);
     automorph_acc(c, acc, x, g);
-    ks_finish(c, dig.get(), x.nct, L, g, key, acc.d, acc.cs(c), true);
+    ks_finish(c, dig.get(), x.nct, L, g, key, acc.d, acc.cs(c), acc.d, acc.cs(c));
     c->cnt[1]++;
 }
 
@@ -605,11 +604,7 @@ static DCt mod_raise(he_ctx *c, const DCt &a, int top) {
     REQUIRE(a.level == 0, HE_EINVAL, "mod_raise needs level 0");
     int npoly = 2 * a.nct, L = top + 1;
     DPtr x0 = dalloc(c, (size_t)npoly * c->N);
-    {
-        ProfScope ps_(c, "copy", 0);
-        CK(cudaMemcpyAsync(x0.get(), a.d, (size_t)npoly * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
-    }
-    ntt(c, x0.get(), npoly, single(0), c->N, true);
+    ntt(c, x0.get(), npoly, single(0), c->N, true, "ntt_modraise", a.d, c->N);
     DCt y = ct_new(c, top, a.nct, a.scale);
     long tot = (long)npoly * L << c->logN;
     {
@@ -617,7 +612,7 @@ static DCt mod_raise(he_ctx *c, const DCt &a, int top) {
         k_modraise<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, x0.get(), npoly, L, qmap(L), c->d_mods, c->mods[0], c->logN);
     }
     LAUNCH_CHECK();
-    ntt(c, y.d, npoly * L, qmap(L), (long)L * c->N, false);
+    ntt(c, y.d, npoly * L, qmap(L), (long)L * c->N, false, "ntt_modraise");
     return y;
 }
 
@@ -958,8 +953,7 @@ struct PolyEval {
         } else {
             double sq = (st * (double)c->mods[lt + 1]) / T[a].scale;
             DCt Q = eval(q, dq, lt + 1, sq);
-            DCt ta = ct_drop(c, T[a], lt + 1);
-            out = hmult(c, ta, Q);
+            out = hmult(c, T[a], Q);   // T_a's limbs above Q's level are not read
         }
         int dr = trim(r, a - 1);
         if (dr >= 1) {
@@ -2040,18 +2034,20 @@ int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len) {
     if (!ctx || !buf || len == 0) return HE_EINVAL;
     API_BEGIN
     CK(cudaStreamSynchronize(ctx->st));
-    std::map<std::string, std::pair<long, double>> fam;
+    std::map<std::string, std::tuple<long, double, double>> fam;
     for (size_t i = 0; i < ctx->prof_used; i++) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, ctx->prof_ev[i].first, ctx->prof_ev[i].second));
         auto &f = fam[ctx->prof_fam[i]];
-        f.first++;
-        f.second += ms;
+        std::get<0>(f)++;
+        std::get<1>(f) += ms;
+        std::get<2>(f) += ctx->prof_b[i];
     }
     std::string out;
     for (const auto &kv : fam) {
-        char line[128];
-        snprintf(line, sizeof line, "%s %ld %.6f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+        char line[160];
+        snprintf(line, sizeof line, "%s %ld %.6f %.6e\n", kv.first.c_str(), std::get<0>(kv.second),
+                 std::get<1>(kv.second), std::get<2>(kv.second));
         out += line;
     }
     ctx->prof_used = 0;

@@ -302,7 +302,7 @@ __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap,
 // then qh[a][ntarget].
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
-                        int logN) {
+                        int logN, const uint64_t *xntt, long sxn) {
     // one thread per (ciphertext, coefficient): the digit's limbs are read once, then every
     // target limb is produced as one 128-bit sum reduced once (cv holds the products of the
     // other digit primes in Montgomery form, so redc returns the plain sum mod m_t)
@@ -324,7 +324,13 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
             y[i] = v;
         }
         uint64_t *o = out + c * so_ct + so_digit + k;
+        // the digit's own limbs: the NTT-form input limbs themselves (the conversion would
+        // reproduce their coefficients)
+        for (int i = 0; i < dsize; i++)
+            o[(long)(digit_lo + i) * N] = xntt[c * sxn + (long)(digit_lo + i) * N + k];
         for (int t = 0; t < ntarget; t++) {
+            if (t == digit_lo) t += dsize;
+            if (t >= ntarget) break;
             const ModC mt = mods[tmap.prime[t]];
             // sum of |y_i| (c or m_t - c): below dsize 2^60 m_t < m_t 2^64
             uint64_t lo = 0, hi = 0;
@@ -378,7 +384,8 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
 
 // out_i = (x_i - conv_i) * pinv_i for the Q limbs of every polynomial; accumulate adds to out
 __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
-                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN, int accumulate) {
+                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN,
+                              const uint64_t *add, long sadd) {
     const int N = 1 << logN;
     long total = (long)npoly * L << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -388,7 +395,8 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
         uint64_t v = sub_mod(x[(long)pl * (L + alpha) * N + (long)i * N + k], conv[(long)pl * L * N + (long)i * N + k], mi.q);
         v = mul_shoup(v, pinv[2 * qmap.prime[i]], pinv[2 * qmap.prime[i] + 1], mi.q);
         long o = (long)(pl / 2) * so + (long)(pl % 2) * L * N + (long)i * N + k;
-        if (accumulate) v = add_mod(out[o], v, mi.q);
+        // add (may be out itself): polynomial p of ciphertext c at add + c sadd + p L N
+        if (add) v = add_mod(add[(long)(pl / 2) * sadd + (long)(pl % 2) * L * N + (long)i * N + k], v, mi.q);
         out[o] = v;
     }
 }
@@ -397,9 +405,9 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
 //   acc_{0,1}[t] = sum_j d~_j[t][pi_g(k)] * key_j^{b,a}[kt][k],
 // with the key limb kt = t for Q limbs and nq_all + (t - L) for P limbs.  The key is read once
 // per (t, k) for all ciphertexts of the batch.
-__global__ void k_ks_inner(uint64_t *acc, const uint64_t *dig, int nct, int ndig, int L, int alpha,
-                           LimbMap tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all,
-                           int g, int logN) {
+__global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
+                           int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
+                           int nq_all, int g, int logN) {
     const int N = 1 << logN;
     const int nl = L + alpha;
     long total = (long)nl << logN;
@@ -413,6 +421,7 @@ __global__ void k_ks_inner(uint64_t *acc, const uint64_t *dig, int nct, int ndig
             kb[j] = key[((long)(2 * j) * key_nlimb + kt) * N + k];
             ka[j] = key[((long)(2 * j + 1) * key_nlimb + kt) * N + k];
         }
+#pragma unroll 2
         for (int c = 0; c < nct; c++) {
             // the key is stored in Montgomery form: sum of d_j (k_j 2^64 mod m) < ndig m^2,
             // below m 2^64, reduced once
@@ -749,7 +758,8 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
 // Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
 template <int LOGE>
 __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const uint64_t *tw, int logN) {
+                                                         const ModC *mods, const uint64_t *tw, int logN,
+                                                         const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
     constexpr int SUB = 256 / TPS;                         // columns per CTA
     __shared__ uint64_t sm[S * SUB];
@@ -759,9 +769,11 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
     const uint64_t q = mods[p].q;
     const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
     const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = blockIdx.x * SUB + c;
+    // out of place when src is given: read limb l of src, write base
+    const uint64_t *in = src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a;
     uint64_t v[E];
 #pragma unroll
-    for (int j = 0; j < E; j++) v[j] = a[(long)(k + E * j) * N2 + col];
+    for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
     // stages m = 1 .. E/2: element index r = k + E j, group = j / (2t) (independent of k)
     ct_stages_strided<LOGE>(v, 1, 0, 0, psi, psip, q);
 #pragma unroll
@@ -821,7 +833,8 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
 // Inverse row pass: stages h = N/2 .. N1 (t = 1 .. N2/2).
 template <int LOGE>
 __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const uint64_t *tw, int logN) {
+                                                         const ModC *mods, const uint64_t *tw, int logN,
+                                                         const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
@@ -834,10 +847,12 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int 
     const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
     const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
     uint64_t *g = a + (long)row * S;
+    // out of place when src is given: read limb l of src, write base
+    const uint64_t *gi = (src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a) + (long)row * S;
     uint64_t v[E];
     // coalesced load, then regroup to the E k + j layout through shared memory
 #pragma unroll
-    for (int j = 0; j < E; j++) sm[rr * SP + k + (E + 1) * j] = g[k + E * j];
+    for (int j = 0; j < E; j++) sm[rr * SP + k + (E + 1) * j] = gi[k + E * j];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = sm[rr * SP + (E + 1) * k + j];
@@ -884,20 +899,22 @@ __global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int npe
 
 template <int LOGE>
 static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
-                      const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st) {
+                      const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st,
+                      const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, SUB = 256 / E;
     dim3 g(((1 << logN) / S) / SUB, count);
     if (!inverse) {
-        k_ntt_cols_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
+        k_ntt_cols_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN, src, src_stride);
         k_ntt_rows_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
     } else {
-        k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
+        k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN, src, src_stride);
         k_ntt_cols_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, ninv, logN);
     }
 }
 
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
-                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st) {
-    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st);
-    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st);
+                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st,
+                   const uint64_t *src, long src_stride) {
+    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st, src, src_stride);
+    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st, src, src_stride);
 }

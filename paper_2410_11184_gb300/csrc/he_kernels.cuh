@@ -56,14 +56,15 @@ __global__ void k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *
 __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap, const ModC *mods, int logN);
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
-                        int logN);
+                        int logN, const uint64_t *xntt, long sxn);
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN);
 __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
-                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN, int accumulate);
-__global__ void k_ks_inner(uint64_t *acc, const uint64_t *dig, int nct, int ndig, int L, int alpha,
-                           LimbMap tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all,
-                           int g, int logN);
+                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN,
+                              const uint64_t *add, long sadd);
+__global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
+                           int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
+                           int nq_all, int g, int logN);
 __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,
                                  const ModC *mods, uint64_t ql, int logN);
 __global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *t, int npoly, int L, LimbMap qmap,
@@ -91,5 +92,8 @@ __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_i
 
 // register-blocked NTT of `count` limbs (N = 2^12: logE = 3, N = 2^16: logE = 4); launches
 // the column and row passes on stream st
+// the first pass reads from src (limb l of polynomial i at src + i src_stride + l N) when it is
+// not null, so the transform can be out of place
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
-                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st);
+                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st,
+                   const uint64_t *src = nullptr, long src_stride = 0);

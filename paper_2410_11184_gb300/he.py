@@ -314,13 +314,14 @@ class Context:
         return ms.value, n.value, b.value
 
     def profile_breakdown(self):
-        """{family: (launches, total_ms)} since he_profile_kernel("all") (then resets)."""
+        """{family: (launches, total_ms, algorithmic bytes)} since he_profile_kernel("all")
+        (then resets); bytes are 0 for families without a stated byte count."""
         buf = C.create_string_buffer(1 << 14)
         self.check(lib().he_profile_breakdown(self.h, buf, len(buf)))
         out = {}
         for line in buf.value.decode().splitlines():
-            name, n, ms = line.split()
-            out[name] = (int(n), float(ms))
+            name, n, ms, b = line.split()
+            out[name] = (int(n), float(ms), float(b))
         return out
 
     def selftest_bounded_wait(self, max_iter):

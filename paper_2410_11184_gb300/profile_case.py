@@ -2,6 +2,7 @@
 
   python -m paper_2410_11184_gb300.profile_case softmax   # one N=2^16 Softmax of dim 256 (1 ciphertext)
   python -m paper_2410_11184_gb300.profile_case keyswitch # 4 HMults at level 12, 64 ciphertexts
+                                                         # (inside the NVTX range "hmult")
 """
 import sys
 
@@ -33,8 +34,12 @@ def main(which):
         for t in range(top + 1):
             d[:, :, t] = rng.integers(0, q[t], (m, 2, g.n), dtype=np.uint64)
         a = g.from_coeff(d, top, 2.0 ** 42)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("hmult")  # ncu --nvtx --nvtx-include "hmult/" selects these launches
         for _ in range(4):
             g.hmult(a, a)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     print("done", which, "launches", g.launch_count())
 
