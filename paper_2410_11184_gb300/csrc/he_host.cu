@@ -82,6 +82,7 @@ struct he_ctx {
     std::vector<ModC> modc;
     ModC *d_mods = nullptr;
     uint64_t *d_tw = nullptr, *d_ninv = nullptr;
+    ulonglong2 *d_tw2 = nullptr;   // the same twiddles as (w, w') pairs for the register-blocked passes
     std::vector<std::vector<size_t>> cv_off;
     uint64_t *d_cv = nullptr;
     uint64_t *d_mdcv = nullptr, *d_pinv = nullptr, *d_qlinv = nullptr;
@@ -240,7 +241,7 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     c->launches++;
     if (rb) {
         // register-blocked passes: 16 (N = 2^16) or 8 (N = 2^12) coefficients per thread
-        launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw,
+        launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
                       c->d_ninv, c->logN, c->st, src, src_stride);
         LAUNCH_CHECK();
         return;
@@ -1467,6 +1468,18 @@ static void build_tables(he_ctx *c) {
     }
     CK(cudaMalloc(&c->d_tw, tw.size() * 8));
     CK(cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
+    {
+        std::vector<ulonglong2> tw2((size_t)nm * 2 * N);
+        for (int t = 0; t < nm; t++) {
+            const uint64_t *T = tw.data() + (size_t)t * 4 * N;
+            for (int k = 0; k < N; k++) {
+                tw2[(size_t)t * 2 * N + k] = make_ulonglong2(T[k], T[N + k]);
+                tw2[(size_t)t * 2 * N + N + k] = make_ulonglong2(T[2 * N + k], T[3 * N + k]);
+            }
+        }
+        CK(cudaMalloc(&c->d_tw2, tw2.size() * sizeof(ulonglong2)));
+        CK(cudaMemcpy(c->d_tw2, tw2.data(), tw2.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc(&c->d_ninv, ninv.size() * 8));
     CK(cudaMemcpy(c->d_ninv, ninv.data(), ninv.size() * 8, cudaMemcpyHostToDevice));
     // ModUp constants per (level, digit)
@@ -1682,7 +1695,7 @@ void he_context_destroy(he_ctx *c) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
-    void *ptrs[] = {c->d_mods, c->d_tw, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx, c->d_zeta,
+    void *ptrs[] = {c->d_mods, c->d_tw, c->d_tw2, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx, c->d_zeta,
                     c->d_rg, c->d_cdt, c->d_radix, c->d_radinv, c->d_qd, c->d_s, c->d_pk};
     for (void *q : ptrs)
         if (q) cudaFree(q);

@@ -707,8 +707,8 @@ __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_i
 // the butterfly pair (j, j + t) in stage m is psi_rev[m + group] exactly as in the radix-2
 // definition, so the result equals the one-stage-at-a-time transform.
 template <int LOGE>
-__device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase, int gmul, const uint64_t *psi,
-                                                  const uint64_t *psip, uint64_t q) {
+__device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase, int gmul, const ulonglong2 *psi,
+                                                  uint64_t q) {
     // elements j (index k + E j); stages with half-distance t = E/2, E/4, ..., 1 in units of j
     constexpr int E = 1 << LOGE;
 #pragma unroll
@@ -720,7 +720,8 @@ __device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase
             // Harvey's lazy butterfly: values stay in [0, 4q); q < 2^61 keeps 4q < 2^63
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (m / m0) * gmul + grp;
-            const uint64_t w = psi[idx], wp = psip[idx];
+            const ulonglong2 tw = __ldg(psi + idx);   // (w, w') in one 16-byte load
+            const uint64_t w = tw.x, wp = tw.y;
             uint64_t u = v[jj];
             if (u >= 2 * q) u -= 2 * q;
             const uint64_t x = v[jj + t] * w - he_mulhi(v[jj + t], wp) * q;   // in [0, 2q)
@@ -731,8 +732,8 @@ __device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase
 }
 
 template <int LOGE>
-__device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase, int gmul, const uint64_t *ipsi,
-                                                  const uint64_t *ipsip, uint64_t q) {
+__device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase, int gmul, const ulonglong2 *ipsi,
+                                                  uint64_t q) {
     // inverse of ct_stages_strided: stages in reverse order (t = 1, 2, ..., E/2 in units of j)
     constexpr int E = 1 << LOGE;
 #pragma unroll
@@ -744,7 +745,8 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
             // lazy Gentleman-Sande butterfly: inputs and outputs in [0, 2q)
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (m / m0) * gmul + grp;
-            const uint64_t w = ipsi[idx], wp = ipsip[idx];
+            const ulonglong2 tw = __ldg(ipsi + idx);
+            const uint64_t w = tw.x, wp = tw.y;
             const uint64_t u = v[jj], x = v[jj + t];
             uint64_t s = u + x;
             if (s >= 2 * q) s -= 2 * q;
@@ -758,7 +760,7 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
 // Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
 template <int LOGE>
 __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const uint64_t *tw, int logN,
+                                                         const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
     constexpr int SUB = 256 / TPS;                         // columns per CTA
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
     const int l = blockIdx.y, p = map.prime[l % nper];
     uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
     const uint64_t q = mods[p].q;
-    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
+    const ulonglong2 *psi = tw2 + (long)p * 2 * N;
     const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = blockIdx.x * SUB + c;
     // out of place when src is given: read limb l of src, write base
     const uint64_t *in = src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a;
@@ -775,14 +777,14 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
     // stages m = 1 .. E/2: element index r = k + E j, group = j / (2t) (independent of k)
-    ct_stages_strided<LOGE>(v, 1, 0, 0, psi, psip, q);
+    ct_stages_strided<LOGE>(v, 1, 0, 0, psi, q);
 #pragma unroll
     for (int j = 0; j < E; j++) sm[(k + E * j) * SUB + c] = v[j];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = sm[(E * k + j) * SUB + c];
     // stages m = E .. S/2 on r = E k + j: group = (E k + j) / (2t) = k * (m / E) + j / (2t)
-    ct_stages_strided<LOGE>(v, E, k, 1, psi, psip, q);
+    ct_stages_strided<LOGE>(v, E, k, 1, psi, q);
 #pragma unroll
     for (int j = 0; j < E; j++) a[(long)(E * k + j) * N2 + col] = v[j];
 }
@@ -790,7 +792,7 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
 // Forward row pass: stages m = N1 .. N/2 on rows of S = N2 contiguous coefficients.
 template <int LOGE>
 __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const uint64_t *tw, int logN) {
+                                                         const ModC *mods, const ulonglong2 *tw2, int logN) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;                         // rows per CTA
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
@@ -800,21 +802,21 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
     const int l = blockIdx.y, p = map.prime[l % nper];
     uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
     const uint64_t q = mods[p].q;
-    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
+    const ulonglong2 *psi = tw2 + (long)p * 2 * N;
     const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
     uint64_t *g = a + (long)row * S;
     uint64_t v[E];
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = g[k + E * j];
     // stages m = N1 .. N1 E/2: group = row (m / N1) + j / (2t)
-    ct_stages_strided<LOGE>(v, N1, row, 1, psi, psip, q);
+    ct_stages_strided<LOGE>(v, N1, row, 1, psi, q);
 #pragma unroll
     for (int j = 0; j < E; j++) sm[rr * SP + k + (E + 1) * j] = v[j];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = sm[rr * SP + (E + 1) * k + j];
     // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
-    ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, psip, q);
+    ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, q);
     // back to the k + E j layout through shared memory so the store is coalesced; the lazy
     // butterflies left values in [0, 4q): reduce to [0, q)
     __syncthreads();
@@ -833,7 +835,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
 // Inverse row pass: stages h = N/2 .. N1 (t = 1 .. N2/2).
 template <int LOGE>
 __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const uint64_t *tw, int logN,
+                                                         const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;
@@ -844,7 +846,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int 
     const int l = blockIdx.y, p = map.prime[l % nper];
     uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
     const uint64_t q = mods[p].q;
-    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
+    const ulonglong2 *ipsi = tw2 + (long)p * 2 * N + N;
     const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
     uint64_t *g = a + (long)row * S;
     // out of place when src is given: read limb l of src, write base
@@ -857,13 +859,13 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int 
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = sm[rr * SP + (E + 1) * k + j];
     __syncthreads();
-    gs_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, ipsi, ipsip, q);
+    gs_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, ipsi, q);
 #pragma unroll
     for (int j = 0; j < E; j++) sm[rr * SP + (E + 1) * k + j] = v[j];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = sm[rr * SP + k + (E + 1) * j];
-    gs_stages_strided<LOGE>(v, N1, row, 1, ipsi, ipsip, q);
+    gs_stages_strided<LOGE>(v, N1, row, 1, ipsi, q);
 #pragma unroll
     for (int j = 0; j < E; j++) g[k + E * j] = v[j];
 }
@@ -871,7 +873,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int 
 // Inverse column pass: stages h = N1/2 .. 1, then the N^{-1} factor.
 template <int LOGE>
 __global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const uint64_t *tw, const uint64_t *ninv,
+                                                         const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv,
                                                          int logN) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;
@@ -880,18 +882,18 @@ __global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int npe
     const int l = blockIdx.y, p = map.prime[l % nper];
     uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
     const uint64_t q = mods[p].q;
-    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
+    const ulonglong2 *ipsi = tw2 + (long)p * 2 * N + N;
     const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = blockIdx.x * SUB + c;
     uint64_t v[E];
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = a[(long)(E * k + j) * N2 + col];
-    gs_stages_strided<LOGE>(v, E, k, 1, ipsi, ipsip, q);
+    gs_stages_strided<LOGE>(v, E, k, 1, ipsi, q);
 #pragma unroll
     for (int j = 0; j < E; j++) sm[(E * k + j) * SUB + c] = v[j];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = sm[(k + E * j) * SUB + c];
-    gs_stages_strided<LOGE>(v, 1, 0, 0, ipsi, ipsip, q);
+    gs_stages_strided<LOGE>(v, 1, 0, 0, ipsi, q);
     const uint64_t ni = ninv[2 * p], nip = ninv[2 * p + 1];
 #pragma unroll
     for (int j = 0; j < E; j++) a[(long)(k + E * j) * N2 + col] = mul_shoup(v[j], ni, nip, q);
@@ -899,22 +901,22 @@ __global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int npe
 
 template <int LOGE>
 static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
-                      const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st,
+                      const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
                       const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, SUB = 256 / E;
     dim3 g(((1 << logN) / S) / SUB, count);
     if (!inverse) {
-        k_ntt_cols_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN, src, src_stride);
-        k_ntt_rows_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN);
+        k_ntt_cols_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
+        k_ntt_rows_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN);
     } else {
-        k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, logN, src, src_stride);
-        k_ntt_cols_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw, ninv, logN);
+        k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
+        k_ntt_cols_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, ninv, logN);
     }
 }
 
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
-                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st,
+                   const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
                    const uint64_t *src, long src_stride) {
-    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st, src, src_stride);
-    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw, ninv, logN, st, src, src_stride);
+    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride);
+    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride);
 }

@@ -94,6 +94,7 @@ __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_i
 // the column and row passes on stream st
 // the first pass reads from src (limb l of polynomial i at src + i src_stride + l N) when it is
 // not null, so the transform can be out of place
+// tw2: per modulus p, N (psi^brv(k), Shoup companion) pairs at tw2 + 2 N p, then N inverse pairs
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
-                   const ModC *mods, const uint64_t *tw, const uint64_t *ninv, int logN, cudaStream_t st,
+                   const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
                    const uint64_t *src = nullptr, long src_stride = 0);
