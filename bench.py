@@ -101,6 +101,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the two forward NTT passes per
+# algorithmic byte (16 N per limb), from one capture of a 512-limb ModUp transform at N = 2^16
+# (python -m paper_2410_11184_gb300.profile_case keyswitch): 1.875 MB per 1.049 MB limb
+NTT_DRAM_PER_ALG_BYTE = 1.875e6 / (16 * 65536)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -238,11 +244,13 @@ def main():
         clocks.start()
         barrier()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include "timed/" selects these launches
         ev[0].record(stream)
         for i in range(args.steps):
             step(True)
             ev[i + 1].record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
         clk = clocks.stop()
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
@@ -305,8 +313,9 @@ def main():
     roof = None
     if k_launch:
         achieved = (k_bytes / k_launch) / ((k_ms / k_launch) * 1e-3) / 1e9
+        traffic = (k_bytes / k_launch) * NTT_DRAM_PER_ALG_BYTE if args.profile_kernel == "ntt" else None
         roof = {"bound": "hbm", "kernel": args.profile_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
                 "launches_per_step": k_launch / args.steps, "kernel_ms_per_step": k_ms / args.steps,
                 "share_of_step": (k_ms / args.steps) / ms_step}
     line = {
