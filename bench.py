@@ -159,8 +159,9 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # key-switch count per Softmax step of this workload, from the circuit's operation list
-    ks_per_step = {"m64": 5700, "m1": 760}[args.workload]
+    # ciphertext key switches per Softmax step of this workload (the circuit's operation list, as
+    # counted by he_counters on the GPU path: 64-ciphertext batch / one ciphertext)
+    ks_per_step = {"m64": 8249, "m1": 875}[args.workload]
     L = wl["m"] * 32768 // wl["n"]
     vals = []
     for _ in range(args.warmup + args.steps):
