@@ -107,6 +107,13 @@ int he_encrypt_slots(he_ctx *ctx, const double *slots, int level, double scale, 
  * batched = 1: every operation runs over all m ciphertexts in one launch (key read once);
  * batched = 0: the same operation list, one ciphertext at a time. */
 int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched);
+/* he_softmax (batched) as one CUDA graph: the first call for a given (cts->data, level, scale,
+ * n_ct, plan) runs the circuit once on a scratch copy (filling the key, diagonal and mask caches),
+ * captures it on the context stream and launches the captured graph; later calls with the same
+ * buffer and shape launch the graph again (no host work per kernel).  Results are those of
+ * he_softmax bit for bit.  Graphs live until he_context_destroy; the buffer must stay allocated
+ * while its graph may be launched. */
+int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts);
 
 /* ---- the hot-path operations, one call each (device buffers as above) ---- */
 /* negacyclic NTT (inverse=0) / inverse NTT of n_limb limbs mod q_0.. in place (device) */
@@ -159,7 +166,10 @@ int he_counters(const he_ctx *ctx, long *out5);
 long he_launch_count(const he_ctx *ctx);
 /* live timing of one kernel family ("ntt", "ks_inner", "modup", "tensor"; "" = off): CUDA
  * events on the context stream around each launch; he_profile_read synchronises, returns the
- * summed device time, the launch count and the algorithmic bytes of those launches, and resets */
+ * summed device time, the launch count and the algorithmic bytes of those launches, and resets.
+ * A graph captured by he_softmax_graph while a family is profiled carries that family's events
+ * inside (event-record nodes, recorded at every launch of the graph); a read counts the latest
+ * launch of each graph launched since the previous read. */
 int he_profile_kernel(he_ctx *ctx, const char *name);
 int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes);
 /* with he_profile_kernel(ctx, "all"): every launch and device copy is timed; this call

@@ -101,6 +101,29 @@ struct he_ctx {
     std::map<int, uint64_t *> keys;
     int ndig_top = 0;
     std::map<std::string, LtLevel> lt_cache;
+    std::map<std::string, DPtr> pt_cache;   // Softmax masks, encoded once per (level, scale, stride)
+    struct ProfRec {
+        const char *fam;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    struct SmGraph {
+        cudaGraphExec_t exec = nullptr;
+        int level = 0;
+        double scale = 0;
+        long launches = 0;
+        long cnt[5] = {0, 0, 0, 0, 0};
+        std::vector<ProfRec> prof;   // timing events captured into the graph (profiling on)
+        bool replayed = false;       // launched since the last he_profile_read/breakdown
+    };
+    std::vector<ProfRec> cap_prof;   // events recorded while capturing
+    // graphs are captured and launched on a stream of their own (the context stream may be the
+    // legacy default stream, which cannot be captured), ordered after / before the context
+    // stream by events
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    std::map<std::string, SmGraph> graphs;  // captured Softmax circuits (he_softmax_graph)
+    bool capturing = false;
     uint64_t *noalloc_scratch = nullptr;   // device address of g_rescale_scratch on this device
     cudaStream_t st = nullptr;
     std::string err;
@@ -123,9 +146,20 @@ struct ProfScope {
     he_ctx *c;
     bool on;
     size_t slot;
-    ProfScope(he_ctx *c_, const char *name, double bytes)
-        : c(c_), on(match(c_->prof_name, name)) {
+    bool cap = false;
+    ProfScope(he_ctx *c_, const char *name, double bytes) : c(c_), on(match(c_->prof_name, name)) {
         if (!on) return;
+        if (c->capturing) {
+            // inside a graph capture: external event-record nodes, owned by the graph
+            cap = true;
+            he_ctx::ProfRec r{name, bytes, nullptr, nullptr};
+            cudaEventCreate(&r.a);
+            cudaEventCreate(&r.b);
+            cudaEventRecordWithFlags(r.a, c->st, cudaEventRecordExternal);
+            c->cap_prof.push_back(r);
+            slot = c->cap_prof.size() - 1;
+            return;
+        }
         if (c->prof_used == c->prof_ev.size()) {
             cudaEvent_t a, b;
             cudaEventCreate(&a);
@@ -148,7 +182,9 @@ struct ProfScope {
         return strncmp(name, want.c_str(), n) == 0 && name[n] == '_';
     }
     ~ProfScope() {
-        if (on) cudaEventRecord(c->prof_ev[slot].second, c->st);
+        if (!on) return;
+        if (cap) cudaEventRecordWithFlags(c->cap_prof[slot].b, c->st, cudaEventRecordExternal);
+        else cudaEventRecord(c->prof_ev[slot].second, c->st);
     }
 };
 
@@ -1402,8 +1438,11 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         for (int i = 0; i < stride; i++) mk[i].x = mval;
         double smk = (slam * qd(c, lm)) / lam.scale;
         if (lam_bts) smk = smk / p.gl[j];
-        DPtr pt = encode(c, mk, smk, lm);
-        ct_mul_plain(c, lam, pt.get());
+        char mkey[128];
+        snprintf(mkey, sizeof mkey, "mask:%d:%d:%a:%a", stride, lm, mval, smk);
+        auto mit = c->pt_cache.find(mkey);
+        if (mit == c->pt_cache.end()) mit = c->pt_cache.emplace(mkey, encode(c, mk, smk, lm)).first;
+        ct_mul_plain(c, lam, mit->second.get());
         lam.scale = lam.scale * smk;
         lam = rescale(c, lam);
         lam = rotsum(c, lam, stride, nrot);
@@ -1689,6 +1728,21 @@ int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out) {
 void he_context_destroy(he_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    if (c->gstream) cudaStreamSynchronize(c->gstream);
+    for (auto &kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (auto &r : kv.second.prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+    }
+    c->graphs.clear();
+    if (c->gstream) {
+        cudaStreamDestroy(c->gstream);
+        cudaEventDestroy(c->gev_in);
+        cudaEventDestroy(c->gev_out);
+    }
+    c->pt_cache.clear();
     c->lt_cache.clear();
     for (auto &kv : c->keys) cudaFree(kv.second);
     for (auto &e : c->prof_ev) {
@@ -1822,14 +1876,19 @@ static Plan plan_of(he_ctx *c, const he_softmax_plan *hp) {
     return p;
 }
 
-int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched) {
+static int softmax_check(he_ctx *ctx, const he_softmax_plan *plan, const he_ct *cts) {
     if (!ctx || !plan || !cts || !cts->data || cts->n_ct < 1 || plan->k < 1 || plan->k > 16) return HE_EINVAL;
     int m = cts->n_ct, n = plan->n;
     if (n < 1 || (n & (n - 1)) || n % m || ctx->n0 % n) {
         ctx->err = "n must be a power of two dividing N/2, and m must divide n";
         return HE_EINVAL;
     }
-    API_BEGIN
+    return HE_OK;
+}
+
+// the Softmax circuit on the m ciphertexts of cts, in place
+static void softmax_inplace(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, bool batched) {
+    int m = cts->n_ct;
     Plan p = plan_of(ctx, plan);
     DCt in = ct_view(cts);
     std::vector<DCt> ys;
@@ -1849,7 +1908,117 @@ int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched
     }
     cts->level = lo;
     cts->scale = ys[0].scale;
-    ys.clear();
+}
+
+int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched) {
+    int rc = softmax_check(ctx, plan, cts);
+    if (rc) return rc;
+    API_BEGIN
+    softmax_inplace(ctx, plan, cts, batched != 0);
+    API_END
+}
+
+// FNV-1a over the bytes of the plan's numbers: graphs are reused only for the same circuit
+static uint64_t plan_hash(const he_softmax_plan *hp) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const void *p, size_t n) {
+        const unsigned char *b = (const unsigned char *)p;
+        for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    mix(&hp->n, sizeof hp->n);
+    mix(&hp->k, sizeof hp->k);
+    mix(&hp->M, sizeof hp->M);
+    mix(&hp->bts_boost, sizeof hp->bts_boost);
+    mix(&hp->exp_deg, sizeof hp->exp_deg);
+    mix(hp->exp_coeffs, sizeof(double) * (hp->exp_deg + 1));
+    mix(hp->inv_deg, sizeof(int) * hp->k);
+    size_t nc = 0;
+    for (int j = 0; j < hp->k; j++) nc += hp->inv_deg[j] + 1;
+    mix(hp->inv_coeffs, sizeof(double) * nc);
+    mix(hp->inv_a, sizeof(double) * hp->k);
+    mix(hp->inv_b, sizeof(double) * hp->k);
+    mix(hp->gain_s, sizeof(double) * hp->k);
+    mix(hp->gain_l, sizeof(double) * hp->k);
+    return h;
+}
+
+int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts) {
+    int rc = softmax_check(ctx, plan, cts);
+    if (rc) return rc;
+    API_BEGIN
+    char key[160];
+    snprintf(key, sizeof key, "%p:%d:%a:%d:%016llx", (void *)cts->data, cts->level, cts->scale, cts->n_ct,
+             (unsigned long long)plan_hash(plan));
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        // 1. an eager run on a copy fills the key, diagonal and mask caches (nothing is
+        //    encoded or allocated outside the stream during the capture)
+        {
+            size_t words = (size_t)cts->n_ct * 2 * (cts->level + 1) * ctx->N;
+            DPtr tmp = dalloc(ctx, words);
+            CK(cudaMemcpyAsync(tmp.get(), cts->data, words * 8, cudaMemcpyDeviceToDevice, ctx->st));
+            he_ct t = *cts;
+            t.data = tmp.get();
+            softmax_inplace(ctx, plan, &t, true);
+        }
+        // 2. capture the circuit on the context stream (temporaries become graph allocations)
+        he_ctx::SmGraph gr;
+        long l0 = ctx->launches, c0[5];
+        for (int i = 0; i < 5; i++) c0[i] = ctx->cnt[i];
+        he_ct out = *cts;
+        cudaGraph_t graph = nullptr;
+        if (!ctx->gstream) {
+            CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ctx->gev_in, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->gev_out, cudaEventDisableTiming));
+        }
+        cudaStream_t user = ctx->st;
+        ctx->st = ctx->gstream;   // everything below is recorded into the graph
+        CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        ctx->cap_prof.clear();
+        try {
+            softmax_inplace(ctx, plan, &out, true);
+        } catch (...) {
+            ctx->capturing = false;
+            cudaStreamEndCapture(ctx->st, &graph);
+            ctx->st = user;
+            if (graph) cudaGraphDestroy(graph);
+            for (auto &r : ctx->cap_prof) {
+                cudaEventDestroy(r.a);
+                cudaEventDestroy(r.b);
+            }
+            ctx->cap_prof.clear();
+            throw;
+        }
+        ctx->capturing = false;
+        gr.prof.swap(ctx->cap_prof);
+        cudaError_t ec = cudaStreamEndCapture(ctx->st, &graph);
+        ctx->st = user;
+        CK(ec);
+        cudaError_t e = cudaGraphInstantiate(&gr.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        gr.level = out.level;
+        gr.scale = out.scale;
+        gr.launches = ctx->launches - l0;
+        for (int i = 0; i < 5; i++) gr.cnt[i] = ctx->cnt[i] - c0[i];
+        // the capture only recorded the work: count it at each launch below
+        ctx->launches = l0;
+        for (int i = 0; i < 5; i++) ctx->cnt[i] = c0[i];
+        it = ctx->graphs.emplace(key, gr).first;
+    }
+    he_ctx::SmGraph &gr = it->second;
+    CK(cudaEventRecord(ctx->gev_in, ctx->st));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev_in, 0));
+    CK(cudaGraphLaunch(gr.exec, ctx->gstream));
+    CK(cudaEventRecord(ctx->gev_out, ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->st, ctx->gev_out, 0));
+    gr.replayed = true;
+    ctx->launches += gr.launches;
+    for (int i = 0; i < 5; i++) ctx->cnt[i] += gr.cnt[i];
+    cts->level = gr.level;
+    cts->scale = gr.scale;
     API_END
 }
 
@@ -2029,15 +2198,27 @@ int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes
     if (!ctx || !total_ms || !launches || !bytes) return HE_EINVAL;
     API_BEGIN
     CK(cudaStreamSynchronize(ctx->st));
-    double t = 0;
+    double t = 0, by = ctx->prof_bytes;
+    long n = (long)ctx->prof_used;
     for (size_t i = 0; i < ctx->prof_used; i++) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, ctx->prof_ev[i].first, ctx->prof_ev[i].second));
         t += ms;
     }
+    for (auto &kv : ctx->graphs) {
+        if (!kv.second.replayed) continue;
+        for (const auto &r : kv.second.prof) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            t += ms;
+            by += r.bytes;
+            n++;
+        }
+        kv.second.replayed = false;
+    }
     *total_ms = t;
-    *launches = (long)ctx->prof_used;
-    *bytes = ctx->prof_bytes;
+    *launches = n;
+    *bytes = by;
     ctx->prof_used = 0;
     ctx->prof_bytes = 0;
     API_END
@@ -2055,6 +2236,18 @@ int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len) {
         std::get<0>(f)++;
         std::get<1>(f) += ms;
         std::get<2>(f) += ctx->prof_b[i];
+    }
+    for (auto &kv : ctx->graphs) {
+        if (!kv.second.replayed) continue;
+        for (const auto &r : kv.second.prof) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            auto &f = fam[r.fam];
+            std::get<0>(f)++;
+            std::get<1>(f) += ms;
+            std::get<2>(f) += r.bytes;
+        }
+        kv.second.replayed = false;
     }
     std::string out;
     for (const auto &kv : fam) {

@@ -63,6 +63,7 @@ def lib():
             "he_decrypt_slots": [vp, C.POINTER(he_ct), C.c_int, dblp],
             "he_encrypt_slots": [vp, dblp, C.c_int, C.c_double, C.c_uint64, C.c_int, C.POINTER(he_ct), C.c_int],
             "he_softmax": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct), C.c_int],
+            "he_softmax_graph": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct)],
             "he_ntt": [vp, vp, C.c_int, C.c_int, C.c_int],
             "he_ct_to_coeff": [vp, C.POINTER(he_ct), u64p],
             "he_ct_from_coeff": [vp, u64p, C.POINTER(he_ct)],
@@ -213,10 +214,17 @@ class Context:
         self.check(lib().he_decrypt_slots(self.h, C.byref(h), ct, buf.ctypes.data_as(dblp)))
         return buf[0::2] + 1j * buf[1::2]
 
-    def softmax(self, cts, plan, batched=True):
+    def softmax(self, cts, plan, batched=True, graph=False):
+        """he_softmax in place; graph=True: he_softmax_graph (captured once per buffer and
+        shape, replayed afterwards; batched only)."""
         pl = Plan(plan)
         h = cts.c()
-        self.check(lib().he_softmax(self.h, C.byref(pl.s), C.byref(h), 1 if batched else 0))
+        if graph:
+            if not batched:
+                raise ValueError("graph replay runs the batched form")
+            self.check(lib().he_softmax_graph(self.h, C.byref(pl.s), C.byref(h)))
+        else:
+            self.check(lib().he_softmax(self.h, C.byref(pl.s), C.byref(h), 1 if batched else 0))
         cts.update(h)
         return cts
 

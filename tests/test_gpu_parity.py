@@ -208,3 +208,33 @@ def test_softmax_bootstrapped_bit_exact(toybts, params, batched):
     for i in range(m):
         assert np.array_equal(got[i], outs[i].data), i
     assert np.abs(g.decrypt(gc, n) - O.softmax_fp64(x)).max() < 2 ** -15
+
+
+def test_softmax_graph_replay_bit_exact(toybts, params):
+    """he_softmax_graph: captured on the first call, replayed on the next ones; every result
+    equals the oracle's Softmax limb for limb, and the replay counts the captured launches."""
+    g, o, em = toybts
+    pl = params[1]["toybts_n16_M32"]
+    n, m = pl["n"], 2
+    g.keygen_softmax(n, m)
+    rng = np.random.default_rng(19)
+    L = m * o.n0 // n
+    x = rng.uniform(-pl["M"], 0, (L, n))
+    src = g.encrypt(x, n, m, pl["M"], 33)
+    top = o.chain["user_top_level"]
+    slots = O.pack(x, m, o.n0)
+    outs = o.softmax([o.encrypt(slots[i], top, (2 / pl["M"]) * o.q[top], 33, i) for i in range(m)], pl, em)
+    work = g.like(src)
+    per_call = []
+    for call in range(3):
+        work.tensor.copy_(src.tensor)
+        work.level, work.scale, work.n_ct = src.level, src.scale, src.n_ct
+        l0 = g.launch_count()
+        g.softmax(work, pl, graph=True)
+        per_call.append(g.launch_count() - l0)
+        assert work.level == outs[0].level and work.scale == outs[0].scale, call
+        got = g.to_coeff(work)
+        for i in range(m):
+            assert np.array_equal(got[i], outs[i].data), (call, i)
+    # the first call also ran the circuit once eagerly to fill the caches
+    assert per_call[1] == per_call[2] > 0 and per_call[0] >= 2 * per_call[1]
