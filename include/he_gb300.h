@@ -107,6 +107,13 @@ int he_encrypt_slots(he_ctx *ctx, const double *slots, int level, double scale, 
  * batched = 1: every operation runs over all m ciphertexts in one launch (key read once);
  * batched = 0: the same operation list, one ciphertext at a time. */
 int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched);
+/* groups independent Softmax batches in one batched pass: the n_ct ciphertexts are groups
+ * consecutive groups of m = n_ct / groups ciphertexts, each packed as in Sec. 4.2 (its own
+ * L = m N0 / n Softmax); the sum of squares stays inside each group and the auxiliary thread
+ * (Alg. 3) runs over a batch of groups ciphertexts.  Every group's result equals he_softmax on
+ * that group alone, bit for bit (all groups share level and scale).  This is how a server batches
+ * requests that arrive separately. */
+int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int groups);
 /* he_softmax (batched) as one CUDA graph: the first call for a given (cts->data, level, scale,
  * n_ct, plan) runs the circuit once on a scratch copy (filling the key, diagonal and mask caches),
  * captures it on the context stream and launches the captured graph; later calls with the same

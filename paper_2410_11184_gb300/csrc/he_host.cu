@@ -578,6 +578,19 @@ static DCt hmult(he_ctx *c, const DCt &a, const DCt &b) {
     return rescale(c, r);
 }
 
+// lam (G ciphertexts) times y (G groups of m ciphertexts): ciphertext i of y with lam[i / m]
+static DCt hmult_grouped(he_ctx *c, const DCt &lam, const DCt &y, int m) {
+    int level = std::min(lam.level, y.level);
+    REQUIRE(level >= 1, HE_ELEVEL, "hmult at level 0");
+    REQUIRE(y.nct == lam.nct * m, HE_EINVAL, "hmult_grouped: batch sizes");
+    DPtr d = dalloc(c, (size_t)y.nct * 3 * (level + 1) * c->N);
+    for (int i = 0; i < y.nct; i++)
+        tensor_into(c, d.get() + (long)i * 3 * (level + 1) * c->N, ct_sub(c, y, i), ct_sub(c, lam, i / m), level, false);
+    DCt r = relinearize(c, d.get(), level, y.nct, lam.scale * y.scale);
+    c->cnt[2]++;
+    return rescale(c, r);
+}
+
 // Rot by galois elements: ModUp(c1) once, then for every g: X -> X^g on the digits and c0,
 // inner product with swk(s(X^g) -> s), ModDown.
 // y.c0 += x.c0(X^g) for every ciphertext of the batch
@@ -1342,8 +1355,11 @@ static void dbg_dump(he_ctx *c, const char *what, int j, const DCt &x) {
     fclose(f);
 }
 
-// ys: the m main-thread ciphertexts, as one batch (batched) or m batches of one
-static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> ys, int m) {
+// ys: the m main-thread ciphertexts, as one batch (batched) or m batches of one; with G > 1
+// (batched only) ys[0] holds G independent groups of m ciphertexts each (G m ciphertexts): the
+// sum of squares stays inside each group and the auxiliary thread runs over a batch of G
+static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> ys, int m, int G = 1) {
+    REQUIRE(G == 1 || (ys.size() == 1 && ys[0].nct == G * m), HE_EINVAL, "softmax: groups need one batch");
     int n0 = c->n0, n = p.n;
     int stride = (int)((long)m * n0 / n);
     int nrot = ilog2c(n / m);
@@ -1363,11 +1379,32 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
             ly = ys[0].level;
             dbg_dump(c, "ybts", j, ys[0]);
         }
-        // S = Relin(sum_c y_c (x) y_c)
+        // S = Relin(sum_c y_c (x) y_c), one sum per group
         int L = ly + 1;
-        DPtr d = dalloc(c, (size_t)3 * L * c->N);
+        DPtr d = dalloc(c, (size_t)G * 3 * L * c->N);
         bool first = true;
+        if (G > 1) {
+            const DCt &y = ys[0];
+            long t3 = 3L * L * c->N;
+            DPtr dd = m > 1 ? dalloc(c, (size_t)y.nct * t3) : DPtr();
+            tensor_into(c, m > 1 ? dd.get() : d.get(), y, y, ly, false);
+            // group g: d[g] = sum_i dd[g m + i] (3 polynomials of L limbs each)
+            for (int g = 0; m > 1 && g < G; g++) {
+                for (int i = 1; i < m; i++) {
+                    const uint64_t *acc = i == 1 ? dd.get() + (long)g * m * t3 : d.get() + g * t3;
+                    {
+                        ProfScope ps_(c, "elementwise", 0);
+                        k_add<<<grid_for(c, t3), 256, 0, c->st>>>(d.get() + g * t3, (long)L * c->N, acc, (long)L * c->N,
+                                                                   dd.get() + ((long)g * m + i) * t3, (long)L * c->N,
+                                                                   3 * L, L, qmap(L), c->d_mods, c->logN, 0);
+                    }
+                    LAUNCH_CHECK();
+                }
+            }
+            first = false;
+        }
         for (auto &y : ys) {
+            if (G > 1) break;
             if (y.nct == 1) {
                 tensor_into(c, d.get(), y, y, ly, !first);
                 first = false;
@@ -1394,7 +1431,7 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
                 first = false;
             }
         }
-        DCt S = relinearize(c, d.get(), ly, 1, ys[0].scale * ys[0].scale);
+        DCt S = relinearize(c, d.get(), ly, G, ys[0].scale * ys[0].scale);
         c->cnt[2]++;
         S = rescale(c, S);
         S = rotsum(c, S, stride, nrot);
@@ -1450,7 +1487,7 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         dbg_dump(c, "lamf", j, lam);
         double soz = zb ? sqrt(y_target(c, p, j + 1, ut - 1) * qd(c, ut)) : 0.0;
         for (auto &y : ys) {
-            DCt z = hmult(c, lam, y);
+            DCt z = G > 1 && m > 1 ? hmult_grouped(c, lam, y, m) : hmult(c, lam, y);
             if (zb) z = bts_boosted(c, p, z, 1.0, soz);
             y = hmult(c, z, z);
         }
@@ -1876,9 +1913,13 @@ static Plan plan_of(he_ctx *c, const he_softmax_plan *hp) {
     return p;
 }
 
-static int softmax_check(he_ctx *ctx, const he_softmax_plan *plan, const he_ct *cts) {
+static int softmax_check(he_ctx *ctx, const he_softmax_plan *plan, const he_ct *cts, int groups = 1) {
     if (!ctx || !plan || !cts || !cts->data || cts->n_ct < 1 || plan->k < 1 || plan->k > 16) return HE_EINVAL;
-    int m = cts->n_ct, n = plan->n;
+    if (groups < 1 || cts->n_ct % groups) {
+        ctx->err = "groups must divide the ciphertext count";
+        return HE_EINVAL;
+    }
+    int m = cts->n_ct / groups, n = plan->n;
     if (n < 1 || (n & (n - 1)) || n % m || ctx->n0 % n) {
         ctx->err = "n must be a power of two dividing N/2, and m must divide n";
         return HE_EINVAL;
@@ -1886,22 +1927,23 @@ static int softmax_check(he_ctx *ctx, const he_softmax_plan *plan, const he_ct *
     return HE_OK;
 }
 
-// the Softmax circuit on the m ciphertexts of cts, in place
-static void softmax_inplace(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, bool batched) {
-    int m = cts->n_ct;
+// the Softmax circuit on the ciphertexts of cts (groups independent groups), in place
+static void softmax_inplace(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, bool batched, int groups = 1) {
+    int m = cts->n_ct / groups;
     Plan p = plan_of(ctx, plan);
     DCt in = ct_view(cts);
     std::vector<DCt> ys;
     if (batched) {
         ys.push_back(ct_copy(ctx, in));
     } else {
+        REQUIRE(groups == 1, HE_EINVAL, "groups need the batched form");
         for (int i = 0; i < m; i++) ys.push_back(ct_copy(ctx, ct_sub(ctx, in, i)));
     }
-    ys = softmax_run(ctx, p, ys, m);
+    ys = softmax_run(ctx, p, ys, m, batched ? groups : 1);
     int lo = ys[0].level;
     long cs = 2L * (lo + 1) * ctx->N;
     if (batched) {
-        CK(cudaMemcpyAsync(cts->data, ys[0].d, (size_t)m * cs * 8, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(cts->data, ys[0].d, (size_t)cts->n_ct * cs * 8, cudaMemcpyDeviceToDevice, ctx->st));
     } else {
         for (int i = 0; i < m; i++)
             CK(cudaMemcpyAsync(cts->data + i * cs, ys[i].d, (size_t)cs * 8, cudaMemcpyDeviceToDevice, ctx->st));
@@ -1915,6 +1957,14 @@ int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched
     if (rc) return rc;
     API_BEGIN
     softmax_inplace(ctx, plan, cts, batched != 0);
+    API_END
+}
+
+int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int groups) {
+    int rc = softmax_check(ctx, plan, cts, groups);
+    if (rc) return rc;
+    API_BEGIN
+    softmax_inplace(ctx, plan, cts, true, groups);
     API_END
 }
 

@@ -302,7 +302,18 @@ def build_all(write=True):
         # bootstrapping-path checks at N=2^12: dim 16 on [-32, 0], k = 4
         "toybts_n16_M32": design_softmax("toybts_n16_M32", "toybts", 16, 32.0, 4, 15,
                                          [15, 15, 15, 31]),
+        # a second dimension at N=2^12 for the mixed-dimension serving checks: dim 64, k = 3
+        "toybts_n64_M32": design_softmax("toybts_n64_M32", "toybts", 64, 32.0, softmax_k(32, 64), 15,
+                                         [63, 31, 63]),
     }
+    # serving mix at N=2^16 (inputs on [-64, 0]) besides n128_M64: k = 4 by Thm 3.3 for both;
+    # at n = 1024 the last round needs degree 255 (alpha 1.4e-7; 127 leaves 2.5e-2).  Dims 4096
+    # and 32768 are not designed: x^{-1/2} on [(1 - alpha)^2 / n, (1 + alpha)^2] keeps alpha
+    # above 0.25 with degree-63 rounds (above 1 at n = 32768), so the iteration does not converge
+    # within the chain's levels between bootstrappings
+    plans["n256_M64"] = design_softmax("n256_M64", "fgb16", 256, 64.0, softmax_k(64, 256), 15, [63, 31, 31, 127])
+    plans["n1024_M64"] = design_softmax("n1024_M64", "fgb16", 1024, 64.0, softmax_k(64, 1024), 15,
+                                        [63, 63, 63, 255])
     evalmod = {"fgb16": design_evalmod(25.0, 3, 63), "toybts": design_evalmod(25.0, 3, 63)}
     if write:
         os.makedirs(PARAMS_DIR, exist_ok=True)

@@ -64,6 +64,7 @@ def lib():
             "he_encrypt_slots": [vp, dblp, C.c_int, C.c_double, C.c_uint64, C.c_int, C.POINTER(he_ct), C.c_int],
             "he_softmax": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct), C.c_int],
             "he_softmax_graph": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct)],
+            "he_softmax_grouped": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct), C.c_int],
             "he_ntt": [vp, vp, C.c_int, C.c_int, C.c_int],
             "he_ct_to_coeff": [vp, C.POINTER(he_ct), u64p],
             "he_ct_from_coeff": [vp, u64p, C.POINTER(he_ct)],
@@ -225,6 +226,15 @@ class Context:
             self.check(lib().he_softmax_graph(self.h, C.byref(pl.s), C.byref(h)))
         else:
             self.check(lib().he_softmax(self.h, C.byref(pl.s), C.byref(h), 1 if batched else 0))
+        cts.update(h)
+        return cts
+
+    def softmax_grouped(self, cts, plan, groups):
+        """he_softmax_grouped in place: `groups` independent Softmax batches of
+        cts.n_ct / groups ciphertexts each."""
+        pl = Plan(plan)
+        h = cts.c()
+        self.check(lib().he_softmax_grouped(self.h, C.byref(pl.s), C.byref(h), groups))
         cts.update(h)
         return cts
 
