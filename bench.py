@@ -180,18 +180,100 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
+def run_serve(args):
+    """Serving workload: Poisson arrivals of one-ciphertext encrypted Softmax requests whose
+    dimension is drawn from {128, 256, 1024} (inputs uniform on [-64, 0], N = 2^16 with
+    bootstrapping), admitted by HBM budget and batched by shape (serve.Server).  Prints one JSON
+    line with p50/p99 request latency, Softmax/s and the worst-case error per dimension."""
+    import torch
+
+    from paper_2410_11184_gb300 import he, serve, workloads
+
+    chains, plans, evalmod = he.load_params()
+    names = ["n128_M64", "n256_M64", "n1024_M64"]
+    g = he.Context(chains["fgb16"], evalmod["fgb16"])
+    g.keygen(5)
+    for nm in names:
+        g.keygen_softmax(plans[nm]["n"], 1)
+    rng = np.random.default_rng(args.seed)
+    pool = {}
+    for nm in names:   # a few distinct encrypted inputs per dimension, in pinned host memory
+        pl = plans[nm]
+        L = g.n0 // pl["n"]
+        for v in range(3):
+            x = workloads.uniform_inputs(L, pl["n"], 1000 + 10 * pl["n"] + v, pl["M"])
+            ct = g.encrypt(x, pl["n"], 1, pl["M"], 77 + v)
+            host = torch.empty(ct.tensor.numel(), dtype=torch.int64).pin_memory()
+            host.copy_(ct.tensor)
+            pool[(nm, v)] = (x, host, ct.level, ct.scale)
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    budget = 0.5 * free
+    srv = serve.Server(g, {nm: plans[nm] for nm in names}, budget, max_batch_ct=args.max_batch_ct)
+    # warm-up: one request per dimension (first use of every plan's masks and diagonals)
+    for nm in names:
+        x, host, lv, sc = pool[(nm, 0)]
+        srv.submit(nm, host, 1, lv, sc).wait(600)
+    srv.finished.clear()
+    srv.batches.clear()
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.requests))
+    picks = [(names[rng.integers(len(names))], int(rng.integers(3))) for _ in range(args.requests)]
+    t0 = time.perf_counter()
+    handles = []
+    for t, key in zip(arrivals, picks):
+        dt = t0 + t - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        x, host, lv, sc = pool[key]
+        handles.append((key, srv.submit(key[0], host, 1, lv, sc)))
+    for _, h in handles:
+        h.wait(1800)
+    srv.close()
+    st = srv.stats()
+    # precision of every distinct result (decrypted on the device)
+    worst = {}
+    for key, h in handles:
+        x = pool[key][0]
+        n = plans[key[0]]["n"]
+        words = 2 * (h.out_level + 1) * g.n
+        ct = g.alloc(h.out_level, 1, h.out_scale)
+        ct.tensor.copy_(h.host_out[:words])
+        e = np.exp(x - x.max(axis=1, keepdims=True))
+        err = float(np.abs(g.decrypt(ct, n) - e / e.sum(axis=1, keepdims=True)).max())
+        worst[n] = max(worst.get(n, 0.0), err)
+    softmax_done = sum(g.n0 // plans[k[0]]["n"] for k, _ in handles)
+    line = {
+        "metric": "serving: request latency p50/p99 and Softmax/s (n in {128,256,1024}, N=2^16, bootstrapping)",
+        "value": st["p99_ms"], "unit": "ms (p99 request latency)", "higher_is_better": False,
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+        "softmax_per_s": softmax_done / st["span_s"], "requests": st["requests"], "span_s": st["span_s"],
+        "arrival_rate_per_s": args.rate, "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
+        "precision_bits_by_n": {str(n): -math.log2(e) if e > 0 else None for n, e in sorted(worst.items())},
+        "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
+        "config": {"workload": "Poisson arrivals, one ciphertext per request, dims 128/256/1024 on [-64, 0]",
+                   "hbm_budget_gb": budget / 1e9, "max_batch_ct": args.max_batch_ct},
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="m64", choices=["m64", "m1"])
+    ap.add_argument("--workload", default="m64", choices=["m64", "m1", "serve"])
+    ap.add_argument("--rate", type=float, default=8.0, help="serve: request arrivals per second")
+    ap.add_argument("--requests", type=int, default=64, help="serve: number of requests")
+    ap.add_argument("--max-batch-ct", type=int, default=16, help="serve: ciphertexts per batched pass")
+    ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-kernel", default="ntt")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
     args = ap.parse_args()
+    if args.workload == "serve":
+        return run_serve(args)
     wl = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)

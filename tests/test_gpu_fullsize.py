@@ -61,3 +61,23 @@ def test_fullsize_softmax_precision(full, params, m, kind):
     # bootstrapping calls of the planned schedule (batched: one call covers all m ciphertexts):
     # S in rounds 1, 2, 3, 5; lambda in rounds 1, 4; z once (round 3)
     assert c1["bts"] - c0["bts"] == 7
+
+
+@pytest.mark.parametrize("plan", ["n128_M64", "n256_M64", "n1024_M64"])
+def test_fullsize_serving_plans_grouped_precision(full, params, plan):
+    """The serving mix's dimensions (inputs on [-64, 0]): two independent one-ciphertext
+    requests in one grouped pass, each >= 15 bits against FP64 Softmax."""
+    g, ch, em = full
+    pl = params[1][plan]
+    n, M = pl["n"], pl["M"]
+    g.keygen_softmax(n, 1)
+    L = g.n0 // n
+    xs = [workloads.uniform_inputs(L, n, 40 + i, M) for i in range(2)]
+    parts = [g.encrypt(x, n, 1, M, 50 + i) for i, x in enumerate(xs)]
+    batch = he.Ciphertexts(g, torch.cat([p.tensor for p in parts]), parts[0].level, parts[0].scale, 2)
+    g.softmax_grouped(batch, pl, 2)
+    w = 2 * (batch.level + 1) * g.n
+    for i, x in enumerate(xs):
+        one = he.Ciphertexts(g, batch.tensor[i * w:(i + 1) * w], batch.level, batch.scale, 1)
+        err = np.abs(g.decrypt(one, n) - O.softmax_fp64(x)).max()
+        assert err < 2 ** -15, (plan, i, -math.log2(err))
