@@ -290,7 +290,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2410_11184_gb300 import he
+    from paper_2410_11184_gb300 import he, shard
 
     chains, plans, evalmod = he.load_params()
     ch, pl, em = chains["fgb16"], plans["n256_M128"], evalmod["fgb16"]
@@ -298,10 +298,11 @@ def main():
     g = he.Context(ch, em, stream=stream, device=dev)
     m, n = wl["m"], wl["n"]
     L = m * g.n0 // n
-    g.keygen(1234 + rank)
+    seeds = shard.replica_seeds(rank)   # independent replica per rank (weak scaling)
+    g.keygen(seeds["key"])
     g.keygen_softmax(n, m)
-    x = attention_logits(L, n, seed=100 + rank)
-    src = g.encrypt(x, n, m, pl["M"], 77 + rank)
+    x = attention_logits(L, n, seed=seeds["inputs"])
+    src = g.encrypt(x, n, m, pl["M"], seeds["encrypt"])
     work = g.like(src)
 
     def step(batched, graph=None):
@@ -389,11 +390,7 @@ def main():
         barrier()
         e2e_ms = te[0].elapsed_time(te[1]) / e2e_steps
 
-    ms_step = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms_step, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, e2e_ms = float(t[0]), float(t[1])
+    ms_step, e2e_ms = shard.max_over_ranks([total_ms / args.steps, e2e_ms], dist)
     if rank != 0:
         return
     per_softmax = ms_step / L  # each rank processes L Softmax; value is whole-job (weak scaling)
