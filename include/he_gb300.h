@@ -123,7 +123,8 @@ int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int
 int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts);
 
 /* ---- the hot-path operations, one call each (device buffers as above) ---- */
-/* negacyclic NTT (inverse=0) / inverse NTT of n_limb limbs mod q_0.. in place (device) */
+/* negacyclic NTT (inverse=0) / inverse NTT of n_limb limbs mod q_0.. in place (device);
+ * inputs reduced mod q_i, outputs in [0, q_i) */
 int he_ntt(he_ctx *ctx, uint64_t *data, int n_poly, int n_limb, int inverse);
 /* coefficient-form host copy of a ciphertext batch [n_ct][2][level+1][N] (synchronises) */
 int he_ct_to_coeff(he_ctx *ctx, const he_ct *x, uint64_t *host);
