@@ -256,13 +256,83 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_llama(args):
+    """LLaMa-7B-shaped batch: 32 layers x 32 heads x 128 query rows = 131072 Softmax of dimension
+    128 (context length 128), logits q.k/sqrt(128) with q, k ~ N(0, sigma^2), sigma ~ U[0.5, 1.5]
+    per head, minus a public bound 16 and clipped to [-64, 0].  Each layer is one
+    many-ciphertext group (4096 Softmax in 16 ciphertexts, n/m = 8, Sec. 4.2); a step runs all
+    32 groups, --layers-per-pass of them per he_softmax_grouped call."""
+    import torch
+
+    from paper_2410_11184_gb300 import he, workloads
+
+    chains, plans, evalmod = he.load_params()
+    pl = plans["n128_M64"]
+    n, M, layers, m = pl["n"], pl["M"], 32, 16
+    stream = torch.cuda.Stream()
+    g = he.Context(chains["fgb16"], evalmod["fgb16"], stream=stream)
+    g.keygen(31)
+    g.keygen_softmax(n, m)
+    L = m * g.n0 // n   # 4096 Softmax per layer
+    xs, cts = [], []
+    for layer in range(layers):
+        x = workloads.attention_logits(L, n, 500 + layer, M=M, d=128, bound=16.0, sigma="per_head",
+                                       rows_per_head=128)
+        xs.append(x)
+        cts.append(g.encrypt(x, n, m, M, 600 + layer))
+    per = args.layers_per_pass
+    srcs = [he.Ciphertexts(g, torch.cat([c.tensor for c in cts[i:i + per]]), cts[0].level, cts[0].scale, per * m)
+            for i in range(0, layers, per)]
+    del cts
+    works = [g.like(s) for s in srcs]
+
+    def step():
+        for s, w in zip(srcs, works):
+            w.tensor.copy_(s.tensor)
+            w.level, w.scale, w.n_ct = s.level, s.scale, s.n_ct
+            g.softmax_grouped(w, pl, per)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for i in range(args.steps):
+            step()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms_step = ev[0].elapsed_time(ev[-1]) / args.steps
+    bits = []
+    for i, w in enumerate(works):   # every layer of the last step against FP64 Softmax
+        lw = m * 2 * (w.level + 1) * g.n   # the output batch is stored compactly at its level
+        for j in range(per):
+            one = he.Ciphertexts(g, w.tensor[j * lw:(j + 1) * lw], w.level, w.scale, m)
+            x = xs[i * per + j]
+            e = np.exp(x - x.max(axis=1, keepdims=True))
+            err = float(np.abs(g.decrypt(one, n) - e / e.sum(axis=1, keepdims=True)).max())
+            bits.append(-math.log2(err))
+    total = layers * L
+    print(json.dumps({
+        "metric": "amortized ms/Softmax (LLaMa-7B shape: 32 layers x 32 heads x 128 rows, n=128, N=2^16)",
+        "value": ms_step / total, "unit": "ms/Softmax", "higher_is_better": False, "ms_per_step": ms_step,
+        "p99_ms_per_step": max(per_step), "softmax_per_step": total, "steps": args.steps, "warmup": args.warmup,
+        "precision_bits_min_over_layers": min(bits), "precision_bits_max_over_layers": max(bits),
+        "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
+        "config": {"workload": "32 per-layer groups of 16 ciphertexts (4096 Softmax each), %d groups per pass" % per,
+                   "n": n, "M": M, "k": pl["k"], "ciphertexts": layers * m},
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="m64", choices=["m64", "m1", "serve"])
+    ap.add_argument("--workload", default="m64", choices=["m64", "m1", "serve", "llama"])
+    ap.add_argument("--layers-per-pass", type=int, default=4, help="llama: layer groups per grouped pass")
     ap.add_argument("--rate", type=float, default=8.0, help="serve: request arrivals per second")
     ap.add_argument("--requests", type=int, default=64, help="serve: number of requests")
     ap.add_argument("--max-batch-ct", type=int, default=16, help="serve: ciphertexts per batched pass")
@@ -271,9 +341,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
+    ap.add_argument("--latency-repeats", type=int, default=50, help="single-ciphertext latency repeats (0: off)")
     args = ap.parse_args()
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "llama":
+        return run_llama(args)
     wl = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -389,6 +462,32 @@ def main():
         te[1].record(stream)
         barrier()
         e2e_ms = te[0].elapsed_time(te[1]) / e2e_steps
+        # latency of one Softmax call on a single ciphertext (128 Softmax of dim 256): graph
+        # replays, each timed with CUDA events (p50 / p99 over the repeats)
+        lat1 = None
+        if args.latency_repeats > 0:
+            g.keygen_softmax(n, 1)
+            x1 = attention_logits(g.n0 // n, n, seed=seeds["inputs"] + 1000)
+            src1 = g.encrypt(x1, n, 1, pl["M"], seeds["encrypt"] + 1000)
+            work1 = g.like(src1)
+
+            def one():
+                work1.tensor.copy_(src1.tensor)
+                work1.level, work1.scale, work1.n_ct = src1.level, src1.scale, src1.n_ct
+                g.softmax(work1, pl, graph=True)
+
+            for _ in range(3):
+                one()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.latency_repeats)]
+            for i in range(args.latency_repeats):
+                evs[2 * i].record(stream)
+                one()
+                evs[2 * i + 1].record(stream)
+            torch.cuda.synchronize(dev)
+            ts = sorted(evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(args.latency_repeats))
+            lat1 = {"workload": "1 ciphertext, 128 Softmax of dim 256", "repeats": args.latency_repeats,
+                    "p50_ms": ts[len(ts) // 2], "p99_ms": ts[min(len(ts) - 1, -(-99 * len(ts) // 100) - 1)],
+                    "max_ms": ts[-1]}
 
     ms_step, e2e_ms = shard.max_over_ranks([total_ms / args.steps, e2e_ms], dist)
     if rank != 0:
@@ -421,6 +520,7 @@ def main():
         "clocks": clk,
         "roofline": roof,
         "breakdown_one_step": breakdown,
+        "single_ct_latency": lat1,
         "e2e": {"value": e2e_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": src.tensor.numel() * 8,
                 "d2h_bytes_per_step": out_words * 8},
     }

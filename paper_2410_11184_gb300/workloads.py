@@ -22,13 +22,15 @@ def paper_normal_inputs(L, n, seed, M):
     return x
 
 
-def attention_logits(L, n, seed, M=128.0, d=64, bound=8.0, sigma=None):
-    """q.k / sqrt(d) with q, k ~ N(0, sigma^2 I_d) (sigma = 1, or one U[0.5, 1.5] draw per row
-    when sigma == 'per_head'), minus a public bound, clipped to [-M, 0]."""
+def attention_logits(L, n, seed, M=128.0, d=64, bound=8.0, sigma=None, rows_per_head=1):
+    """q.k / sqrt(d) with q, k ~ N(0, sigma^2 I_d) (sigma = 1, or with sigma == 'per_head' one
+    U[0.5, 1.5] draw per head of rows_per_head consecutive rows), minus a public bound, clipped
+    to [-M, 0]."""
     rng = np.random.default_rng(seed)
     s = np.ones((L, 1))
     if sigma == "per_head":
-        s = rng.uniform(0.5, 1.5, (L, 1))
+        heads = -(-L // rows_per_head)
+        s = np.repeat(rng.uniform(0.5, 1.5, (heads, 1)), rows_per_head, axis=0)[:L]
     q = rng.standard_normal((L, 1, d)) * s[:, :, None]
     k = rng.standard_normal((L, n, d)) * s[:, :, None]
     logits = np.einsum("lid,ljd->lj", q, k) / np.sqrt(d)
