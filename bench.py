@@ -163,7 +163,7 @@ def run_reference(args, wl):
         return
     # ciphertext key switches per Softmax step of this workload (the circuit's operation list, as
     # counted by he_counters on the GPU path: 64-ciphertext batch / one ciphertext)
-    ks_per_step = {"m64": 8249, "m1": 875}[args.workload]
+    ks_per_step = {"m64": 7969, "m1": 847}[args.workload]
     L = wl["m"] * 32768 // wl["n"]
     vals = []
     for _ in range(args.warmup + args.steps):

@@ -314,7 +314,9 @@ def build_all(write=True):
     plans["n256_M64"] = design_softmax("n256_M64", "fgb16", 256, 64.0, softmax_k(64, 256), 15, [63, 31, 31, 127])
     plans["n1024_M64"] = design_softmax("n1024_M64", "fgb16", 1024, 64.0, softmax_k(64, 1024), 15,
                                         [63, 63, 63, 255])
-    evalmod = {"fgb16": design_evalmod(25.0, 3, 63), "toybts": design_evalmod(25.0, 3, 63)}
+    # N = 2^16: a degree-31 cosine and 4 double angles (9 levels, like degree 63 with 3, but fewer
+    # products at the top levels); the toy set keeps degree 63 with 3
+    evalmod = {"fgb16": design_evalmod(25.0, 4, 31), "toybts": design_evalmod(25.0, 3, 63)}
     if write:
         os.makedirs(PARAMS_DIR, exist_ok=True)
         with open(os.path.join(PARAMS_DIR, "chains.json"), "w") as fh:
