@@ -314,7 +314,10 @@ static DCt ct_new(he_ctx *c, int level, int nct, double scale) {
     return x;
 }
 
-static DCt ct_view(const he_ct *h) {
+// a caller's ciphertext batch; descriptors that could reach a kernel out of bounds are refused
+static DCt ct_view(const he_ctx *c, const he_ct *h) {
+    REQUIRE(h && h->data && h->n_ct >= 1 && h->level >= 0 && h->level < c->nq, HE_EINVAL,
+            "ciphertext: data must be set, n_ct >= 1 and 0 <= level < n_q");
     DCt x;
     x.d = h->data;
     x.level = h->level;
@@ -1860,7 +1863,7 @@ int he_decrypt(he_ctx *ctx, const he_ct *cts, int n, double *y, size_t count) {
     size_t L = (size_t)m * ctx->n0 / n;
     if (count != L * (size_t)n) return HE_EINVAL;
     API_BEGIN
-    DCt x = ct_view(cts);
+    DCt x = ct_view(ctx, cts);
     for (int c = 0; c < m; c++) {
         std::vector<double2> z = decrypt_slots(ctx, x, c);
         for (int t = 0; t < per; t++)
@@ -1872,7 +1875,7 @@ int he_decrypt(he_ctx *ctx, const he_ct *cts, int n, double *y, size_t count) {
 int he_decrypt_slots(he_ctx *ctx, const he_ct *cts, int ct, double *slots) {
     if (!ctx || !cts || !slots || ct < 0 || ct >= cts->n_ct) return HE_EINVAL;
     API_BEGIN
-    std::vector<double2> z = decrypt_slots(ctx, ct_view(cts), ct);
+    std::vector<double2> z = decrypt_slots(ctx, ct_view(ctx, cts), ct);
     memcpy(slots, z.data(), sizeof(double2) * ctx->n0);
     API_END
 }
@@ -1931,7 +1934,7 @@ static int softmax_check(he_ctx *ctx, const he_softmax_plan *plan, const he_ct *
 static void softmax_inplace(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, bool batched, int groups = 1) {
     int m = cts->n_ct / groups;
     Plan p = plan_of(ctx, plan);
-    DCt in = ct_view(cts);
+    DCt in = ct_view(ctx, cts);
     std::vector<DCt> ys;
     if (batched) {
         ys.push_back(ct_copy(ctx, in));
@@ -2116,15 +2119,15 @@ int he_encode(he_ctx *ctx, const double *slots, double scale, int level, uint64_
 int he_add(he_ctx *ctx, he_ct *a, const he_ct *b) {
     if (!ctx || !a || !b) return HE_EINVAL;
     API_BEGIN
-    DCt x = ct_view(a);
-    ct_add_inplace(ctx, x, ct_view(b));
+    DCt x = ct_view(ctx, a);
+    ct_add_inplace(ctx, x, ct_view(ctx, b));
     API_END
 }
 
 int he_mul_plain(he_ctx *ctx, he_ct *a, const uint64_t *pt) {
     if (!ctx || !a || !pt) return HE_EINVAL;
     API_BEGIN
-    DCt x = ct_view(a);
+    DCt x = ct_view(ctx, a);
     ct_mul_plain(ctx, x, pt);
     API_END
 }
@@ -2140,7 +2143,7 @@ static void put_out(he_ctx *ctx, const DCt &y, he_ct *out) {
 int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out) {
     if (!ctx || !a || !out) return HE_EINVAL;
     API_BEGIN
-    put_out(ctx, rescale(ctx, ct_view(a)), out);
+    put_out(ctx, rescale(ctx, ct_view(ctx, a)), out);
     API_END
 }
 
@@ -2163,7 +2166,7 @@ int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out) {
         return HE_EINVAL;
     }
     API_BEGIN
-    rescale_noalloc(ctx, ct_view(a), out->data);
+    rescale_noalloc(ctx, ct_view(ctx, a), out->data);
     out->level = a->level - 1;
     out->scale = a->scale / (double)ctx->mods[a->level];
     out->n_ct = a->n_ct;
@@ -2173,7 +2176,7 @@ int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out) {
 int he_hmult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out) {
     if (!ctx || !a || !b || !out) return HE_EINVAL;
     API_BEGIN
-    put_out(ctx, hmult(ctx, ct_view(a), ct_view(b)), out);
+    put_out(ctx, hmult(ctx, ct_view(ctx, a), ct_view(ctx, b)), out);
     API_END
 }
 
@@ -2187,14 +2190,14 @@ int he_relinearize(he_ctx *ctx, const uint64_t *d, int level, int n_ct, he_ct *o
 int he_rotate(he_ctx *ctx, const he_ct *a, int r, he_ct *out) {
     if (!ctx || !a || !out) return HE_EINVAL;
     API_BEGIN
-    put_out(ctx, rotate(ctx, ct_view(a), galois_for_rot(ctx, r)), out);
+    put_out(ctx, rotate(ctx, ct_view(ctx, a), galois_for_rot(ctx, r)), out);
     API_END
 }
 
 int he_conjugate(he_ctx *ctx, const he_ct *a, he_ct *out) {
     if (!ctx || !a || !out) return HE_EINVAL;
     API_BEGIN
-    put_out(ctx, rotate(ctx, ct_view(a), 2 * ctx->N - 1), out);
+    put_out(ctx, rotate(ctx, ct_view(ctx, a), 2 * ctx->N - 1), out);
     API_END
 }
 
@@ -2202,7 +2205,7 @@ int he_poly_eval(he_ctx *ctx, const he_ct *u, const double *coeffs, int deg, int
     if (!ctx || !u || !coeffs || !out || deg < 1 || level_out < 0) return HE_EINVAL;
     API_BEGIN
     std::vector<double> cf(coeffs, coeffs + deg + 1);
-    put_out(ctx, poly_eval(ctx, ct_view(u), cf, level_out, scale_out), out);
+    put_out(ctx, poly_eval(ctx, ct_view(ctx, u), cf, level_out, scale_out), out);
     API_END
 }
 
@@ -2210,21 +2213,21 @@ int he_lintrans(he_ctx *ctx, const he_ct *a, int nlev, int inverse, int which, d
     if (!ctx || !a || !out || nlev < 1 || which < 0 || which >= nlev) return HE_EINVAL;
     API_BEGIN
     std::vector<LtDesc> lv = lt_levels(ctx, nlev, inverse);
-    put_out(ctx, lt_eval_level(ctx, ct_view(a), lv[which], gain, pt_scale), out);
+    put_out(ctx, lt_eval_level(ctx, ct_view(ctx, a), lv[which], gain, pt_scale), out);
     API_END
 }
 
 int he_bootstrap(he_ctx *ctx, const he_ct *a, double gain, double out_scale, he_ct *out) {
     if (!ctx || !a || !out) return HE_EINVAL;
     API_BEGIN
-    put_out(ctx, bootstrap(ctx, ct_view(a), gain, out_scale), out);
+    put_out(ctx, bootstrap(ctx, ct_view(ctx, a), gain, out_scale), out);
     API_END
 }
 
 int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out) {
     if (!ctx || !a || !out || top < 0 || top >= ctx->nq) return HE_EINVAL;
     API_BEGIN
-    put_out(ctx, mod_raise(ctx, ct_view(a), top), out);
+    put_out(ctx, mod_raise(ctx, ct_view(ctx, a), top), out);
     API_END
 }
 
