@@ -360,13 +360,13 @@ uint64_t *modup(orc_ctx *c, const uint64_t *d, int level) {
     return out;
 }
 
-/* Inner product of the (optionally automorphed) extended digits with key, then ModDown.
+/* Inner product of the (optionally automorphed) extended digits with key: the two
+ * polynomials of sum_j d~_j swk_j over Q_l u P, coefficient form, [(level+1)+np][N] each,
+ * added to acc0 / acc1 (which the caller zeroes for a single key switch).
  * galois 0 or 1: no automorphism. */
-int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_key *key, uint64_t *out0, uint64_t *out1) {
+int ks_inner(orc_ctx *c, uint64_t *digits, int level, int galois, orc_key *key, uint64_t *acc0, uint64_t *acc1) {
     int L = level + 1, nl = L + c->np, al = c->alpha;
     int nd = (L + al - 1) / al;
-    uint64_t *acc0 = calloc((size_t)nl * N_, sizeof(uint64_t));
-    uint64_t *acc1 = calloc((size_t)nl * N_, sizeof(uint64_t));
 #pragma omp parallel for schedule(dynamic)
     for (int tt = 0; tt < nl; tt++) {
         int t = tt < L ? tt : c->nq + (tt - L);
@@ -387,13 +387,23 @@ int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_ke
         }
         ntt_inv(c, t, s0);
         ntt_inv(c, t, s1);
-        memcpy(acc0 + (size_t)tt * N_, s0, sizeof(uint64_t) * N_);
-        memcpy(acc1 + (size_t)tt * N_, s1, sizeof(uint64_t) * N_);
+        uint64_t *a0 = acc0 + (size_t)tt * N_, *a1 = acc1 + (size_t)tt * N_;
+        for (int k = 0; k < N_; k++) {
+            a0[k] = addmod(a0[k], s0[k], q);
+            a1[k] = addmod(a1[k], s1[k], q);
+        }
         free(x);
         free(s0);
         free(s1);
     }
-    /* ModDown */
+    c->n_ks++;
+    return 0;
+}
+
+/* ModDown of the two extended polynomials acc0 / acc1 (coefficient form, Q_l u P):
+ * out = (acc_Q - Conv_{P->Q}([acc]_P)) P^{-1} mod q_i, i <= level. */
+int moddown(orc_ctx *c, const uint64_t *acc0, const uint64_t *acc1, int level, uint64_t *out0, uint64_t *out1) {
+    int L = level + 1;
     int np = c->np;
     uint64_t phat_inv[ORC_MAXP];
     for (int k = 0; k < np; k++) {
@@ -403,7 +413,8 @@ int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_ke
         phat_inv[k] = invmod(prod, pk);
     }
     for (int which = 0; which < 2; which++) {
-        uint64_t *acc = which ? acc1 : acc0, *out = which ? out1 : out0;
+        const uint64_t *acc = which ? acc1 : acc0;
+        uint64_t *out = which ? out1 : out0;
 #pragma omp parallel for schedule(dynamic)
         for (int t = 0; t < L; t++) {
             uint64_t q = c->mod[t];
@@ -429,9 +440,17 @@ int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_ke
             }
         }
     }
+    return 0;
+}
+
+/* one key switch: inner product, then ModDown */
+int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_key *key, uint64_t *out0, uint64_t *out1) {
+    size_t nl = (size_t)(level + 1) + c->np;
+    uint64_t *acc0 = calloc(nl * N_, sizeof(uint64_t)), *acc1 = calloc(nl * N_, sizeof(uint64_t));
+    ks_inner(c, digits, level, galois, key, acc0, acc1);
+    moddown(c, acc0, acc1, level, out0, out1);
     free(acc0);
     free(acc1);
-    c->n_ks++;
     return 0;
 }
 

@@ -14,7 +14,9 @@
  * order the stages apply.  A level is evaluated as sum_d diag_d (.) Rot(x, d) with the
  * baby-step/giant-step split d = e h_min, e = a g + b (0 <= b < g, g = 2^ceil((r+1)/2)):
  *   sum_a Rot( sum_b Rot(diag_{ag+b}, -a g h_min) (.) Rot(x, b h_min), a g h_min ),
- * the plaintext products summed without rescaling, one rescale at the end of the level. */
+ * the plaintext products summed without rescaling, one rescale at the end of the level.
+ * The giant-step rotations share one ModDown: their key-switch inner products are summed
+ * over Q_l u P, the c0(X^g) parts over Q_l, and the sum is brought down by P once. */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -142,9 +144,12 @@ int lt_eval_level(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, doub
     }
     orc_ct *baby = calloc(nb, sizeof(orc_ct));
     rotate_hoisted(c, x, gal, nb, baby);
-    orc_ct acc;
-    int have_acc = 0;
     int level = x->level;
+    size_t nl = (size_t)(level + 1) + c->np;
+    orc_ct acc = ct_alloc(c, level);   /* zero: sum over the giant steps */
+    acc.scale = x->scale * pt_scale;
+    uint64_t *ext0 = calloc(nl * c->n, sizeof(uint64_t)), *ext1 = calloc(nl * c->n, sizeof(uint64_t));
+    int have_ext = 0;
     uint64_t *pt = malloc(sizeof(uint64_t) * (size_t)(level + 1) * c->n);
     cplx *rd = malloc(sizeof(cplx) * n0);
     for (int a = amin; a <= amax; a++) {
@@ -172,16 +177,37 @@ int lt_eval_level(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, doub
             }
         }
         if (!have_inner) continue;
-        inner.scale = x->scale * pt_scale;
-        if (a != 0) {
-            orc_ct rot;
-            rotate(c, &inner, galois_for_rot(c, (long)a * g * hmin), &rot);
-            ct_free(&inner);
-            inner = rot;
+        inner.scale = acc.scale;
+        if (a == 0) {
+            ct_add(c, &acc, &inner);
+        } else {
+            /* Rot(inner, a g h_min): c0(X^g) into acc, the key switch of c1(X^g) into ext */
+            int gal_a = galois_for_rot(c, (long)a * g * hmin);
+            uint64_t *dig = modup(c, ct_poly(c, &inner, 1), level);
+            ks_inner(c, dig, level, gal_a, get_key(c, gal_a), ext0, ext1);
+            free(dig);
+            uint64_t *tmp = malloc(sizeof(uint64_t) * c->n);
+            uint64_t *a0 = ct_poly(c, &acc, 0);
+            for (int t = 0; t <= level; t++) {
+                uint64_t q = c->mod[t];
+                automorph_poly(c, t, ct_poly(c, &inner, 0) + (size_t)t * c->n, gal_a, tmp);
+                for (int k = 0; k < c->n; k++) a0[(size_t)t * c->n + k] = addmod(a0[(size_t)t * c->n + k], tmp[k], q);
+            }
+            free(tmp);
+            have_ext = 1;
+            c->n_rot++;
         }
-        if (!have_acc) { acc = inner; have_acc = 1; }
-        else { ct_add(c, &acc, &inner); ct_free(&inner); }
+        ct_free(&inner);
     }
+    if (have_ext) {
+        orc_ct md = ct_alloc(c, level);
+        md.scale = acc.scale;
+        moddown(c, ext0, ext1, level, ct_poly(c, &md, 0), ct_poly(c, &md, 1));
+        ct_add(c, &acc, &md);
+        ct_free(&md);
+    }
+    free(ext0);
+    free(ext1);
     for (int b = 0; b < nb; b++) ct_free(&baby[b]);
     free(baby);
     free(pt);

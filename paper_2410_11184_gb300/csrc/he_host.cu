@@ -500,36 +500,54 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     return dig;
 }
 
-// inner product with key (automorphism g applied to the digits when g > 1) and ModDown into out
-// (nct ciphertexts at level L-1, stride so); when add is given (it may be out itself) its two
-// polynomials (ciphertext stride sadd) are added to the result
-static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, const uint64_t *key, uint64_t *out,
-                      long so, const uint64_t *add, long sadd) {
+// key-switch inner product sum_j d~_j swk_j over Q_l u P (automorphism g applied to the digits
+// when g > 1) into acc [nct][2][L + alpha][N] (NTT form); accumulate: added to acc
+static void ks_inner_into(he_ctx *c, uint64_t *acc, const uint64_t *dig, int nct, int L, int g, const uint64_t *key,
+                          bool accumulate) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
-    DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
     {
-        ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl));
-        k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc.get(), dig, nct, nd, L, al, extmap(c, L),
-                                                                        c->d_mods, key, c->nm, c->nq, g, c->logN);
+        ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl *
+                                                                            (accumulate ? 2 : 1)));
+        k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc, dig, nct, nd, L, al, extmap(c, L), c->d_mods,
+                                                                        key, c->nm, c->nq, g, c->logN,
+                                                                        accumulate ? 1 : 0);
     }
     LAUNCH_CHECK();
-    ntt(c, acc.get() + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true, "ntt_moddown");
+    c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
+}
+
+// ModDown of acc (its P limbs are transformed in place) into out (nct ciphertexts at level
+// L-1, stride so); when add is given (it may be out itself) its two polynomials (ciphertext
+// stride sadd) are added to the result
+static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, long so, const uint64_t *add,
+                       long sadd) {
+    int al = c->alpha, nl = L + al;
+    ntt(c, acc + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true, "ntt_moddown");
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
     long tot = (long)2 * nct * L << c->logN;
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (al + L));
-        k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc.get(), 2 * nct, L, al, qmap(L), c->d_pidx,
-                                                             c->d_mods, c->d_mdcv, c->nq, c->logN);
+        k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc, 2 * nct, L, al, qmap(L),
+                                                                                  c->d_pidx, c->d_mods, c->d_mdcv,
+                                                                                  c->nq, c->logN);
     }
     LAUNCH_CHECK();
     ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown");
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * L * (add ? 4 : 3));
-        k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc.get(), conv.get(), 2 * nct, L, al, qmap(L),
+        k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc, conv.get(), 2 * nct, L, al, qmap(L),
                                                             c->d_mods, c->d_pinv, c->logN, add, sadd);
     }
     LAUNCH_CHECK();
-    c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
+}
+
+// one key switch: inner product and ModDown into out (see ks_moddown for add)
+static void ks_finish(he_ctx *c, const uint64_t *dig, int nct, int L, int g, const uint64_t *key, uint64_t *out,
+                      long so, const uint64_t *add, long sadd) {
+    int nl = L + c->alpha;
+    DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
+    ks_inner_into(c, acc.get(), dig, nct, L, g, key, false);
+    ks_moddown(c, acc.get(), nct, L, out, so, add, sadd);
 }
 
 static const uint64_t *get_key(he_ctx *c, int galois) {
@@ -632,17 +650,6 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
 }
 
 static DCt rotate(he_ctx *c, const DCt &x, int g) { return rotate_hoisted(c, x, std::vector<int>{g})[0]; }
-
-// acc += Rot_g(x) (same level and count): the key switch accumulates into acc directly
-static void rotate_acc(he_ctx *c, const DCt &x, int g, DCt &acc) {
-    REQUIRE(acc.level == x.level && acc.nct == x.nct, HE_EINVAL, "rotate_acc: level/count mismatch");
-    int L = x.level + 1;
-    const uint64_t *key = get_key(c, g);
-    DPtr dig = ks_modup(c, x.d + (long)L * c->N, x.cs(c), x.nct, L);
-    automorph_acc(c, acc, x, g);
-    ks_finish(c, dig.get(), x.nct, L, g, key, acc.d, acc.cs(c), acc.d, acc.cs(c));
-    c->cnt[1]++;
-}
 
 static int galois_for_rot(he_ctx *c, long r) {
     long n0 = c->n0, m = 2L * c->N;
@@ -1227,16 +1234,36 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         k_lt_bsgs<<<grid, 256, smem, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
-    // acc = sum_a Rot(out_a, a g hmin), the rotations accumulated into acc
-    int first = -1;
+    // acc = sum_a Rot(out_a, a g hmin): the c0(X^g) parts are added over Q_l, the key-switch
+    // inner products of the c1(X^g) parts are summed over Q_l u P and brought down by P once
+    DCt acc;
+    bool have_acc = false;
     for (size_t i = 0; i < gi.size(); i++)
-        if (gi[i] == 0) first = (int)i;
-    DCt acc = first >= 0 ? inner[first] : rotate(c, inner[0], galois_for_rot(c, (long)gi[0] * Lv.g * Lv.hmin));
-    if (first < 0) first = 0;
-    for (size_t i = 0; i < gi.size(); i++) {
-        if ((int)i == first) continue;
-        rotate_acc(c, inner[i], galois_for_rot(c, (long)gi[i] * Lv.g * Lv.hmin), acc);
+        if (gi[i] == 0) {
+            acc = inner[i];
+            have_acc = true;
+        }
+    if (!have_acc) {
+        acc = ct_new(c, x.level, x.nct, x.scale * pt_scale);
+        {
+            ProfScope ps_(c, "copy", 0);
+            CK(cudaMemsetAsync(acc.d, 0, (size_t)acc.nct * acc.cs(c) * 8, c->st));
+        }
     }
+    DPtr ext;
+    bool have_ext = false;
+    for (size_t i = 0; i < gi.size(); i++) {
+        if (gi[i] == 0) continue;
+        int ga = galois_for_rot(c, (long)gi[i] * Lv.g * Lv.hmin);
+        const uint64_t *key = get_key(c, ga);
+        if (!have_ext) ext = dalloc(c, (size_t)x.nct * 2 * (L + c->alpha) * c->N);
+        DPtr dig = ks_modup(c, inner[i].d + (long)L * c->N, inner[i].cs(c), x.nct, L);
+        ks_inner_into(c, ext.get(), dig.get(), x.nct, L, ga, key, have_ext);
+        automorph_acc(c, acc, inner[i], ga);
+        have_ext = true;
+        c->cnt[1]++;
+    }
+    if (have_ext) ks_moddown(c, ext.get(), x.nct, L, acc.d, acc.cs(c), acc.d, acc.cs(c));
     acc.scale = x.scale * pt_scale;
     return rescale(c, acc);
 }

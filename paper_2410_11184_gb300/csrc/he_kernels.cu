@@ -407,7 +407,7 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
 // per (t, k) for all ciphertexts of the batch.
 __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
                            int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
-                           int nq_all, int g, int logN) {
+                           int nq_all, int g, int logN, int accumulate) {
     const int N = 1 << logN;
     const int nl = L + alpha;
     long total = (long)nl << logN;
@@ -431,8 +431,14 @@ __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restric
                 mac_wide(l0, h0, d, kb[j]);
                 mac_wide(l1, h1, d, ka[j]);
             }
-            acc[((long)(2 * c) * nl + t) * N + k] = redc(l0, h0, m);
-            acc[((long)(2 * c + 1) * nl + t) * N + k] = redc(l1, h1, m);
+            uint64_t r0 = redc(l0, h0, m), r1 = redc(l1, h1, m);
+            const long o0 = ((long)(2 * c) * nl + t) * N + k, o1 = ((long)(2 * c + 1) * nl + t) * N + k;
+            if (accumulate) {   // sums of several key switches over Q u P (one ModDown after)
+                r0 = add_mod(acc[o0], r0, m.q);
+                r1 = add_mod(acc[o1], r1, m.q);
+            }
+            acc[o0] = r0;
+            acc[o1] = r1;
         }
     }
 }

@@ -64,7 +64,7 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
                               const uint64_t *add, long sadd);
 __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
                            int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
-                           int nq_all, int g, int logN);
+                           int nq_all, int g, int logN, int accumulate);
 __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,
                                  const ModC *mods, uint64_t ql, int logN);
 __global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *t, int npoly, int L, LimbMap qmap,
