@@ -258,10 +258,15 @@ static LimbMap single(int p) {
 // ------------------------------------------------------------------------- NTT launches
 // NTT of `count` limbs in place, or out of place from src (limb l of polynomial i at
 // src + i src_stride + l N) when src is given
+static bool ntt_rb(const he_ctx *c) { return c->logN == 16 || c->logN == 12; }
+
+// fuse (register-blocked sizes only): neighbours of a forward transform, see NttFuse
 static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long poly_stride, bool inverse,
-                const char *site = "ntt", const uint64_t *src = nullptr, long src_stride = 0) {
+                const char *site = "ntt", const uint64_t *src = nullptr, long src_stride = 0,
+                const NttFuse *fuse = nullptr) {
     if (count <= 0) return;
-    bool rb = c->logN == 16 || c->logN == 12;
+    bool rb = ntt_rb(c);
+    REQUIRE(!fuse || (rb && !inverse), HE_EINVAL, "fused transform: forward, register-blocked sizes only");
     if (src && !rb) {
         CK(cudaMemcpy2DAsync(base, (size_t)poly_stride * 8, src, (size_t)src_stride * 8, (size_t)map.nper * c->N * 8,
                              count / map.nper, cudaMemcpyDeviceToDevice, c->st));
@@ -273,12 +278,14 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     int R = std::max(1, std::min(N1, 2048 / N2));
     dim3 g1(N2 / C, count), g2(N1 / R, count);
     size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
-    ProfScope ps(c, site, 16.0 * count * c->N);
+    // algorithmic bytes: the transform's read + write, plus what a fused ModDown epilogue reads
+    double extra = fuse && fuse->kind == 1 ? 8.0 * count * c->N * (fuse->add ? 2 : 1) : 0.0;
+    ProfScope ps(c, site, 16.0 * count * c->N + extra);
     c->launches++;
     if (rb) {
         // register-blocked passes: 16 (N = 2^16) or 8 (N = 2^12) coefficients per thread
         launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
-                      c->d_ninv, c->logN, c->st, src, src_stride);
+                      c->d_ninv, c->logN, c->st, src, src_stride, fuse);
         LAUNCH_CHECK();
         return;
     }
@@ -422,6 +429,20 @@ static DCt rescale(he_ctx *c, const DCt &a) {
     DPtr last = dalloc(c, (size_t)npoly * c->N);
     ntt(c, last.get(), npoly, single(l), c->N, true, "ntt_rescale", a.d + (long)l * c->N, (long)L * c->N);
     DPtr tmp = dalloc(c, (size_t)npoly * l * c->N);
+    if (ntt_rb(c)) {
+        // spread of the centred last limb and the final (x - t) q_l^{-1} fused into the transform
+        DCt y = ct_new(c, l - 1, a.nct, a.scale / (double)c->mods[l]);
+        NttFuse F{};
+        F.kind = 2;
+        F.x = a.d;
+        F.out = y.d;
+        F.cst = c->d_qlinv + (size_t)l * 2 * c->nq;
+        F.last = last.get();
+        F.ql = c->mods[l];
+        ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false, "ntt_rescale", nullptr, 0, &F);
+        c->cnt[3]++;
+        return y;
+    }
     long tot = (long)npoly * l << c->logN;
     {
         ProfScope ps_(c, "rescale", 8.0 * c->N * npoly * (1 + l));
@@ -532,6 +553,20 @@ static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, 
                                                                                   c->nq, c->logN);
     }
     LAUNCH_CHECK();
+    if (ntt_rb(c)) {
+        // (x - conv) P^{-1} (+ add) fused into the transform of conv
+        NttFuse F{};
+        F.kind = 1;
+        F.alpha = al;
+        F.x = acc;
+        F.out = out;
+        F.so = so;
+        F.add = add;
+        F.sadd = sadd;
+        F.cst = c->d_pinv;
+        ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown", nullptr, 0, &F);
+        return;
+    }
     ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown");
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * L * (add ? 4 : 3));

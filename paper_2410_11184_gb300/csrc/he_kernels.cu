@@ -764,10 +764,10 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
 }
 
 // Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
-template <int LOGE>
+template <int LOGE, int KIND>
 __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
-                                                         const uint64_t *src, long src_stride) {
+                                                         const uint64_t *src, long src_stride, NttFuse F) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
     constexpr int SUB = 256 / TPS;                         // columns per CTA
     __shared__ uint64_t sm[S * SUB];
@@ -780,8 +780,19 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
     // out of place when src is given: read limb l of src, write base
     const uint64_t *in = src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a;
     uint64_t v[E];
+    if (KIND == 2) {
+        // rescale: t_i = centred last limb mod q_i
+        const ModC mi = mods[p];
+        const uint64_t *lp = F.last + (long)(l / nper) * N;
 #pragma unroll
-    for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
+        for (int j = 0; j < E; j++) {
+            const uint64_t r = lp[(long)(k + E * j) * N2 + col];
+            v[j] = r <= (F.ql - 1) / 2 ? mul_mod(r, 1, mi) : neg_mod(mul_mod(F.ql - r, 1, mi), mi.q);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
+    }
     // stages m = 1 .. E/2: element index r = k + E j, group = j / (2t) (independent of k)
     ct_stages_strided<LOGE>(v, 1, 0, 0, psi, q);
 #pragma unroll
@@ -796,9 +807,10 @@ __global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int npe
 }
 
 // Forward row pass: stages m = N1 .. N/2 on rows of S = N2 contiguous coefficients.
-template <int LOGE>
+template <int LOGE, int KIND>
 __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
-                                                         const ModC *mods, const ulonglong2 *tw2, int logN) {
+                                                         const ModC *mods, const ulonglong2 *tw2, int logN,
+                                                         NttFuse F) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = 256 / TPS;                         // rows per CTA
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
@@ -834,8 +846,32 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
         sm[rr * SP + (E + 1) * k + j] = r;
     }
     __syncthreads();
+    if (KIND == 0) {
 #pragma unroll
-    for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * SP + k + (E + 1) * j];
+        for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * SP + k + (E + 1) * j];
+        return;
+    }
+    // fused epilogue (ModDown or rescale): out from x and the transformed values
+    const int pl = l / nper, i = l % nper;
+    const long at = (long)i * N + (long)row * S + k;
+    if (KIND == 1) {
+        const uint64_t w = F.cst[2 * p], wp = F.cst[2 * p + 1];
+        const uint64_t *xp = F.x + (long)pl * (nper + F.alpha) * N + at;
+        const long o = (long)(pl / 2) * F.so + (long)(pl % 2) * nper * N + at;
+        const long oa = (long)(pl / 2) * F.sadd + (long)(pl % 2) * nper * N + at;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            uint64_t r = mul_shoup(sub_mod(xp[E * j], sm[rr * SP + k + (E + 1) * j], q), w, wp, q);
+            if (F.add) r = add_mod(F.add[oa + E * j], r, q);
+            F.out[o + E * j] = r;
+        }
+    } else {
+        const uint64_t w = F.cst[2 * i], wp = F.cst[2 * i + 1];
+        const uint64_t *xp = F.x + (long)pl * (nper + 1) * N + at;
+        uint64_t *op = F.out + (long)pl * nper * N + at;
+#pragma unroll
+        for (int j = 0; j < E; j++) op[E * j] = mul_shoup(sub_mod(xp[E * j], sm[rr * SP + k + (E + 1) * j], q), w, wp, q);
+    }
 }
 
 // Inverse row pass: stages h = N/2 .. N1 (t = 1 .. N2/2).
@@ -908,12 +944,18 @@ __global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int npe
 template <int LOGE>
 static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
                       const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
-                      const uint64_t *src, long src_stride) {
+                      const uint64_t *src, long src_stride, const NttFuse &F) {
     constexpr int E = 1 << LOGE, S = E * E, SUB = 256 / E;
     dim3 g(((1 << logN) / S) / SUB, count);
-    if (!inverse) {
-        k_ntt_cols_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
-        k_ntt_rows_fwd_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN);
+    if (!inverse && F.kind == 1) {
+        k_ntt_cols_fwd_rb<LOGE, 1><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 1><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+    } else if (!inverse && F.kind == 2) {
+        k_ntt_cols_fwd_rb<LOGE, 2><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 2><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+    } else if (!inverse) {
+        k_ntt_cols_fwd_rb<LOGE, 0><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 0><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else {
         k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
         k_ntt_cols_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, ninv, logN);
@@ -922,7 +964,9 @@ static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long po
 
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
                    const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
-                   const uint64_t *src, long src_stride) {
-    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride);
-    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride);
+                   const uint64_t *src, long src_stride, const NttFuse *fuse) {
+    NttFuse F{};
+    if (fuse) F = *fuse;
+    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
+    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
 }

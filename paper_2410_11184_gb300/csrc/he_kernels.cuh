@@ -21,6 +21,27 @@ struct LtArgs {
     int nb, na, npt;
 };
 
+// Neighbours fused into a forward NTT (passed by value; kind 0: none).  Limb i of polynomial p of
+// the transformed batch (nper limbs per polynomial, coefficient index k):
+//   kind 1 (ModDown): the batch is Conv_{P->Q}; the row pass writes
+//       out_i = (x_i - NTT(conv)_i) pinv_i (+ add_i), x_i at x + p (nper + alpha) N + i N,
+//       out / add polynomial p at base + (p / 2) stride + (p % 2) nper N, pinv = cst[2 prime], cst[2 prime + 1];
+//   kind 2 (rescale): the column pass reads the centred last limb last[p] reduced mod q_i
+//       instead of the batch, the row pass writes out_i = (x_i - NTT(t)_i) qlinv_i,
+//       x_i at x + p (nper + 1) N + i N, out_i at out + p nper N + i N, qlinv = cst[2 i], cst[2 i + 1].
+struct NttFuse {
+    int kind;
+    int alpha;
+    const uint64_t *x;
+    uint64_t *out;
+    long so;
+    const uint64_t *add;
+    long sadd;
+    const uint64_t *cst;
+    const uint64_t *last;
+    uint64_t ql;
+};
+
 // Linear combination sum_t w_t x_t (+ w0 on c0) of up to HE_LC_MAXT batches at any levels
 #define HE_LC_MAXT 8
 struct LcArgs {
@@ -97,4 +118,4 @@ __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_i
 // tw2: per modulus p, N (psi^brv(k), Shoup companion) pairs at tw2 + 2 N p, then N inverse pairs
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
                    const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
-                   const uint64_t *src = nullptr, long src_stride = 0);
+                   const uint64_t *src = nullptr, long src_stride = 0, const NttFuse *fuse = nullptr);
