@@ -71,6 +71,7 @@ def lib():
         L.orc_rescale.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, u64p, dblp]
         L.orc_tensor.argtypes = [C.c_void_p, u64p, u64p, C.c_int, u64p]
         L.orc_relin.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
+        L.orc_relin_rescale.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
         L.orc_hmult.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, u64p, C.c_int, C.c_double,
                                 u64p, intp, dblp]
         L.orc_galois_for_rot.argtypes = [C.c_void_p, C.c_long]
@@ -227,6 +228,12 @@ class Oracle:
     def relin(self, d012, level):
         out = np.zeros((2, level + 1, self.n), dtype=np.uint64)
         self._chk(lib().orc_relin(self.ptr, P(_u64(d012)), level, P(out)))
+        return out
+
+    def relin_rescale(self, d012, level):
+        """relinearisation and rescale in one division by P q_level: [2][level][N]"""
+        out = np.zeros((2, level, self.n), dtype=np.uint64)
+        self._chk(lib().orc_relin_rescale(self.ptr, P(_u64(d012)), level, P(out)))
         return out
 
     def hmult(self, a, b):

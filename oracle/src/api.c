@@ -199,6 +199,15 @@ int orc_tensor(orc_ctx *c, const uint64_t *a, const uint64_t *b, int level, uint
     return rc;
 }
 
+int orc_relin_rescale(orc_ctx *c, const uint64_t *d012, int level, uint64_t *out) {
+    size_t sz = (size_t)(level + 1) * c->n;
+    orc_ct x;
+    int rc = relin_rescale(c, d012, d012 + sz, d012 + 2 * sz, level, 1.0, &x);
+    if (rc) return rc;
+    unwrap(c, &x, out, NULL, NULL);
+    return 0;
+}
+
 int orc_relin(orc_ctx *c, const uint64_t *d012, int level, uint64_t *out) {
     size_t sz = (size_t)(level + 1) * c->n;
     orc_ct x;

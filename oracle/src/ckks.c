@@ -473,19 +473,86 @@ int relinearize(orc_ctx *c, const uint64_t *d0, const uint64_t *d1, const uint64
     return 0;
 }
 
-/* Tensor, relinearise, rescale.  Operands at different levels: the higher is dropped. */
+/* Relinearisation and rescale as one division.  K = the key switch of d2 over Q_l u P,
+ * Y = P (d0, d1) + K over Q_l u P, and the output at level l - 1 is
+ *   out_i = (Y_i - Conv_{D->q_i}([Y]_D)) (P q_l)^{-1} mod q_i,   D = {q_l} u P,
+ * the conversion taking centred representatives as ModDown does: Y / (P q_l) rounded up to the
+ * usual small conversion error, one rounding where ModDown followed by a rescale has two. */
+int relin_rescale(orc_ctx *c, const uint64_t *d0, const uint64_t *d1, const uint64_t *d2, int level, double scale,
+                  orc_ct *out) {
+    int l = level, L = level + 1, np = c->np, nl = L + np, nd = np + 1;
+    if (l < 1) { snprintf(c->err, sizeof c->err, "relin_rescale at level 0"); return -1; }
+    uint64_t *dig = modup(c, d2, level);
+    uint64_t *y0 = calloc((size_t)nl * N_, sizeof(uint64_t)), *y1 = calloc((size_t)nl * N_, sizeof(uint64_t));
+    ks_inner(c, dig, level, 0, get_key(c, 0), y0, y1);
+    free(dig);
+    /* Y = K + P d on the Q limbs (P d vanishes mod every p_k) */
+    for (int t = 0; t <= l; t++) {
+        uint64_t q = c->mod[t], pm = 1 % q;
+        for (int k = 0; k < np; k++) pm = mulmod(pm, c->mod[c->nq + k] % q, q);
+        for (int k = 0; k < N_; k++) {
+            size_t i = (size_t)t * N_ + k;
+            y0[i] = addmod(y0[i], mulmod(d0[i], pm, q), q);
+            y1[i] = addmod(y1[i], mulmod(d1[i], pm, q), q);
+        }
+    }
+    /* the dropped moduli D: q_l (limb l), then p_0 .. p_{np-1} (limbs L ..): limbs l .. l + np */
+    uint64_t md[ORC_MAXP + 1], dhat_inv[ORC_MAXP + 1];
+    md[0] = c->mod[l];
+    for (int k = 0; k < np; k++) md[1 + k] = c->mod[c->nq + k];
+    for (int j = 0; j < nd; j++) {
+        uint64_t prod = 1 % md[j];
+        for (int j2 = 0; j2 < nd; j2++)
+            if (j2 != j) prod = mulmod(prod, md[j2] % md[j], md[j]);
+        dhat_inv[j] = invmod(prod, md[j]);
+    }
+    *out = ct_alloc(c, l - 1);
+    out->scale = scale / (double)c->mod[l];
+    for (int which = 0; which < 2; which++) {
+        const uint64_t *y = which ? y1 : y0;
+        uint64_t *o = ct_poly(c, out, which);
+#pragma omp parallel for schedule(dynamic)
+        for (int t = 0; t < l; t++) {
+            uint64_t q = c->mod[t], dhat_t[ORC_MAXP + 1], dq = 1 % q;
+            for (int j = 0; j < nd; j++) {
+                uint64_t prod = 1 % q;
+                for (int j2 = 0; j2 < nd; j2++)
+                    if (j2 != j) prod = mulmod(prod, md[j2] % q, q);
+                dhat_t[j] = prod;
+                dq = mulmod(dq, md[j] % q, q);
+            }
+            uint64_t dinv = invmod(dq, q);
+            for (int k = 0; k < N_; k++) {
+                uint64_t conv = 0;
+                for (int j = 0; j < nd; j++) {
+                    uint64_t v = mulmod(y[(size_t)(l + j) * N_ + k], dhat_inv[j], md[j]);
+                    i128 vc = v <= (md[j] - 1) / 2 ? (i128)v : (i128)v - (i128)md[j];
+                    conv = addmod(conv, mulmod(reduce_i128(vc, q), dhat_t[j], q), q);
+                }
+                o[(size_t)t * N_ + k] = mulmod(submod(y[(size_t)t * N_ + k], conv, q), dinv, q);
+            }
+        }
+    }
+    free(y0);
+    free(y1);
+    c->n_rescale++;
+    return 0;
+}
+
+/* Tensor, then relinearisation and rescale in one division.  Operands at different levels:
+ * the higher is dropped. */
 int hmult(orc_ctx *c, const orc_ct *a, const orc_ct *b, orc_ct *out) {
     int level = a->level < b->level ? a->level : b->level;
     if (level < 1) { snprintf(c->err, sizeof c->err, "hmult at level %d", level); return -1; }
     size_t sz = (size_t)(level + 1) * N_;
     uint64_t *d0 = malloc(sizeof(uint64_t) * sz), *d1 = malloc(sizeof(uint64_t) * sz), *d2 = malloc(sizeof(uint64_t) * sz);
     tensor(c, a, b, d0, d1, d2, level);
-    relinearize(c, d0, d1, d2, level, a->scale * b->scale, out);
+    int rc = relin_rescale(c, d0, d1, d2, level, a->scale * b->scale, out);
     free(d0);
     free(d1);
     free(d2);
     c->n_hmult++;
-    return rescale(c, out);
+    return rc;
 }
 
 int galois_for_rot(const orc_ctx *c, long r) {

@@ -130,6 +130,8 @@ uint64_t *modup(orc_ctx *c, const uint64_t *d, int level);
 int ks_inner_moddown(orc_ctx *c, uint64_t *digits, int level, int galois, orc_key *k, uint64_t *out0, uint64_t *out1);
 int ks_inner(orc_ctx *c, uint64_t *digits, int level, int galois, orc_key *k, uint64_t *acc0, uint64_t *acc1);
 int moddown(orc_ctx *c, const uint64_t *acc0, const uint64_t *acc1, int level, uint64_t *out0, uint64_t *out1);
+int relin_rescale(orc_ctx *c, const uint64_t *d0, const uint64_t *d1, const uint64_t *d2, int level, double scale,
+                  orc_ct *out);
 int relinearize(orc_ctx *c, const uint64_t *d0, const uint64_t *d1, const uint64_t *d2, int level, double scale, orc_ct *out);
 int hmult(orc_ctx *c, const orc_ct *a, const orc_ct *b, orc_ct *out);
 int rotate_hoisted(orc_ctx *c, const orc_ct *x, const int *galois, int nrot, orc_ct *out);

@@ -11,7 +11,7 @@
  *   y_c   = P_exp(u_c)                                     (exp(x/2^k))
  *   for j = 1..k:
  *     (fallback: bootstrapping of every y_c if level(y) < bts_min + 1)
- *     S    = Relin(sum_c y_c (x) y_c), rescaled           (Step 1 of Alg. 3, one key switch)
+ *     S    = Relin(sum_c y_c (x) y_c), rescaled in the same division (Step 1 of Alg. 3, one key switch)
  *     S    = RotSum(S, L, log2(n/m))                      (Steps 3-5)
  *     if level(S) - depth_j - 1 >= bts_min: v = gain_s S by scale bookkeeping
  *     else                                 : v = Bootstrap(S, gain_s)
@@ -150,10 +150,9 @@ int softmax(orc_ctx *c, const orc_plan *p, const orc_bts *b, orc_ct *cts, int m)
         }
         free(e0); free(e1); free(e2);
         orc_ct S;
-        relinearize(c, d0, d1, d2, ly, cts[0].scale * cts[0].scale, &S);
+        if (relin_rescale(c, d0, d1, d2, ly, cts[0].scale * cts[0].scale, &S)) return -1;
         free(d0); free(d1); free(d2);
         c->n_hmult++;
-        if (rescale(c, &S)) return -1;
         if (rotsum(c, &S, stride, nrot)) return -1;
         dbg(c, "S", j, &S);
         int dj = ilog2(p->inv_deg[j] + 1);

@@ -87,6 +87,12 @@ struct he_ctx {
     uint64_t *d_cv = nullptr;
     uint64_t *d_mdcv = nullptr, *d_pinv = nullptr, *d_qlinv = nullptr;
     int *d_pidx = nullptr;
+    // relinearisation + rescale as one division by P q_l (per level l): conversion constants
+    // from D = {q_l} u P (layout of the ModDown table, alpha + 1 sources), the sources' prime
+    // indices, and per kept limb i: (P mod q_i, Shoup), ((P q_l)^{-1} mod q_i, Shoup)
+    uint64_t *d_rrcv = nullptr, *d_rrpq = nullptr;
+    int *d_rridx = nullptr;
+    size_t rrcv_stride = 0;
     double2 *d_zeta = nullptr;
     int *d_rg = nullptr;
     std::vector<double2> zeta;
@@ -279,7 +285,9 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     dim3 g1(N2 / C, count), g2(N1 / R, count);
     size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
     // algorithmic bytes: the transform's read + write, plus what a fused ModDown epilogue reads
-    double extra = fuse && fuse->kind == 1 ? 8.0 * count * c->N * (fuse->add ? 2 : 1) : 0.0;
+    double extra = !fuse ? 0.0
+                   : fuse->kind == 1 ? 8.0 * count * c->N * (fuse->add ? 2 : 1)
+                   : fuse->kind == 3 ? 16.0 * count * c->N : 0.0;
     ProfScope ps(c, site, 16.0 * count * c->N + extra);
     c->launches++;
     if (rb) {
@@ -605,6 +613,72 @@ static DCt relinearize(he_ctx *c, const uint64_t *d, int level, int nct, double 
     return y;
 }
 
+// Relinearisation and rescale as one division by P q_l: K = KS(d2) over Q_l u P,
+// Y = P (d0, d1) + K, out_i = (Y_i - Conv_{D->q_i}([Y]_D)) (P q_l)^{-1} with D = {q_l} u P
+// (the dropped limbs l .. l + alpha of Y, contiguous).  d: [nct][3][l+1][N] NTT form.
+static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, double scale) {
+    int l = level, L = l + 1, al = c->alpha, nl = L + al, nd = al + 1;
+    REQUIRE(l >= 1, HE_ELEVEL, "relinearise + rescale at level 0");
+    DPtr dig = ks_modup(c, d + 2L * L * c->N, 3L * L * c->N, nct, L);
+    DPtr acc = dalloc(c, (size_t)nct * 2 * nl * c->N);
+    ks_inner_into(c, acc.get(), dig.get(), nct, L, 0, get_key(c, 0), false);
+    dig.reset();
+    // Y_l = K_l + P d_l (P d vanishes mod every p_k); polynomials 0 and 1 of every ciphertext
+    Scal pm;
+    {
+        uint64_t q = c->mods[l], v = 1 % q;
+        for (int k = 0; k < al; k++) v = h_mulmod(v, c->mods[c->nq + k] % q, q);
+        pm.v[0] = v;
+    }
+    for (int p = 0; p < 2; p++) {
+        {
+            ProfScope ps_(c, "elementwise", 0);
+            k_axpy_scalar<<<grid_for(c, (long)nct << c->logN), 256, 0, c->st>>>(
+                acc.get() + (long)p * nl * c->N + (long)l * c->N, 2L * nl * c->N, d + (long)p * L * c->N + (long)l * c->N,
+                3L * L * c->N, pm, nct, 1, single(l), c->d_mods, c->logN);
+        }
+        LAUNCH_CHECK();
+    }
+    // the dropped limbs to coefficient form, converted to q_0 .. q_{l-1}
+    LimbMap dm;
+    dm.nper = nd;
+    dm.prime[0] = l;
+    for (int k = 0; k < al; k++) dm.prime[1 + k] = c->nq + k;
+    ntt(c, acc.get() + (long)l * c->N, 2 * nct * nd, dm, (long)nl * c->N, true, "ntt_moddown");
+    DPtr conv = dalloc(c, (size_t)2 * nct * l * c->N);
+    {
+        ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (nd + l));
+        k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(
+            conv.get(), acc.get(), 2 * nct, l, nd, qmap(l), c->d_rridx + (size_t)l * nd, c->d_mods,
+            c->d_rrcv + (size_t)l * c->rrcv_stride, c->nq, c->logN);
+    }
+    LAUNCH_CHECK();
+    DCt y = ct_new(c, l - 1, nct, scale / (double)c->mods[l]);
+    const uint64_t *cst = c->d_rrpq + (size_t)l * c->nq * 4;
+    if (ntt_rb(c)) {
+        NttFuse F{};
+        F.kind = 3;
+        F.alpha = nd;
+        F.x = acc.get();
+        F.add = d;
+        F.sadd = 3L * L * c->N;
+        F.out = y.d;
+        F.so = y.cs(c);
+        F.cst = cst;
+        ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown", nullptr, 0, &F);
+    } else {
+        ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown");
+        {
+            ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * l * 4);
+            k_relin_rescale_fin<<<grid_for(c, (long)2 * nct * l << c->logN), 256, 0, c->st>>>(
+                y.d, acc.get(), nl, d, conv.get(), 2 * nct, l, qmap(l), c->d_mods, cst, c->logN);
+        }
+        LAUNCH_CHECK();
+    }
+    c->cnt[3]++;
+    return y;
+}
+
 static void tensor_into(he_ctx *c, uint64_t *d, const DCt &a, const DCt &b, int level, bool accumulate) {
     int L = level + 1;
     long tot = (long)a.nct * L << c->logN;
@@ -629,9 +703,9 @@ static DCt hmult(he_ctx *c, const DCt &a, const DCt &b) {
         for (int i = 0; i < nct; i++)
             tensor_into(c, d.get() + (long)i * 3 * (level + 1) * c->N, ct_sub(c, many, i), one, level, false);
     }
-    DCt r = relinearize(c, d.get(), level, nct, a.scale * b.scale);
+    DCt r = relin_rescale(c, d.get(), level, nct, a.scale * b.scale);
     c->cnt[2]++;
-    return rescale(c, r);
+    return r;
 }
 
 // lam (G ciphertexts) times y (G groups of m ciphertexts): ciphertext i of y with lam[i / m]
@@ -642,9 +716,9 @@ static DCt hmult_grouped(he_ctx *c, const DCt &lam, const DCt &y, int m) {
     DPtr d = dalloc(c, (size_t)y.nct * 3 * (level + 1) * c->N);
     for (int i = 0; i < y.nct; i++)
         tensor_into(c, d.get() + (long)i * 3 * (level + 1) * c->N, ct_sub(c, y, i), ct_sub(c, lam, i / m), level, false);
-    DCt r = relinearize(c, d.get(), level, y.nct, lam.scale * y.scale);
+    DCt r = relin_rescale(c, d.get(), level, y.nct, lam.scale * y.scale);
     c->cnt[2]++;
-    return rescale(c, r);
+    return r;
 }
 
 // Rot by galois elements: ModUp(c1) once, then for every g: X -> X^g on the digits and c0,
@@ -1496,9 +1570,8 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
                 first = false;
             }
         }
-        DCt S = relinearize(c, d.get(), ly, G, ys[0].scale * ys[0].scale);
+        DCt S = relin_rescale(c, d.get(), ly, G, ys[0].scale * ys[0].scale);
         c->cnt[2]++;
-        S = rescale(c, S);
         S = rotsum(c, S, stride, nrot);
         dbg_dump(c, "S", j, S);
         int dj = ilog2c(p.inv_deg[j] + 1);
@@ -1692,6 +1765,54 @@ static void build_tables(he_ctx *c) {
         }
     CK(cudaMalloc(&c->d_qlinv, ql.size() * 8));
     CK(cudaMemcpy(c->d_qlinv, ql.data(), ql.size() * 8, cudaMemcpyHostToDevice));
+    {
+        // relinearisation + rescale: D = {q_l, p_0 .. p_{alpha-1}}
+        int nd = al + 1;
+        c->rrcv_stride = 2 * (size_t)nd + (size_t)nd * c->nq;
+        std::vector<uint64_t> rrcv((size_t)c->nq * c->rrcv_stride, 0), rrpq((size_t)c->nq * 4 * c->nq, 0);
+        std::vector<int> rridx((size_t)c->nq * nd, 0);
+        for (int l = 1; l < c->nq; l++) {
+            uint64_t md[HE_MAX_LIMBS];
+            int mi[HE_MAX_LIMBS];
+            md[0] = c->mods[l];
+            mi[0] = l;
+            for (int k = 0; k < al; k++) {
+                md[1 + k] = c->mods[c->nq + k];
+                mi[1 + k] = c->nq + k;
+            }
+            uint64_t *cv = rrcv.data() + (size_t)l * c->rrcv_stride;
+            for (int j = 0; j < nd; j++) {
+                rridx[(size_t)l * nd + j] = mi[j];
+                uint64_t prod = 1 % md[j];
+                for (int j2 = 0; j2 < nd; j2++)
+                    if (j2 != j) prod = h_mulmod(prod, md[j2] % md[j], md[j]);
+                cv[j] = h_inv(prod, md[j]);
+                cv[nd + j] = h_shoup(cv[j], md[j]);
+                for (int i = 0; i < c->nq; i++) {
+                    uint64_t q = c->mods[i], pr = 1 % q;
+                    for (int j2 = 0; j2 < nd; j2++)
+                        if (j2 != j) pr = h_mulmod(pr, md[j2] % q, q);
+                    cv[2 * nd + (size_t)j * c->nq + i] = h_mont(pr, q);
+                }
+            }
+            for (int i = 0; i < l; i++) {
+                uint64_t q = c->mods[i], pm = 1 % q;
+                for (int k = 0; k < al; k++) pm = h_mulmod(pm, c->mods[c->nq + k] % q, q);
+                uint64_t w = h_inv(h_mulmod(pm, c->mods[l] % q, q), q);
+                uint64_t *e = rrpq.data() + ((size_t)l * c->nq + i) * 4;
+                e[0] = pm;
+                e[1] = h_shoup(pm, q);
+                e[2] = w;
+                e[3] = h_shoup(w, q);
+            }
+        }
+        CK(cudaMalloc(&c->d_rrcv, rrcv.size() * 8));
+        CK(cudaMemcpy(c->d_rrcv, rrcv.data(), rrcv.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&c->d_rrpq, rrpq.size() * 8));
+        CK(cudaMemcpy(c->d_rrpq, rrpq.data(), rrpq.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&c->d_rridx, rridx.size() * sizeof(int)));
+        CK(cudaMemcpy(c->d_rridx, rridx.data(), rridx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     // canonical embedding tables: zeta^j = exp(2 pi i j / 2N), 5^j mod 2N
     int m = 2 * N;
     c->zeta.resize(m);
@@ -1851,7 +1972,8 @@ void he_context_destroy(he_ctx *c) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
-    void *ptrs[] = {c->d_mods, c->d_tw, c->d_tw2, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx, c->d_zeta,
+    void *ptrs[] = {c->d_mods, c->d_tw, c->d_tw2, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx,
+                    c->d_rrcv, c->d_rrpq, c->d_rridx, c->d_zeta,
                     c->d_rg, c->d_cdt, c->d_radix, c->d_radinv, c->d_qd, c->d_s, c->d_pk};
     for (void *q : ptrs)
         if (q) cudaFree(q);

@@ -170,6 +170,34 @@ __global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa,
     }
 }
 
+// relinearisation + rescale, final step where the transform is not fused (see NttFuse kind 3):
+// out_i = (P d_i + K_i - conv_i) (P q_l)^{-1} for the npoly output polynomials of l limbs
+__global__ void k_relin_rescale_fin(uint64_t *out, const uint64_t *K, int nl, const uint64_t *d, const uint64_t *conv,
+                                    int npoly, int l, LimbMap qmap, const ModC *mods, const uint64_t *cst, int logN) {
+    const int N = 1 << logN;
+    long total = (long)npoly * l << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int r = (int)(id >> logN), k = (int)(id & (N - 1));
+        int i = r % l, pl = r / l;
+        const uint64_t q = mods[qmap.prime[i]].q;
+        const uint64_t *e = cst + 4 * i;
+        uint64_t y = add_mod(mul_shoup(d[(long)(pl / 2) * 3 * (l + 1) * N + (long)(pl % 2) * (l + 1) * N + (long)i * N + k],
+                                       e[0], e[1], q),
+                             K[(long)pl * nl * N + (long)i * N + k], q);
+        out[(long)(pl / 2) * 2 * l * N + (long)(pl % 2) * l * N + (long)i * N + k] =
+            mul_shoup(sub_mod(y, conv[(long)r * N + k], q), e[2], e[3], q);
+    }
+}
+
+// out += a * scal[li] on the selected limbs
+__global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal, int count, int nper,
+                              LimbMap map, const ModC *mods, int logN) {
+    EW_PROLOGUE
+    long off = (long)li * N + k;
+    out[po * so + off] = add_mod(out[po * so + off], mul_mod(a[po * sa + off], scal.v[li], m), m.q);
+    }
+}
+
 // adds scal[li] to every evaluation point of the selected polynomials (a constant polynomial
 // has the same value at every root)
 __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int nper, LimbMap map,
@@ -865,12 +893,22 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
             if (F.add) r = add_mod(F.add[oa + E * j], r, q);
             F.out[o + E * j] = r;
         }
-    } else {
+    } else if (KIND == 2) {
         const uint64_t w = F.cst[2 * i], wp = F.cst[2 * i + 1];
         const uint64_t *xp = F.x + (long)pl * (nper + 1) * N + at;
         uint64_t *op = F.out + (long)pl * nper * N + at;
 #pragma unroll
         for (int j = 0; j < E; j++) op[E * j] = mul_shoup(sub_mod(xp[E * j], sm[rr * SP + k + (E + 1) * j], q), w, wp, q);
+    } else {
+        const uint64_t pm = F.cst[4 * i], pmp = F.cst[4 * i + 1], w = F.cst[4 * i + 2], wp = F.cst[4 * i + 3];
+        const uint64_t *kp = F.x + (long)pl * (nper + F.alpha) * N + at;
+        const uint64_t *dp = F.add + (long)(pl / 2) * F.sadd + (long)(pl % 2) * (nper + 1) * N + at;
+        uint64_t *op = F.out + (long)(pl / 2) * F.so + (long)(pl % 2) * nper * N + at;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const uint64_t y = add_mod(mul_shoup(dp[E * j], pm, pmp, q), kp[E * j], q);
+            op[E * j] = mul_shoup(sub_mod(y, sm[rr * SP + k + (E + 1) * j], q), w, wp, q);
+        }
     }
 }
 
@@ -950,6 +988,9 @@ static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long po
     if (!inverse && F.kind == 1) {
         k_ntt_cols_fwd_rb<LOGE, 1><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
         k_ntt_rows_fwd_rb<LOGE, 1><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+    } else if (!inverse && F.kind == 3) {
+        k_ntt_cols_fwd_rb<LOGE, 3><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 3><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse && F.kind == 2) {
         k_ntt_cols_fwd_rb<LOGE, 2><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
         k_ntt_rows_fwd_rb<LOGE, 2><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);

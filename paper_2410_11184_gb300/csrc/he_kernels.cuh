@@ -28,7 +28,11 @@ struct LtArgs {
 //       out / add polynomial p at base + (p / 2) stride + (p % 2) nper N, pinv = cst[2 prime], cst[2 prime + 1];
 //   kind 2 (rescale): the column pass reads the centred last limb last[p] reduced mod q_i
 //       instead of the batch, the row pass writes out_i = (x_i - NTT(t)_i) qlinv_i,
-//       x_i at x + p (nper + 1) N + i N, out_i at out + p nper N + i N, qlinv = cst[2 i], cst[2 i + 1].
+//       x_i at x + p (nper + 1) N + i N, out_i at out + p nper N + i N, qlinv = cst[2 i], cst[2 i + 1];
+//   kind 3 (relinearise + rescale): the batch is Conv_{D->Q}, D = {q_l} u P; the row pass writes
+//       out_i = (P d_i + K_i - NTT(conv)_i) (P q_l)^{-1}, K_i at x + p (nper + alpha) N + i N,
+//       d_i (tensor) at add + (p / 2) sadd + (p % 2) (nper + 1) N + i N, out as in kind 1,
+//       cst[4 i ..]: P mod q_i, Shoup, (P q_l)^{-1} mod q_i, Shoup.
 struct NttFuse {
     int kind;
     int alpha;
@@ -71,6 +75,10 @@ __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int npe
 __global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
                          int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
 __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN);
+__global__ void k_relin_rescale_fin(uint64_t *out, const uint64_t *K, int nl, const uint64_t *d, const uint64_t *conv,
+                                    int npoly, int l, LimbMap qmap, const ModC *mods, const uint64_t *cst, int logN);
+__global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal, int count, int nper,
+                              LimbMap map, const ModC *mods, int logN);
 __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, LimbMap map,
                                 const ModC *mods, int g, int logN);
 __global__ void k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN);

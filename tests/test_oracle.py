@@ -220,6 +220,40 @@ def test_relinearisation_noise_is_small(params):
     assert worst < 2 ** 20  # key-switching error, far below Q ~ 2^220
 
 
+def test_relin_rescale_is_rounded_division(params):
+    """The merged relinearisation + rescale: (M0 + M1 s) equals (d0 + d1 s + d2 s^2) / q_l over
+    Q_{l-1} up to the key-switching and conversion error, checked with exact integers."""
+    o = small_oracle(params, log_n=6)
+    rng = np.random.default_rng(16)
+    s = o.secret().astype(np.int64)
+    lv = 4
+    d = np.zeros((3, lv + 1, o.n), dtype=np.uint64)
+    for t in range(lv + 1):
+        d[:, t] = rng.integers(0, o.q[t], (3, o.n), dtype=np.uint64)
+    got_ct = o.relin_rescale(d, lv)
+    mods, mods_out = o.q[:lv + 1], o.q[:lv]
+    Q, Qo = math.prod(mods), math.prod(mods_out)
+
+    def dec(parts, ms):
+        # coefficients of parts[0] + parts[1] s (+ parts[2] s^2) per limb, CRT-combined, centred
+        limbs = []
+        for t, q in enumerate(ms):
+            st = np.array([x % q for x in s.tolist()], dtype=np.uint64)
+            acc = parts[0][t].astype(object) + o.polymul(t, parts[1][t], st).astype(object)
+            if len(parts) > 2:
+                acc = acc + o.polymul(t, parts[2][t], o.polymul(t, st, st)).astype(object)
+            limbs.append([int(v) % q for v in acc])
+        M = math.prod(ms)
+        return [centred(crt([limbs[t][i] for t in range(len(ms))], ms)[0], M) for i in range(o.n)]
+
+    want = dec(d, mods)
+    got = dec(got_ct, mods_out)
+    ql = o.q[lv]
+    worst = max(abs(g - w / ql) for g, w in zip(got, want))
+    assert worst < 2 ** 12  # key-switch error / P plus the conversion error, far below Q_{l-1}
+    assert Qo > 2 ** 100
+
+
 def test_ciphertext_semantics(toy_oracle):
     o = toy_oracle
     rng = np.random.default_rng(7)
