@@ -504,6 +504,26 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true, "ntt_modup", x, sx);
     DPtr dig = dalloc(c, (size_t)nct * nd * nl * c->N);
     LimbMap em = extmap(c, L);
+    if (nct <= 4) {
+        // small batches: every digit converted in one launch and transformed in one more (the
+        // per-digit launches would each fill a fraction of the GPU); the digit's own limbs are
+        // converted too, which reproduces them exactly
+        ModUpDigits D{};
+        for (int j = 0; j < nd; j++) {
+            D.lo[j] = j * al;
+            D.ds[j] = std::min(al, L - j * al);
+            D.cvoff[j] = (long)c->cv_off[L - 1][j] - (long)c->cv_off[L - 1][0];
+        }
+        dim3 grid(grid_for(c, (long)nct << c->logN).x, nd);
+        {
+            ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * L + (double)nct * nd * nl));
+            k_modup_all<<<grid, 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, tmp.get(), (long)L * c->N, nct, D, nl,
+                                                 em, c->d_mods, c->d_cv + c->cv_off[L - 1][0], c->logN);
+        }
+        LAUNCH_CHECK();
+        ntt(c, dig.get(), nct * nd * nl, em, (long)nl * c->N, false, "ntt_modup");
+        return dig;
+    }
     for (int j = 0; j < nd; j++) {
         int lo = j * al, ds = std::min(al, L - lo);
         long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)

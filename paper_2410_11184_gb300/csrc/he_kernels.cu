@@ -371,6 +371,42 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
     }
 }
 
+// ModUp of all digits of nct polynomials in one launch (grid.y = digit j): every target limb of
+// the extended basis is converted, the digit's own limbs included (there the conversion is the
+// CRT identity and returns x exactly), so one transform of all digits follows.  Output
+// [nct][ndig][ntarget][N] (coefficient form).
+__global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long sx, int nct, ModUpDigits D,
+                            int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN) {
+    const int N = 1 << logN;
+    const int j = blockIdx.y, lo = D.lo[j], ds = D.ds[j];
+    const uint64_t *cv = cvbase + D.cvoff[j];
+    long total = (long)nct << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int c = (int)(id >> logN), k = (int)(id & (N - 1));
+        uint64_t y[8];
+        unsigned negmask = 0;
+        for (int i = 0; i < ds; i++) {
+            uint64_t qi = mods[tmap.prime[lo + i]].q;
+            uint64_t v = mul_shoup(x[c * sx + (long)(lo + i) * N + k], cv[i], cv[ds + i], qi);
+            if (v > (qi - 1) / 2) {
+                v = qi - v;
+                negmask |= 1u << i;
+            }
+            y[i] = v;
+        }
+        uint64_t *o = out + c * so_ct + (long)j * ntarget * N + k;
+        for (int t = 0; t < ntarget; t++) {
+            const ModC mt = mods[tmap.prime[t]];
+            uint64_t l0 = 0, h0 = 0;
+            for (int i = 0; i < ds; i++) {
+                uint64_t w = cv[2 * ds + i * ntarget + t];
+                mac_wide(l0, h0, y[i], (negmask >> i) & 1 ? mt.q - w : w);
+            }
+            o[(long)t * N] = redc(l0, h0, mt);
+        }
+    }
+}
+
 // ModDown conversion: conv_i = sum_k [y_k * phinv_k]_{p_k} (phat_k mod q_i); writes conv into
 // out (coefficient domain) for the Q limbs.  x: [npoly][L + alpha][N] with the coefficient-domain
 // P limbs at offset L.  cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][nqall] (by Q index).

@@ -46,6 +46,13 @@ struct NttFuse {
     uint64_t ql;
 };
 
+// ModUp of every digit in one launch (grid.y = digit): digit j covers limbs [lo[j], lo[j] + ds[j])
+// and its constants start at cvoff[j] (the layout k_modup uses)
+struct ModUpDigits {
+    int lo[8], ds[8];
+    long cvoff[8];
+};
+
 // Linear combination sum_t w_t x_t (+ w0 on c0) of up to HE_LC_MAXT batches at any levels
 #define HE_LC_MAXT 8
 struct LcArgs {
@@ -86,6 +93,8 @@ __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap,
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN, const uint64_t *xntt, long sxn);
+__global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long sx, int nct, ModUpDigits D,
+                            int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN);
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN);
 __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
