@@ -557,9 +557,10 @@ static void ks_inner_into(he_ctx *c, uint64_t *acc, const uint64_t *dig, int nct
     {
         ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl *
                                                                             (accumulate ? 2 : 1)));
+        KsMulti M{};
         k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc, dig, nct, nd, L, al, extmap(c, L), c->d_mods,
                                                                         key, c->nm, c->nq, g, c->logN,
-                                                                        accumulate ? 1 : 0);
+                                                                        accumulate ? 1 : 0, M);
     }
     LAUNCH_CHECK();
     c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
@@ -762,6 +763,50 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
     bool need = false;
     for (int g : gal) need |= g != 1;
     if (need) dig = ks_modup(c, x.d + (long)L * c->N, x.cs(c), x.nct, L);
+    std::vector<int> gs;
+    for (int g : gal)
+        if (g != 1) gs.push_back(g);
+    if (x.nct <= 4 && gs.size() >= 2 && gs.size() <= 16) {
+        // small batches: the key switches of all rotations in one inner-product launch and one
+        // ModDown over all of them (each separately would fill a fraction of the GPU)
+        int al = c->alpha, nd = (L + al - 1) / al, nl = L + al, ng = (int)gs.size();
+        KsMulti M{};
+        M.n = ng;
+        M.acc_stride = (long)x.nct * 2 * nl * c->N;
+        for (int r = 0; r < ng; r++) {
+            M.key[r] = get_key(c, gs[r]);
+            M.g[r] = gs[r];
+        }
+        DPtr acc = dalloc(c, (size_t)ng * M.acc_stride);
+        {
+            ProfScope ps(c, "ks_inner", 8.0 * c->N * ng * ((double)x.nct * nd * nl + 2.0 * nd * nl + 2.0 * x.nct * nl));
+            dim3 grid(grid_for(c, (long)nl << c->logN).x, ng);
+            k_ks_inner<<<grid, 256, 0, c->st>>>(acc.get(), dig.get(), x.nct, nd, L, al, extmap(c, L), c->d_mods, nullptr,
+                                                 c->nm, c->nq, 0, c->logN, 0, M);
+        }
+        LAUNCH_CHECK();
+        c->cnt[0] += (long)ng * x.nct;
+        long cs = x.cs(c);
+        DPtr ys = dalloc(c, (size_t)ng * x.nct * cs);
+        ks_moddown(c, acc.get(), ng * x.nct, L, ys.get(), cs, nullptr, 0);
+        size_t r = 0;
+        for (int g : gal) {
+            if (g == 1) {
+                out.push_back(ct_copy(c, x));
+                continue;
+            }
+            DCt y;
+            y.buf = ys;
+            y.d = ys.get() + (long)r++ * x.nct * cs;
+            y.level = x.level;
+            y.scale = x.scale;
+            y.nct = x.nct;
+            automorph_acc(c, y, x, g);
+            out.push_back(y);
+            c->cnt[1]++;
+        }
+        return out;
+    }
     for (int g : gal) {
         if (g == 1) {
             out.push_back(ct_copy(c, x));

@@ -471,9 +471,14 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
 // per (t, k) for all ciphertexts of the batch.
 __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
                            int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
-                           int nq_all, int g, int logN, int accumulate) {
+                           int nq_all, int g, int logN, int accumulate, KsMulti M) {
     const int N = 1 << logN;
     const int nl = L + alpha;
+    if (M.n) {   // key switch blockIdx.y of several (same digits, own key and galois element)
+        key = M.key[blockIdx.y];
+        g = M.g[blockIdx.y];
+        acc += blockIdx.y * M.acc_stride;
+    }
     long total = (long)nl << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
         int t = (int)(id >> logN), k = (int)(id & (N - 1));
