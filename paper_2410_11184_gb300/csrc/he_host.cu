@@ -1383,7 +1383,13 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         bidx[b] = A.nb;
         A.baby[A.nb++] = b == 0 ? x.d : rots[ri++].d;
     }
-    // giant steps a (plaintexts are sorted by a): out_a = sum_b pt_{a,b} (.) baby_b in one pass
+    // giant steps a (plaintexts are sorted by a): out_a = sum_b pt_{a,b} (.) baby_b in one pass;
+    // small batches keep all the sums in one buffer (their c1 parts are then one ModUp batch)
+    int na_max = 0;
+    for (size_t pi = 0; pi < Lv.pts.size(); pi++)
+        if (pi == 0 || Lv.pts[pi].a != Lv.pts[pi - 1].a) na_max++;
+    const bool small = x.nct <= 4 && na_max >= 3;
+    DPtr innerbuf = small ? dalloc(c, (size_t)na_max * x.nct * x.cs(c)) : DPtr();
     std::vector<int> gi;
     std::vector<DCt> inner;
     memset(A.ptix, -1, sizeof A.ptix);
@@ -1393,7 +1399,17 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         if (gi.empty() || gi.back() != a) {
             REQUIRE(gi.size() < HE_LT_MAXA, HE_EINVAL, "lintrans: too many giant steps");
             gi.push_back(a);
-            inner.push_back(ct_new(c, x.level, x.nct, x.scale * pt_scale));
+            if (small) {
+                DCt v;
+                v.buf = innerbuf;
+                v.d = innerbuf.get() + (long)A.na * x.nct * x.cs(c);
+                v.level = x.level;
+                v.scale = x.scale * pt_scale;
+                v.nct = x.nct;
+                inner.push_back(v);
+            } else {
+                inner.push_back(ct_new(c, x.level, x.nct, x.scale * pt_scale));
+            }
             A.out[A.na++] = inner.back().d;
         }
         A.ptix[A.na - 1][bidx.at(Lv.pts[pi].b)] = (signed char)A.npt;
@@ -1426,6 +1442,38 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
     }
     DPtr ext;
     bool have_ext = false;
+    if (small) {
+        // one ModUp of every giant step's c1 (a = 0 included, unused), one launch summing all
+        // their key-switch inner products, one ModDown
+        int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
+        DPtr dig = ks_modup(c, innerbuf.get() + (long)L * c->N, x.cs(c), (int)gi.size() * x.nct, L);
+        KsMulti M{};
+        for (size_t i = 0; i < gi.size(); i++) {
+            if (gi[i] == 0) continue;
+            int ga = galois_for_rot(c, (long)gi[i] * Lv.g * Lv.hmin);
+            REQUIRE(M.n < 16, HE_EINVAL, "lintrans: too many giant steps");
+            M.key[M.n] = get_key(c, ga);
+            M.g[M.n] = ga;
+            M.dig_off[M.n] = (long)i * x.nct * nd * nl * c->N;
+            M.n++;
+            automorph_acc(c, acc, inner[i], ga);
+            c->cnt[1]++;
+        }
+        if (M.n) {
+            ext = dalloc(c, (size_t)x.nct * 2 * nl * c->N);
+            {
+                ProfScope ps(c, "ks_inner", 8.0 * c->N * M.n * ((double)x.nct * nd * nl + 2.0 * nd * nl) +
+                                                8.0 * c->N * 2.0 * x.nct * nl);
+                k_ks_inner_sum<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(
+                    ext.get(), dig.get(), x.nct, nd, L, al, extmap(c, L), c->d_mods, c->nm, c->nq, c->logN, M);
+            }
+            LAUNCH_CHECK();
+            c->cnt[0] += (long)M.n * x.nct;
+            ks_moddown(c, ext.get(), x.nct, L, acc.d, acc.cs(c), acc.d, acc.cs(c));
+        }
+        acc.scale = x.scale * pt_scale;
+        return rescale(c, acc);
+    }
     for (size_t i = 0; i < gi.size(); i++) {
         if (gi[i] == 0) continue;
         int ga = galois_for_rot(c, (long)gi[i] * Lv.g * Lv.hmin);

@@ -512,6 +512,42 @@ __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restric
     }
 }
 
+// The sum of M.n key switches (key M.key[r], galois element M.g[r], digits at dig + M.dig_off[r])
+// written into acc: each thread runs them in turn for its (limb, coefficient), reducing after each.
+__global__ void k_ks_inner_sum(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig,
+                               int L, int alpha, LimbMap tmap, const ModC *mods, int key_nlimb, int nq_all, int logN,
+                               KsMulti M) {
+    const int N = 1 << logN;
+    const int nl = L + alpha;
+    long total = (long)nl << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        int t = (int)(id >> logN), k = (int)(id & (N - 1));
+        const ModC m = mods[tmap.prime[t]];
+        int kt = t < L ? t : nq_all + (t - L);
+        for (int r = 0; r < M.n; r++) {
+            const uint64_t *kr = M.key[r];
+            const uint64_t *dr = dig + M.dig_off[r];
+            int src = M.g[r] > 1 ? auto_index(k, M.g[r], logN) : k;
+            for (int c = 0; c < nct; c++) {
+                uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+                for (int j = 0; j < ndig; j++) {
+                    uint64_t d = dr[(((long)c * ndig + j) * nl + t) * N + src];
+                    mac_wide(l0, h0, d, kr[((long)(2 * j) * key_nlimb + kt) * N + k]);
+                    mac_wide(l1, h1, d, kr[((long)(2 * j + 1) * key_nlimb + kt) * N + k]);
+                }
+                uint64_t r0 = redc(l0, h0, m), r1 = redc(l1, h1, m);
+                const long o0 = ((long)(2 * c) * nl + t) * N + k, o1 = ((long)(2 * c + 1) * nl + t) * N + k;
+                if (r > 0) {
+                    r0 = add_mod(acc[o0], r0, m.q);
+                    r1 = add_mod(acc[o1], r1, m.q);
+                }
+                acc[o0] = r0;
+                acc[o1] = r1;
+            }
+        }
+    }
+}
+
 // Rescale, step 1: r = centred last limb (coefficient form, [npoly][N]); writes r mod q_i for
 // the remaining L-1 limbs into tmp [npoly][L-1][N].
 __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,

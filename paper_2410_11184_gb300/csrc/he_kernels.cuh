@@ -46,11 +46,13 @@ struct NttFuse {
     uint64_t ql;
 };
 
-// Several key switches of the same digits in one inner-product launch (grid.y = r): key[r],
-// galois element g[r], output at acc + r acc_stride.  n = 0: the single key and g arguments.
+// Several key switches in one inner-product launch.  k_ks_inner: the same digits, grid.y = r,
+// key[r], galois element g[r], output at acc + r acc_stride (n = 0: the single key and g
+// arguments).  k_ks_inner_sum: the sum of the n key switches with digits at dig + dig_off[r].
 struct KsMulti {
     const uint64_t *key[16];
     int g[16];
+    long dig_off[16];
     long acc_stride;
     int n;
 };
@@ -112,6 +114,9 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
 __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
                            int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
                            int nq_all, int g, int logN, int accumulate, KsMulti M);
+__global__ void k_ks_inner_sum(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig,
+                               int L, int alpha, LimbMap tmap, const ModC *mods, int key_nlimb, int nq_all, int logN,
+                               KsMulti M);
 __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,
                                  const ModC *mods, uint64_t ql, int logN);
 __global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *t, int npoly, int L, LimbMap qmap,
