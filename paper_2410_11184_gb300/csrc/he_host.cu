@@ -558,9 +558,8 @@ static void ks_inner_into(he_ctx *c, uint64_t *acc, const uint64_t *dig, int nct
         ProfScope ps(c, "ks_inner", 8.0 * c->N * ((double)nct * nd * nl + 2.0 * nd * nl + 2.0 * nct * nl *
                                                                             (accumulate ? 2 : 1)));
         KsMulti M{};
-        k_ks_inner<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(acc, dig, nct, nd, L, al, extmap(c, L), c->d_mods,
-                                                                        key, c->nm, c->nq, g, c->logN,
-                                                                        accumulate ? 1 : 0, M);
+        launch_ks_inner(grid_for(c, (long)nl << c->logN), c->st, acc, dig, nct, nd, L, al, extmap(c, L), c->d_mods, key,
+                        c->nm, c->nq, g, c->logN, accumulate ? 1 : 0, M);
     }
     LAUNCH_CHECK();
     c->cnt[0] += nct;  // ciphertext key switches (a batch of nct counts nct)
@@ -781,8 +780,8 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
         {
             ProfScope ps(c, "ks_inner", 8.0 * c->N * ng * ((double)x.nct * nd * nl + 2.0 * nd * nl + 2.0 * x.nct * nl));
             dim3 grid(grid_for(c, (long)nl << c->logN).x, ng);
-            k_ks_inner<<<grid, 256, 0, c->st>>>(acc.get(), dig.get(), x.nct, nd, L, al, extmap(c, L), c->d_mods, nullptr,
-                                                 c->nm, c->nq, 0, c->logN, 0, M);
+            launch_ks_inner(grid, c->st, acc.get(), dig.get(), x.nct, nd, L, al, extmap(c, L), c->d_mods, nullptr, c->nm,
+                            c->nq, 0, c->logN, 0, M);
         }
         LAUNCH_CHECK();
         c->cnt[0] += (long)ng * x.nct;

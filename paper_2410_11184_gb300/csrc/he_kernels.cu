@@ -469,9 +469,11 @@ __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const u
 //   acc_{0,1}[t] = sum_j d~_j[t][pi_g(k)] * key_j^{b,a}[kt][k],
 // with the key limb kt = t for Q limbs and nq_all + (t - L) for P limbs.  The key is read once
 // per (t, k) for all ciphertexts of the batch.
-__global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
-                           int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
-                           int nq_all, int g, int logN, int accumulate, KsMulti M) {
+// NDIG digits at compile time: the key words of a (limb, coefficient) stay in registers
+template <int NDIG>
+__global__ void k_ks_inner_t(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int L, int alpha,
+                             LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
+                             int nq_all, int g, int logN, int accumulate, KsMulti M) {
     const int N = 1 << logN;
     const int nl = L + alpha;
     if (M.n) {   // key switch blockIdx.y of several (same digits, own key and galois element)
@@ -485,8 +487,9 @@ __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restric
         const ModC m = mods[tmap.prime[t]];
         int kt = t < L ? t : nq_all + (t - L);
         int src = g > 1 ? auto_index(k, g, logN) : k;
-        uint64_t kb[8], ka[8];
-        for (int j = 0; j < ndig; j++) {
+        uint64_t kb[NDIG], ka[NDIG];
+#pragma unroll
+        for (int j = 0; j < NDIG; j++) {
             kb[j] = key[((long)(2 * j) * key_nlimb + kt) * N + k];
             ka[j] = key[((long)(2 * j + 1) * key_nlimb + kt) * N + k];
         }
@@ -495,8 +498,9 @@ __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restric
             // the key is stored in Montgomery form: sum of d_j (k_j 2^64 mod m) < ndig m^2,
             // below m 2^64, reduced once
             uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
-            for (int j = 0; j < ndig; j++) {
-                uint64_t d = dig[(((long)c * ndig + j) * nl + t) * N + src];
+#pragma unroll
+            for (int j = 0; j < NDIG; j++) {
+                uint64_t d = dig[(((long)c * NDIG + j) * nl + t) * N + src];
                 mac_wide(l0, h0, d, kb[j]);
                 mac_wide(l1, h1, d, ka[j]);
             }
@@ -510,6 +514,21 @@ __global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restric
             acc[o1] = r1;
         }
     }
+}
+
+void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *dig, int nct, int ndig, int L, int alpha,
+                     const LimbMap &tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all, int g,
+                     int logN, int accumulate, const KsMulti &M) {
+#define HE_KS_CASE(D)                                                                                          \
+    case D:                                                                                                    \
+        k_ks_inner_t<D><<<grid, 256, 0, st>>>(acc, dig, nct, L, alpha, tmap, mods, key, key_nlimb, nq_all, g, logN, \
+                                              accumulate, M);                                                  \
+        break;
+    switch (ndig) {
+        HE_KS_CASE(1) HE_KS_CASE(2) HE_KS_CASE(3) HE_KS_CASE(4) HE_KS_CASE(5) HE_KS_CASE(6) HE_KS_CASE(7)
+        HE_KS_CASE(8)
+    }
+#undef HE_KS_CASE
 }
 
 // The sum of M.n key switches (key M.key[r], galois element M.g[r], digits at dig + M.dig_off[r])

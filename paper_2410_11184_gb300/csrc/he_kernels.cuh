@@ -111,9 +111,7 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
 __global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
                               int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN,
                               const uint64_t *add, long sadd);
-__global__ void k_ks_inner(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig, int L,
-                           int alpha, LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
-                           int nq_all, int g, int logN, int accumulate, KsMulti M);
+
 __global__ void k_ks_inner_sum(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig,
                                int L, int alpha, LimbMap tmap, const ModC *mods, int key_nlimb, int nq_all, int logN,
                                KsMulti M);
@@ -141,6 +139,12 @@ __global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qm
 __global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
                               Scal pm, int nl, int dlo, int dhi, LimbMap map, const ModC *mods, int logN);
 __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter);
+
+// key-switching inner product sum_j d~_j swk_j (k_ks_inner_t<ndig>, ndig in 1 .. 8: the key
+// words of a (limb, coefficient) kept in registers); M.n > 0: grid.y key switches of the same digits
+void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *dig, int nct, int ndig, int L, int alpha,
+                     const LimbMap &tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all, int g,
+                     int logN, int accumulate, const KsMulti &M);
 
 // register-blocked NTT of `count` limbs (N = 2^12: logE = 3, N = 2^16: logE = 4); launches
 // the column and row passes on stream st
