@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #define HE_MAX_LIMBS 64
+#define HE_CONV_MAXSRC 9   // basis conversions: at most alpha + 1 source moduli (alpha <= 8)
 #define HE_MAX_MODS 64
 
 struct ModC {

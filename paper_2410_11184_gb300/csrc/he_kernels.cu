@@ -340,9 +340,11 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
         int c = (int)(id >> logN), k = (int)(id & (N - 1));
         // centred representatives (-q_i/2, q_i/2] (|y_i| and a sign bit): the result is
         // d + u Q_D with zero-mean u
-        uint64_t y[8];
+        uint64_t y[HE_CONV_MAXSRC];   // (loops unrolled to the bound: y stays in registers)
         unsigned negmask = 0;
-        for (int i = 0; i < dsize; i++) {
+#pragma unroll
+        for (int i = 0; i < HE_CONV_MAXSRC; i++) {
+            if (i >= dsize) break;
             uint64_t qi = mods[tmap.prime[digit_lo + i]].q;
             uint64_t v = mul_shoup(x[c * sx + (long)(digit_lo + i) * N + k], cv[i], cv[dsize + i], qi);
             if (v > (qi - 1) / 2) {
@@ -362,7 +364,9 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
             const ModC mt = mods[tmap.prime[t]];
             // sum of |y_i| (c or m_t - c): below dsize 2^60 m_t < m_t 2^64
             uint64_t lo = 0, hi = 0;
-            for (int i = 0; i < dsize; i++) {
+#pragma unroll
+            for (int i = 0; i < HE_CONV_MAXSRC; i++) {
+                if (i >= dsize) break;
                 uint64_t w = cv[2 * dsize + i * ntarget + t];
                 mac_wide(lo, hi, y[i], (negmask >> i) & 1 ? mt.q - w : w);
             }
@@ -383,9 +387,11 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
     long total = (long)nct << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
         int c = (int)(id >> logN), k = (int)(id & (N - 1));
-        uint64_t y[8];
+        uint64_t y[HE_CONV_MAXSRC];   // (loops unrolled to the bound: y stays in registers)
         unsigned negmask = 0;
-        for (int i = 0; i < ds; i++) {
+#pragma unroll
+        for (int i = 0; i < HE_CONV_MAXSRC; i++) {
+            if (i >= ds) break;
             uint64_t qi = mods[tmap.prime[lo + i]].q;
             uint64_t v = mul_shoup(x[c * sx + (long)(lo + i) * N + k], cv[i], cv[ds + i], qi);
             if (v > (qi - 1) / 2) {
@@ -398,7 +404,9 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
         for (int t = 0; t < ntarget; t++) {
             const ModC mt = mods[tmap.prime[t]];
             uint64_t l0 = 0, h0 = 0;
-            for (int i = 0; i < ds; i++) {
+#pragma unroll
+            for (int i = 0; i < HE_CONV_MAXSRC; i++) {
+                if (i >= ds) break;
                 uint64_t w = cv[2 * ds + i * ntarget + t];
                 mac_wide(l0, h0, y[i], (negmask >> i) & 1 ? mt.q - w : w);
             }
@@ -421,9 +429,12 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
         // y_j in centred form (-p_j/2, p_j/2]: keep |y_j| and its sign, so that the conversion
         // error v P has zero mean (a biased v is a constant on every coefficient, whose slot
         // values concentrate where the evaluation point is near 1)
-        uint64_t y[16];
+        // (loops unrolled to the largest source count, so that y stays in registers)
+        uint64_t y[HE_CONV_MAXSRC];
         unsigned negmask = 0;
-        for (int j = 0; j < alpha; j++) {
+#pragma unroll
+        for (int j = 0; j < HE_CONV_MAXSRC; j++) {
+            if (j >= alpha) break;
             uint64_t pj = mods[pidx[j]].q;
             uint64_t v = mul_shoup(xp[(long)j * N], cv[j], cv[alpha + j], pj);
             if (v > (pj - 1) / 2) {
@@ -437,7 +448,9 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
             const ModC mi = mods[qmap.prime[i]];
             // one 128-bit sum, reduced once (phat_j mod q_i stored in Montgomery form)
             uint64_t lo = 0, hi = 0;
-            for (int j = 0; j < alpha; j++) {
+#pragma unroll
+            for (int j = 0; j < HE_CONV_MAXSRC; j++) {
+                if (j >= alpha) break;
                 uint64_t w = cv[2 * alpha + j * nqall + qmap.prime[i]];
                 mac_wide(lo, hi, y[j], (negmask >> j) & 1 ? mi.q - w : w);
             }
