@@ -862,7 +862,7 @@ __device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase
         for (int b = 0; b < E / 2; b++) {
             // Harvey's lazy butterfly: values stay in [0, 4q); q < 2^61 keeps 4q < 2^63
             const int grp = b / t, jj = 2 * grp * t + (b % t);
-            const int idx = m + gbase * (m / m0) * gmul + grp;
+            const int idx = m + gbase * (1 << p) * gmul + grp;   // m / m0 = 2^p
             const ulonglong2 tw = __ldg(psi + idx);   // (w, w') in one 16-byte load
             const uint64_t w = tw.x, wp = tw.y;
             uint64_t u = v[jj];
@@ -887,7 +887,7 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
         for (int b = 0; b < E / 2; b++) {
             // lazy Gentleman-Sande butterfly: inputs and outputs in [0, 2q)
             const int grp = b / t, jj = 2 * grp * t + (b % t);
-            const int idx = m + gbase * (m / m0) * gmul + grp;
+            const int idx = m + gbase * (1 << p) * gmul + grp;   // m / m0 = 2^p
             const ulonglong2 tw = __ldg(ipsi + idx);
             const uint64_t w = tw.x, wp = tw.y;
             const uint64_t u = v[jj], x = v[jj + t];
