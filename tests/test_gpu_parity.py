@@ -238,3 +238,34 @@ def test_softmax_graph_replay_bit_exact(toybts, params):
             assert np.array_equal(got[i], outs[i].data), (call, i)
     # the first call also ran the circuit once eagerly to fill the caches
     assert per_call[1] == per_call[2] > 0 and per_call[0] >= 2 * per_call[1]
+
+
+def test_large_batch_paths_bit_exact(toybts):
+    """Batches of more than 4 ciphertexts take the per-digit ModUp, per-rotation key switches and
+    separate giant-step ModUps (smaller batches take the merged launches): 6 ciphertexts through
+    multiplication, rotation, a CoeffToSlot level and bootstrapping, each against the oracle."""
+    g, o, em = toybts
+    rng = np.random.default_rng(17)
+    m = 6
+    lv = 5
+    cts = [o.encrypt(rng.uniform(-1, 1, o.n0), lv, 2.0 ** 42, 40 + i) for i in range(m)]
+    ga = g.from_coeff(np.stack([c.data for c in cts]), lv, cts[0].scale)
+    assert ga.n_ct == m
+    gp = g.hmult(ga, ga)
+    got = g.to_coeff(gp)
+    for i in range(m):
+        assert np.array_equal(got[i], o.hmult(cts[i], cts[i]).data), ("hmult", i)
+    got = g.to_coeff(g.rotate(ga, 1))
+    for i in range(m):
+        assert np.array_equal(got[i], o.rotate(cts[i], 1).data), ("rotate", i)
+    b3 = [o.encrypt(rng.uniform(-1, 1, o.n0), 3, 2.0 ** 42, 60 + i) for i in range(m)]
+    gb = g.from_coeff(np.stack([c.data for c in b3]), 3, b3[0].scale)
+    got = g.to_coeff(g.lintrans(gb, 3, False, 0, 16.0, float(o.q[3])))
+    for i in range(m):
+        assert np.array_equal(got[i], o.lintrans(b3[i], 3, False, 0, 16.0, float(o.q[3])).data), ("lintrans", i)
+    gr = g.bootstrap(gb, 16.0, 2.0 ** 42)
+    got = g.to_coeff(gr)
+    for i in range(m):
+        r = o.bootstrap(b3[i], em, gain=16.0)
+        assert gr.level == r.level and gr.scale == r.scale
+        assert np.array_equal(got[i], r.data), ("bootstrap", i)
