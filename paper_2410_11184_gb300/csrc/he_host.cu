@@ -1420,7 +1420,11 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         dim3 grid((unsigned)std::min<long>(tiles, c->max_grid / 4), 1);
         size_t smem = (size_t)A.npt * HE_LT_KT * 8;
         ProfScope ps_(c, "lintrans", 8.0 * c->N * ((double)L * A.npt + (double)x.nct * 2 * L * (A.nb + A.na)));
-        k_lt_bsgs<<<grid, 256, smem, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
+        if (2 * x.nct <= 8)   // a few rows: no staging (a staged tile would serve only these rows)
+            k_lt_bsgs_direct<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods,
+                                                                                 c->logN);
+        else
+            k_lt_bsgs<<<grid, 256, smem, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
     // acc = sum_a Rot(out_a, a g hmin): the c0(X^g) parts are added over Q_l, the key-switch

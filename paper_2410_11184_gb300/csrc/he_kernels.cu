@@ -301,6 +301,35 @@ __global__ void __launch_bounds__(256) k_lt_bsgs(LtArgs A, int npoly, int L, Lim
     }
 }
 
+// The same sums for batches of a few rows (npoly <= 8): one thread per (limb, coefficient), no
+// staging; the plaintext values of a giant step are loaded once and used for every row.
+__global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN) {
+    const int N = 1 << logN;
+    long total = (long)L << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        const ModC m = mods[qmap.prime[l]];
+        for (int a = 0; a < A.na; a++) {
+            uint64_t pv[HE_LT_MAXB];
+#pragma unroll
+            for (int b = 0; b < HE_LT_MAXB; b++) {
+                const int pi = b < A.nb ? A.ptix[a][b] : -1;
+                pv[b] = pi >= 0 ? A.pt[pi][(long)l * N + k] : 0;
+            }
+            for (int r = 0; r < npoly; r++) {
+                const long off = ((long)r * L + l) * N + k;
+                uint64_t lo = 0, hi = 0;
+#pragma unroll
+                for (int b = 0; b < HE_LT_MAXB; b++) {
+                    const int pi = b < A.nb ? A.ptix[a][b] : -1;
+                    if (pi >= 0) mac_wide(lo, hi, A.baby[b][off], pv[b]);
+                }
+                A.out[a][off] = redc(lo, hi, m);
+            }
+        }
+    }
+}
+
 // out[c][p][l] = sum_t x_t[c][p][l] w_t[l] (+ w_nt[l] when p = 0) for l < L: rows t < nt of w in
 // Montgomery form (sums of at most 8 products stay below q 2^64), row nt a plain residue.
 // Reads each input once (only its first L limbs).

@@ -100,6 +100,7 @@ __global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa
 __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, LimbMap map,
                                 const ModC *mods, int g, int logN);
 __global__ void k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN);
+__global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN);
 __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap, const ModC *mods, int logN);
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
