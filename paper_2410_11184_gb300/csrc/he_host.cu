@@ -1987,6 +1987,8 @@ static void build_tables(he_ctx *c) {
     // dynamic shared memory of the column pass (N1 * 16 words)
     int logN1 = c->logN / 2;
     size_t sm1 = (size_t)(1 << logN1) * std::min(16, N >> logN1) * 8;
+    // linear-transform inner sums: up to HE_LT_MAXPT staged plaintext tiles of HE_LT_KT words
+    CK(cudaFuncSetAttribute(k_lt_bsgs, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_LT_MAXPT * HE_LT_KT * 8));
     if (sm1 > 48 * 1024) {
         CK(cudaFuncSetAttribute(k_ntt_cols_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
         CK(cudaFuncSetAttribute(k_ntt_cols_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));

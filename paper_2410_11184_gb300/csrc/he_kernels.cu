@@ -267,7 +267,7 @@ __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long 
 }
 
 // Baby-step/giant-step inner sums of a linear-transform level: every block stages the
-// plaintext diagonals of one (limb, 32-coefficient tile) in shared memory, then each row
+// plaintext diagonals of one (limb, HE_LT_KT-coefficient tile) in shared memory, then each row
 // (ciphertext polynomial) reads its nb baby-step values once and writes the na giant-step
 // sums once; the sums are 128-bit and reduced once (plaintexts in Montgomery form, at most 16
 // terms below 16 q^2 < q 2^64).  Dynamic shared memory: npt * HE_LT_KT words.

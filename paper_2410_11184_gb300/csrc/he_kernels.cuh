@@ -12,7 +12,7 @@ struct Scal {
 #define HE_LT_MAXB 16
 #define HE_LT_MAXA 16
 #define HE_LT_MAXPT 128
-#define HE_LT_KT 32   // coefficients per tile (plaintext tile staged in shared memory)
+#define HE_LT_KT 64   // coefficients per tile (plaintext tile staged in shared memory)
 struct LtArgs {
     const uint64_t *baby[HE_LT_MAXB];
     uint64_t *out[HE_LT_MAXA];
