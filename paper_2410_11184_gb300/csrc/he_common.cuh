@@ -3,7 +3,8 @@
 // Residues are uint64 in [0, q) with q < 2^61 (NTT-friendly primes q = 1 mod 2N).
 //  - mul_mod   : Barrett reduction of the 128-bit product with mu = floor(2^(s+63) / q),
 //                s = bitlen(q): the quotient estimate is at most 2 below the true one.
-//  - mul_shoup : Shoup's multiplication by a fixed w with w' = floor(w 2^64 / q).
+//  - mul_shoup : Shoup's multiplication by a fixed w with w' = floor(w 2^64 / q);
+//                mul_shoup_lazy leaves the product in [0, 4q) for the NTT butterflies.
 //  - mac_wide / redc : sums of products kept as 128-bit integers and reduced once by
 //                Montgomery's REDC (R = 2^64): redc(T) = T R^{-1} mod q for T < q 2^64, so
 //                a sum of products whose constant factors are stored as c R mod q comes out
@@ -50,6 +51,17 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
     uint64_t h = he_mulhi(a, wp);
     uint64_t r = a * w - h * q;
     return r >= q ? r - q : r;
+}
+
+// a w mod q in [0, 4q), for any a < 2^64, with nq = 2^64 - q.  The Shoup quotient
+// floor(a w' / 2^64) is estimated from three of the four 32x32 partial products: dropping
+// a0 w'0 and the low halves of a0 w'1 and a1 w'0 loses less than 3 * 2^32 of a w', so the
+// estimate is at most 2 below the exact quotient and a w - h q < 2q + 2q.  The low word
+// a w + h nq = a w - h q is exact mod 2^64 because the true value is below 4q < 2^63.
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t nq) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), p0 = (uint32_t)wp, p1 = (uint32_t)(wp >> 32);
+    const uint64_t h = (uint64_t)a1 * p1 + __umulhi(a0, p1) + __umulhi(a1, p0);
+    return a * w + h * nq;
 }
 
 // valid for a < 2^62 and b < q (the quotient estimate stays within 2 of the true one)

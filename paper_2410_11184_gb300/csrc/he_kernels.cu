@@ -883,22 +883,23 @@ __device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase
                                                   uint64_t q) {
     // elements j (index k + E j); stages with half-distance t = E/2, E/4, ..., 1 in units of j
     constexpr int E = 1 << LOGE;
+    const uint64_t nq = 0 - q;
 #pragma unroll
     for (int p = 0; p < LOGE; p++) {
         const int t = E >> (p + 1);          // distance in j
         const int m = m0 << p;               // stage parameter
 #pragma unroll
         for (int b = 0; b < E / 2; b++) {
-            // Harvey's lazy butterfly: values stay in [0, 4q); q < 2^61 keeps 4q < 2^63
+            // Harvey's lazy butterfly with a 3-product Shoup quotient: values stay in [0, 8q);
+            // q < 2^61 keeps 8q < 2^64
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (1 << p) * gmul + grp;   // m / m0 = 2^p
             const ulonglong2 tw = __ldg(psi + idx);   // (w, w') in one 16-byte load
-            const uint64_t w = tw.x, wp = tw.y;
             uint64_t u = v[jj];
-            if (u >= 2 * q) u -= 2 * q;
-            const uint64_t x = v[jj + t] * w - he_mulhi(v[jj + t], wp) * q;   // in [0, 2q)
+            if (u >= 4 * q) u -= 4 * q;
+            const uint64_t x = mul_shoup_lazy(v[jj + t], tw.x, tw.y, nq);   // in [0, 4q)
             v[jj] = u + x;
-            v[jj + t] = u - x + 2 * q;
+            v[jj + t] = u - x + 4 * q;
         }
     }
 }
@@ -908,30 +909,30 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
                                                   uint64_t q) {
     // inverse of ct_stages_strided: stages in reverse order (t = 1, 2, ..., E/2 in units of j)
     constexpr int E = 1 << LOGE;
+    const uint64_t nq = 0 - q;
 #pragma unroll
     for (int p = LOGE - 1; p >= 0; p--) {
         const int t = E >> (p + 1);
         const int m = m0 << p;
 #pragma unroll
         for (int b = 0; b < E / 2; b++) {
-            // lazy Gentleman-Sande butterfly: inputs and outputs in [0, 2q)
+            // lazy Gentleman-Sande butterfly: inputs and outputs in [0, 4q)
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (1 << p) * gmul + grp;   // m / m0 = 2^p
             const ulonglong2 tw = __ldg(ipsi + idx);
-            const uint64_t w = tw.x, wp = tw.y;
             const uint64_t u = v[jj], x = v[jj + t];
             uint64_t s = u + x;
-            if (s >= 2 * q) s -= 2 * q;
-            const uint64_t d = u - x + 2 * q;
+            if (s >= 4 * q) s -= 4 * q;
+            const uint64_t d = u - x + 4 * q;
             v[jj] = s;
-            v[jj + t] = d * w - he_mulhi(d, wp) * q;
+            v[jj + t] = mul_shoup_lazy(d, tw.x, tw.y, nq);
         }
     }
 }
 
 // Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
 template <int LOGE, int KIND>
-__global__ void __launch_bounds__(256) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+__global__ void __launch_bounds__(256, 3) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride, NttFuse F) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
@@ -1002,11 +1003,12 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
     // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
     ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, q);
     // back to the k + E j layout through shared memory so the store is coalesced; the lazy
-    // butterflies left values in [0, 4q): reduce to [0, q)
+    // butterflies left values in [0, 8q): reduce to [0, q)
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) {
         uint64_t r = v[j];
+        if (r >= 4 * q) r -= 4 * q;
         if (r >= 2 * q) r -= 2 * q;
         if (r >= q) r -= q;
         sm[rr * SP + (E + 1) * k + j] = r;
