@@ -40,7 +40,7 @@ typedef struct he_ctx he_ctx;
 typedef struct {
     int log_n;                 /* ring degree N = 2^log_n, N/2 slots */
     int n_q;
-    const uint64_t *q;         /* n_q primes, q_i = 1 mod 2N, < 2^61 */
+    const uint64_t *q;         /* n_q primes, q_i = 1 mod 2N, < 2^60 */
     int n_p;
     const uint64_t *p;         /* n_p special primes */
     int h;                     /* Hamming weight of the ternary secret */

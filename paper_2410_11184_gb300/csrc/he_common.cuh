@@ -1,6 +1,6 @@
 // Device-side building blocks for the RNS-CKKS kernels (sm_103a).
 //
-// Residues are uint64 in [0, q) with q < 2^61 (NTT-friendly primes q = 1 mod 2N).
+// Residues are uint64 in [0, q) with q < 2^60 (NTT-friendly primes q = 1 mod 2N).
 //  - mul_mod   : Barrett reduction of the 128-bit product with mu = floor(2^(s+63) / q),
 //                s = bitlen(q): the quotient estimate is at most 2 below the true one.
 //  - mul_shoup : Shoup's multiplication by a fixed w with w' = floor(w 2^64 / q);

@@ -1757,7 +1757,7 @@ static void build_tables(he_ctx *c) {
     for (int i = 0; i < nm; i++) {
         uint64_t q = c->mods[i];
         int s = 64 - __builtin_clzll(q);
-        REQUIRE(s <= 61 && s >= 20, HE_EINVAL, "modulus size");
+        REQUIRE(s <= 60 && s >= 20, HE_EINVAL, "modulus size");   // 16q < 2^64 in the NTT
         REQUIRE((q - 1) % (2 * (uint64_t)N) == 0, HE_EINVAL, "modulus not 1 mod 2N");
         ModC m;
         m.q = q;

@@ -883,20 +883,23 @@ __device__ __forceinline__ void ct_stages_strided(uint64_t *v, int m0, int gbase
                                                   uint64_t q) {
     // elements j (index k + E j); stages with half-distance t = E/2, E/4, ..., 1 in units of j
     constexpr int E = 1 << LOGE;
-    const uint64_t nq = 0 - q;
+    const uint64_t nq = 0 - q, red = (LOGE % 2 == 0 ? 8 : 4) * q;
 #pragma unroll
     for (int p = 0; p < LOGE; p++) {
         const int t = E >> (p + 1);          // distance in j
         const int m = m0 << p;               // stage parameter
 #pragma unroll
         for (int b = 0; b < E / 2; b++) {
-            // Harvey's lazy butterfly with a 3-product Shoup quotient: values stay in [0, 8q);
-            // q < 2^61 keeps 8q < 2^64
+            // Harvey's lazy butterfly with a 3-product Shoup quotient (x < 4q).  With an even
+            // number of stages per half-pass, u is reduced by 8q only in odd stages: stages
+            // without the reduction map [0, 12q) to [0, 16q), those with it map [0, 16q) back to
+            // [0, 12q); q < 2^60 keeps 16q < 2^64.  Otherwise every stage reduces by 4q and
+            // values stay in [0, 8q).
             const int grp = b / t, jj = 2 * grp * t + (b % t);
             const int idx = m + gbase * (1 << p) * gmul + grp;   // m / m0 = 2^p
             const ulonglong2 tw = __ldg(psi + idx);   // (w, w') in one 16-byte load
             uint64_t u = v[jj];
-            if (u >= 4 * q) u -= 4 * q;
+            if ((LOGE % 2 != 0 || (p & 1)) && u >= red) u -= red;
             const uint64_t x = mul_shoup_lazy(v[jj + t], tw.x, tw.y, nq);   // in [0, 4q)
             v[jj] = u + x;
             v[jj + t] = u - x + 4 * q;
@@ -1003,11 +1006,12 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
     // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
     ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, q);
     // back to the k + E j layout through shared memory so the store is coalesced; the lazy
-    // butterflies left values in [0, 8q): reduce to [0, q)
+    // butterflies left values in [0, 12q): reduce to [0, q)
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) {
         uint64_t r = v[j];
+        if (r >= 8 * q) r -= 8 * q;
         if (r >= 4 * q) r -= 4 * q;
         if (r >= 2 * q) r -= 2 * q;
         if (r >= q) r -= q;

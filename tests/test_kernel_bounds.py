@@ -3,8 +3,9 @@ a model of their arithmetic (no GPU).
 
 mul_shoup_lazy (he_common.cuh) estimates Shoup's quotient floor(a w' / 2^64) from three of the
 four 32x32 partial products and forms a w - h q mod 2^64 as a w + h (2^64 - q).  The forward
-butterflies keep values in [0, 8q) and the inverse ones in [0, 4q); both need q < 2^61, the
-largest modulus the library accepts."""
+butterflies of a 16-coefficient register block reduce u by 8q only in every other stage, so
+values alternate between [0, 12q) and [0, 16q); the inverse ones stay in [0, 4q).  Both need
+q < 2^60, the largest modulus the library accepts."""
 import random
 
 import pytest
@@ -23,7 +24,7 @@ def _cases(rng, q):
     return edge + [rng.getrandbits(64) for _ in range(300)]
 
 
-@pytest.mark.parametrize("bits", [20, 42, 50, 58, 60, 61])
+@pytest.mark.parametrize("bits", [20, 42, 50, 58, 60])
 def test_lazy_shoup_product_is_congruent_and_below_4q(bits):
     rng = random.Random(bits)
     for _ in range(20):
@@ -37,23 +38,59 @@ def test_lazy_shoup_product_is_congruent_and_below_4q(bits):
                 assert r < 4 * q and r % q == (a * w) % q
 
 
-def test_butterfly_ranges_fit_64_bits():
-    """Forward: u < 8q reduced by 4q, x < 4q, outputs u + x and u - x + 4q in [0, 8q).
-    Inverse: u, x < 4q, s = u + x reduced by 4q, d = u - x + 4q in (0, 8q), Shoup(d) < 4q.
-    The largest value formed is below 8q, so every sum is exact for q < 2^61."""
-    q = (1 << 61) - 1
-    assert 8 * q <= M64
-    u, x = 4 * q - 1, 4 * q - 1
-    assert u + x < 8 * q and u - 0 + 4 * q < 8 * q and 0 - x + 4 * q > 0
+def _forward_block(v, ws, q, reduce_every_stage):
+    """Radix-2 stages of one 16-coefficient register block as the forward kernel runs them:
+    stage p pairs (j, j + t), t = 8 >> p; returns the values after each stage."""
+    out = []
+    for p in range(4):
+        t = 8 >> p
+        red = 4 * q if reduce_every_stage else 8 * q
+        for b in range(8):
+            grp, jj = b // t, 2 * (b // t) * t + b % t
+            w = ws[p][grp]
+            u = v[jj]
+            if (reduce_every_stage or p & 1) and u >= red:
+                u -= red
+            x, _ = lazy_shoup(v[jj + t], w, (w << 64) // q, q)
+            v[jj], v[jj + t] = u + x, u - x + 4 * q
+        out.append(list(v))
+    return out
+
+
+def test_forward_butterfly_ranges_fit_64_bits():
+    """Inputs below 12q (canonical on entry, below 12q after each block): stages 0 and 2 leave
+    values below 16q, stages 1 and 3 below 12q, and every value is congruent to the textbook
+    radix-2 result; the largest q allowed (2^60 - 1) keeps 16q < 2^64."""
+    assert 16 * ((1 << 60) - 1) <= M64
     rng = random.Random(5)
+    for trial in range(300):
+        q = ((1 << 60) - 1 - 2 * trial) if trial < 5 else (rng.randrange(1 << 40, 1 << 60) | 1)
+        ws = [[rng.randrange(q) for _ in range(8)] for _ in range(4)]
+        v = [rng.randrange(12 * q) if trial % 2 else 12 * q - 1 - rng.randrange(4) for _ in range(16)]
+        ref = [x % q for x in v]
+        for p, lazy in enumerate(_forward_block(list(v), ws, q, False)):
+            t = 8 >> p
+            for b in range(8):
+                grp, jj = b // t, 2 * (b // t) * t + b % t
+                w = ws[p][grp]
+                u, x = ref[jj], ref[jj + t] * w % q
+                ref[jj], ref[jj + t] = (u + x) % q, (u - x) % q
+            bound = 16 * q if p % 2 == 0 else 12 * q
+            assert all(0 <= y < bound for y in lazy), (p, q)
+            assert [y % q for y in lazy] == ref
+
+
+def test_inverse_butterfly_ranges_fit_64_bits():
+    """Inverse: u, x < 4q, s = u + x reduced by 4q, d = u - x + 4q in (0, 8q), Shoup(d) < 4q."""
+    rng = random.Random(6)
     for _ in range(2000):
-        qq = rng.randrange(1 << 40, 1 << 61) | 1
+        qq = rng.randrange(1 << 40, 1 << 60) | 1
         w = rng.randrange(qq)
-        wp = (w << 64) // qq
-        u, v = rng.randrange(8 * qq), rng.randrange(8 * qq)
-        if u >= 4 * qq:
-            u -= 4 * qq
-        x, _ = lazy_shoup(v, w, wp, qq)
-        hi, lo = u + x, u - x + 4 * qq
-        assert 0 <= hi < 8 * qq and 0 < lo < 8 * qq
-        assert (hi - u - v * w) % qq == 0 and (lo - u + v * w) % qq == 0
+        u, x = rng.randrange(4 * qq), rng.randrange(4 * qq)
+        s = u + x
+        if s >= 4 * qq:
+            s -= 4 * qq
+        d = u - x + 4 * qq
+        y, _ = lazy_shoup(d, w, (w << 64) // qq, qq)
+        assert 0 <= s < 4 * qq and 0 < d < 8 * qq and 0 <= y < 4 * qq
+        assert (s - u - x) % qq == 0 and (y - (u - x) * w) % qq == 0
