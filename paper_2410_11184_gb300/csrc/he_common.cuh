@@ -58,10 +58,17 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
 // a0 w'0 and the low halves of a0 w'1 and a1 w'0 loses less than 3 * 2^32 of a w', so the
 // estimate is at most 2 below the exact quotient and a w - h q < 2q + 2q.  The low word
 // a w + h nq = a w - h q is exact mod 2^64 because the true value is below 4q < 2^63.
+// Written as 32-bit multiply-adds only: with h = H + t2, H = a1 w'1 + hi(a0 w'1) (exact in
+// 64 bits) and t2 = hi(a1 w'0), h nq = H nq + t2 nq, so no 64-bit addition is needed.
 __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t nq) {
     const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), p0 = (uint32_t)wp, p1 = (uint32_t)(wp >> 32);
-    const uint64_t h = (uint64_t)a1 * p1 + __umulhi(a0, p1) + __umulhi(a1, p0);
-    return a * w + h * nq;
+    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32), n0 = (uint32_t)nq, n1 = (uint32_t)(nq >> 32);
+    const uint32_t t2 = __umulhi(a1, p0);
+    const uint64_t H = (uint64_t)a1 * p1 + __umulhi(a0, p1);
+    const uint32_t h0 = (uint32_t)H, h1 = (uint32_t)(H >> 32);
+    const uint64_t acc = (uint64_t)a0 * w0 + (uint64_t)h0 * n0 + (uint64_t)t2 * n0;
+    const uint32_t hi = (uint32_t)(acc >> 32) + a0 * w1 + a1 * w0 + h0 * n1 + h1 * n0 + t2 * n1;
+    return ((uint64_t)hi << 32) | (uint32_t)acc;
 }
 
 // valid for a < 2^62 and b < q (the quotient estimate stays within 2 of the true one)

@@ -19,6 +19,20 @@ def lazy_shoup(a, w, wp, q):
     return (a * w + h * ((1 << 64) - q)) & M64, h
 
 
+def lazy_shoup_words(a, w, wp, q):
+    """The same product as the kernel forms it, from 32-bit multiply-adds only: h = H + t2 with
+    H = a1 w'1 + hi(a0 w'1) and t2 = hi(a1 w'0), and h nq = H nq + t2 nq."""
+    m, nq = 0xFFFFFFFF, (1 << 64) - q
+    a0, a1, p0, p1, w0, w1, n0, n1 = a & m, a >> 32, wp & m, wp >> 32, w & m, w >> 32, nq & m, nq >> 32
+    t2 = (a1 * p0) >> 32
+    H = a1 * p1 + ((a0 * p1) >> 32)
+    assert H <= M64
+    h0, h1 = H & m, H >> 32
+    acc = (a0 * w0 + h0 * n0 + t2 * n0) & M64
+    hi = ((acc >> 32) + a0 * w1 + a1 * w0 + h0 * n1 + h1 * n0 + t2 * n1) & m
+    return (hi << 32) | (acc & m)
+
+
 def _cases(rng, q):
     edge = [0, 1, q - 1, q, 2 * q - 1, 4 * q - 1, 8 * q - 1, M64, 1 << 63, (1 << 32) - 1, 1 << 32]
     return edge + [rng.getrandbits(64) for _ in range(300)]
@@ -33,6 +47,7 @@ def test_lazy_shoup_product_is_congruent_and_below_4q(bits):
             wp = (w << 64) // q
             for a in _cases(rng, q):
                 r, h = lazy_shoup(a, w, wp, q)
+                assert lazy_shoup_words(a, w, wp, q) == r
                 exact = (a * wp) >> 64
                 assert exact - 2 <= h <= exact
                 assert r < 4 * q and r % q == (a * w) % q
