@@ -1006,14 +1006,18 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
     // stages m = N1 E .. N/2: group = row (m / N1) + k (m / (N1 E)) + j / (2t)
     ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, q);
     // back to the k + E j layout through shared memory so the store is coalesced; the lazy
-    // butterflies left values in [0, 12q): reduce to [0, q)
+    // butterflies left values r < 16q < 2^(s+4) (s = bit length of q): reduce to [0, q) with a
+    // small-quotient Barrett step.  With t = floor(r / 2^(s-6)) < 2^10 and
+    // mu6 = floor(2^(s+6) / q) = floor(mu / 2^57), k = floor(t mu6 / 2^12) underestimates r / q
+    // by less than 2^(10-12) + 2^(s-6) / q < 1, so r - k q lies in [0, 2q).
+    const uint32_t mu6 = (uint32_t)(mods[p].mu >> 57);
+    const int sh = mods[p].s - 6;
+    const uint64_t nq = 0 - q;
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < E; j++) {
-        uint64_t r = v[j];
-        if (r >= 8 * q) r -= 8 * q;
-        if (r >= 4 * q) r -= 4 * q;
-        if (r >= 2 * q) r -= 2 * q;
+        const uint32_t kq = ((uint32_t)(v[j] >> sh) * mu6) >> 12;
+        uint64_t r = v[j] + (uint64_t)kq * nq;   // v - kq q
         if (r >= q) r -= q;
         sm[rr * SP + (E + 1) * k + j] = r;
     }

@@ -109,3 +109,22 @@ def test_inverse_butterfly_ranges_fit_64_bits():
         y, _ = lazy_shoup(d, w, (w << 64) // qq, qq)
         assert 0 <= s < 4 * qq and 0 < d < 8 * qq and 0 <= y < 4 * qq
         assert (s - u - x) % qq == 0 and (y - (u - x) * w) % qq == 0
+
+
+def test_final_reduction_small_quotient_barrett():
+    """The forward row pass reduces r < 16q to [0, q) with k = floor(floor(r / 2^(s-6)) mu6 / 2^12),
+    mu6 = floor(mu / 2^57) where mu = floor(2^(s+63) / q) is the stored Barrett constant; k is
+    floor(r / q) or one less, so one conditional subtraction finishes."""
+    rng = random.Random(7)
+    for _ in range(20000):
+        s = rng.randrange(20, 61)
+        q = rng.randrange(1 << (s - 1), 1 << s) | 1
+        mu6 = ((1 << (s + 63)) // q) >> 57
+        assert mu6 == (1 << (s + 6)) // q
+        for r in (0, q - 1, q, 12 * q - 1, 16 * q - 1, rng.randrange(16 * q)):
+            t = r >> (s - 6)
+            assert t < 1 << 10
+            k = (t * mu6) >> 12
+            x = (r + k * ((1 << 64) - q)) & M64
+            assert k * q <= r and x == r - k * q < 2 * q
+            assert (x - q if x >= q else x) == r % q
