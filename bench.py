@@ -105,8 +105,8 @@ class ClockSampler:
 
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the two forward NTT passes per
 # algorithmic byte (16 N per limb), from one capture of a 320-limb ModUp transform at N = 2^16
-# (python -m paper_2410_11184_gb300.profile_case keyswitch): 1.745 MB per 1.049 MB limb
-NTT_DRAM_PER_ALG_BYTE = 1.745e6 / (16 * 65536)
+# (python -m paper_2410_11184_gb300.profile_case keyswitch): 1.733 MB per 1.049 MB limb
+NTT_DRAM_PER_ALG_BYTE = 1.733e6 / (16 * 65536)
 
 
 def peaks():
