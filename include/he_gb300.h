@@ -122,19 +122,38 @@ int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int
  * while its graph may be launched. */
 int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts);
 
-/* ---- the hot-path operations, one call each (device buffers as above) ---- */
-/* negacyclic NTT (inverse=0) / inverse NTT of n_limb limbs mod q_0.. in place (device);
- * inputs reduced mod q_i, outputs in [0, q_i) */
+/* ---- the hot-path operations, one call each ----
+ * Common to the calls below: ciphertext batches are he_ct device buffers as above; a result
+ * is formed in library-owned scratch and copied to out->data (caller-allocated, at least
+ * n_ct * 2 * (level_out+1) * N words; it may be an input's buffer, except for
+ * he_rescale_noalloc), and out->level / scale / n_ct are written.  Errors: HE_EINVAL
+ * for a NULL pointer, a NULL data pointer, n_ct < 1 or a level outside the chain;
+ * HE_ELEVEL where the operation needs a level the input no longer has; HE_ENOKEY where an
+ * evaluation key was not generated; HE_ECUDA if a CUDA call fails.  Nothing is launched before
+ * the arguments are checked. */
+
+/* Negacyclic NTT (inverse = 0: evaluation at the odd powers psi^(2k+1) of a primitive 2N-th
+ * root mod q_i, output in bit-reversed order) or its inverse, in place, on n_poly polynomials of
+ * n_limb limbs each ([n_poly][n_limb][N] uint64, device; limb i is reduced mod q_i).  The
+ * evaluation representation that all CKKS products below work in; the paper delegates it to its
+ * library.  Inputs must be below q_i; outputs are in [0, q_i).  HE_EINVAL if n_limb > n_q. */
 int he_ntt(he_ctx *ctx, uint64_t *data, int n_poly, int n_limb, int inverse);
 /* coefficient-form host copy of a ciphertext batch [n_ct][2][level+1][N] (synchronises) */
 int he_ct_to_coeff(he_ctx *ctx, const he_ct *x, uint64_t *host);
 /* loads a coefficient-form host ciphertext batch into x (x->data, level, scale, n_ct set) */
 int he_ct_from_coeff(he_ctx *ctx, const uint64_t *host, he_ct *x);
-/* encode N/2 complex slots (interleaved, host) at scale into a device plaintext [level+1][N] (NTT) */
+/* Ecd (Sec. 2.2): N/2 complex slots (interleaved re/im, host) scaled by `scale`, rounded to
+ * integers, into a device plaintext pt [level+1][N] in NTT form. */
 int he_encode(he_ctx *ctx, const double *slots, double scale, int level, uint64_t *pt);
-int he_add(he_ctx *ctx, he_ct *a, const he_ct *b);                 /* a += b */
-int he_mul_plain(he_ctx *ctx, he_ct *a, const uint64_t *pt);       /* a *= pt (no rescale) */
-int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out);           /* out at level-1 */
+/* Add (Sec. 2.2, Functionalities): a += b, in place.  HE_EINVAL unless both batches have the
+ * same level, n_ct and scale (relative difference at most 1e-9). */
+int he_add(he_ctx *ctx, he_ct *a, const he_ct *b);
+/* plaintext product (Sec. 2.2, Functionalities): a *= pt with pt [a.level+1][N] from
+ * he_encode at a.level; no rescale (the scale becomes a.scale times the plaintext's). */
+int he_mul_plain(he_ctx *ctx, he_ct *a, const uint64_t *pt);
+/* Rescale (Sec. 2.2, Levels): out = round(a / q_level) at level-1, scale / q_level.
+ * HE_ELEVEL at level 0. */
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out);
 /* Rescale that allocates no device memory (no counterpart in the paper; an interface for
  * callers that cannot allocate once they are running: a server that reserved its whole HBM
  * budget at start-up and admits work against it, or a host program whose memory pool is
@@ -149,22 +168,37 @@ int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out);           /* out at lev
  * on the GPU (several streams, or several contexts on one device) race on it, so serialise
  * them.  Errors as he_rescale. */
 int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out);
-/* tensor + relinearise + rescale (Mult of Sec. 2.2) */
+/* Mult (Sec. 2.2, Functionalities): tensor product, relinearisation with the hybrid key
+ * switch, and rescale (relinearisation and rescale as one division by P q_level), out at
+ * level min(a, b) - 1.  a and b may differ in n_ct only if one of them has n_ct = 1 (it is
+ * broadcast).  HE_ELEVEL at level 0. */
 int he_hmult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out);
-/* relinearise a degree-2 batch d [n_ct][3][level+1][N] into out (no rescale) */
+/* relinearisation (Sec. 2.2) of a degree-2 batch d [n_ct][3][level+1][N] (device, NTT form)
+ * into out at the same level (no rescale). */
 int he_relinearize(he_ctx *ctx, const uint64_t *d, int level, int n_ct, he_ct *out);
-/* Rot(ct, r): slot j of the output holds slot (j + r) mod N/2 (Sec. 2.2) */
+/* Rot(ct, r) (Sec. 2.2, Functionalities): slot j of the output holds slot (j + r) mod N/2.
+ * HE_ENOKEY if the rotation key for r was not generated (he_keygen, he_keygen_softmax). */
 int he_rotate(he_ctx *ctx, const he_ct *a, int r, he_ct *out);
+/* complex conjugation of every slot (the Galois map X -> X^(2N-1)). */
 int he_conjugate(he_ctx *ctx, const he_ct *a, he_ct *out);
-/* p(u) = sum c_k T_k(u) at level_out with scale scale_out (levels: ceil(log2(deg+1))) */
+/* polynomial evaluation (Sec. 2.2, Functions as polynomials; Sec. 5.1.2): p(u) =
+ * sum_{k <= deg} c_k T_k(u) (Chebyshev basis, coeffs host) at level_out with scale scale_out;
+ * it consumes ceil(log2(deg + 1)) levels, so u must be at level_out + that.  HE_ELEVEL
+ * otherwise. */
 int he_poly_eval(he_ctx *ctx, const he_ct *u, const double *coeffs, int deg, int level_out, double scale_out,
                  he_ct *out);
-/* one level of SlotToCoeff (inverse=0) or CoeffToSlot (inverse=1), split into nlev levels */
+/* one level (which = 0 .. nlev-1) of the bootstrapping's linear transforms (Sec. 2.2, Levels):
+ * SlotToCoeff (inverse = 0) or CoeffToSlot (inverse = 1) of N/2 slots factored into nlev
+ * sparse levels, evaluated baby-step giant-step; gain multiplies the result, pt_scale is the
+ * scale of the diagonals.  Needs the bootstrapping rotation keys (HE_ENOKEY otherwise). */
 int he_lintrans(he_ctx *ctx, const he_ct *a, int nlev, int inverse, int which, double gain, double pt_scale,
                 he_ct *out);
-/* bootstrapping: out (level user_top) encrypts gain * message with scale out_scale */
+/* bootstrapping (Sec. 2.2, Levels; Sec. 5.1.1): SlotToCoeff, ModRaise, CoeffToSlot,
+ * EvalMod; out at user_top_level encrypts gain * message with scale out_scale.  HE_EINVAL if the
+ * context was created without bootstrapping, HE_ELEVEL below the level SlotToCoeff needs. */
 int he_bootstrap(he_ctx *ctx, const he_ct *a, double gain, double out_scale, he_ct *out);
-/* ModRaise of a level-0 batch to level top */
+/* ModRaise (bootstrapping's first step): a level-0 batch reinterpreted modulo q_0 ... q_top
+ * (centred lift).  HE_EINVAL unless a is at level 0 and top < n_q. */
 int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
 
 /* operation counters since creation: [ciphertext key switches (a batched key switch over n
