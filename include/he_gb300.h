@@ -82,6 +82,11 @@ int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out);
 void he_context_destroy(he_ctx *ctx);
 const char *he_last_error(const he_ctx *ctx);
 int he_ring_degree(const he_ctx *ctx);
+/* 1 if p is below the paper's 128-bit-security parameter size (Sec. 5.1.1: N = 2^16,
+ * log2(QP) <= 1555, ternary secret of Hamming weight h = 192; for other N the modulus bound is
+ * taken as proportional to N) -- the small test chains are --, 0 otherwise, HE_EINVAL for a
+ * NULL or malformed p.  Host only: needs no GPU and no context. */
+int he_params_insecure(const he_params *p);
 
 /* KeyGen (Sec. 2.2): secret, public key, relinearisation and conjugation keys, rotation keys
  * for the n_rot slot rotations in rot_steps, and (if bootstrapping) every rotation key that

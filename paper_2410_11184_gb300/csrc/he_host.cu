@@ -2101,6 +2101,20 @@ void he_context_destroy(he_ctx *c) {
 const char *he_last_error(const he_ctx *c) { return c ? c->err.c_str() : "null context"; }
 int he_ring_degree(const he_ctx *c) { return c ? c->N : 0; }
 
+// The paper's parameter set (Sec. 5.1.1, the parameter table): N = 2^16, log2(QP) = 1555 and a
+// sparse ternary secret of Hamming weight h = 192 give 128-bit security.  Anything with a
+// smaller ring, a larger modulus for its ring (the bound taken as proportional to N) or a
+// sparser secret is flagged: the small test chains are.
+int he_params_insecure(const he_params *p) {
+    if (!p || p->log_n < 1 || p->log_n > 20 || p->n_q < 1 || !p->q || p->n_p < 0 || (p->n_p > 0 && !p->p))
+        return HE_EINVAL;
+    double log_qp = 0.0;
+    for (int i = 0; i < p->n_q; i++) log_qp += std::log2((double)p->q[i]);
+    for (int i = 0; i < p->n_p; i++) log_qp += std::log2((double)p->p[i]);
+    const double bound = 1555.0 * std::ldexp(1.0, p->log_n - 16) + 0.5;
+    return (p->log_n < 16 || p->h < 192 || log_qp > bound) ? 1 : 0;
+}
+
 int he_keygen(he_ctx *ctx, uint64_t seed, const int *rot_steps, int n_rot) {
     if (!ctx || n_rot < 0 || (n_rot > 0 && !rot_steps)) return HE_EINVAL;
     API_BEGIN

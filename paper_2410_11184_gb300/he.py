@@ -54,6 +54,7 @@ def lib():
         vp = C.c_void_p
         sig = {
             "he_context_create": [C.POINTER(he_params), vp, C.POINTER(vp)],
+            "he_params_insecure": [C.POINTER(he_params)],
             "he_context_destroy": [vp],
             "he_ring_degree": [vp],
             "he_keygen": [vp, C.c_uint64, intp, C.c_int],
@@ -131,6 +132,29 @@ class Ciphertexts:
         self.level, self.scale, self.n_ct = h.level, h.scale, h.n_ct
 
 
+def _make_params(chain, evalmod=None):
+    """he_params for a chain dict (params/chains.json) and the arrays it points into (keep them
+    alive as long as the struct is used)."""
+    q = np.array([int(x) for x in chain["q"]], dtype=np.uint64)
+    p = np.array([int(x) for x in chain["p"]], dtype=np.uint64)
+    bts = int(chain.get("bootstrap", 0))
+    em = _hex(evalmod["coeffs"]) if (bts and evalmod) else np.zeros(1)
+    prm = he_params(chain["log_n"], len(q), q.ctypes.data_as(u64p), len(p), p.ctypes.data_as(u64p), chain["h"],
+                    chain["sigma"], chain["log_scale"], chain["user_top_level"], bts, chain.get("stc_levels", 0),
+                    chain.get("cts_levels", 0), chain.get("bts_min_level", 0), evalmod["K"] if evalmod else 0.0,
+                    evalmod["r"] if evalmod else 0, evalmod["deg"] if evalmod else 0, em.ctypes.data_as(dblp))
+    return prm, (q, p, em)
+
+
+def params_insecure(chain):
+    """True if the chain is below the paper's 128-bit parameter size (he_params_insecure; no GPU)."""
+    prm, keep = _make_params(chain)
+    rc = lib().he_params_insecure(C.byref(prm))
+    if rc < 0:
+        raise RuntimeError("he_params_insecure: malformed parameters (%d)" % rc)
+    return bool(rc)
+
+
 class Context:
     """he_ctx handle: parameters from a chain dict (params/chains.json)."""
 
@@ -140,18 +164,10 @@ class Context:
         self.torch = torch
         self.device = torch.device(device)
         self.chain = chain
-        self.q = np.array([int(x) for x in chain["q"]], dtype=np.uint64)
-        self.p = np.array([int(x) for x in chain["p"]], dtype=np.uint64)
+        prm, (self.q, self.p, self._em) = _make_params(chain, evalmod)
         self.n = 1 << chain["log_n"]
         self.n0 = self.n // 2
-        bts = int(chain.get("bootstrap", 0))
-        self._em = _hex(evalmod["coeffs"]) if (bts and evalmod) else np.zeros(1)
-        prm = he_params(chain["log_n"], len(self.q), self.q.ctypes.data_as(u64p), len(self.p),
-                        self.p.ctypes.data_as(u64p), chain["h"], chain["sigma"], chain["log_scale"],
-                        chain["user_top_level"], bts, chain.get("stc_levels", 0), chain.get("cts_levels", 0),
-                        chain.get("bts_min_level", 0), evalmod["K"] if evalmod else 0.0,
-                        evalmod["r"] if evalmod else 0, evalmod["deg"] if evalmod else 0,
-                        self._em.ctypes.data_as(dblp))
+        self.insecure = params_insecure(chain)   # the small test chains
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = C.c_void_p()
         rc = lib().he_context_create(C.byref(prm), C.c_void_p(self.stream.cuda_stream), C.byref(h))

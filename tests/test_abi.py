@@ -43,3 +43,16 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
         assert "no CPU fallback" in str(e)
     else:
         raise AssertionError("expected a failure")
+
+
+def test_toy_chains_are_flagged_insecure(params):
+    """The paper's parameter set (N = 2^16, log2(QP) = 1555, h = 192; Sec. 5.1.1) passes; the
+    small test chains and a chain with a sparser secret or a larger modulus are flagged."""
+    from paper_2410_11184_gb300 import build, he
+
+    build.build()
+    chains = params[0]
+    assert not he.params_insecure(chains["fgb16"])
+    assert he.params_insecure(chains["toy"]) and he.params_insecure(chains["toybts"])
+    assert he.params_insecure(dict(chains["fgb16"], h=64))
+    assert he.params_insecure(dict(chains["fgb16"], p=chains["fgb16"]["p"] + chains["fgb16"]["p"][:1]))
