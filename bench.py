@@ -341,6 +341,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-packing (one problem per ciphertext) timing")
     ap.add_argument("--latency-repeats", type=int, default=50, help="single-ciphertext latency repeats (0: off)")
     args = ap.parse_args()
     if args.workload == "serve":
@@ -465,8 +466,9 @@ def main():
         # latency of one Softmax call on a single ciphertext (128 Softmax of dim 256): graph
         # replays, each timed with CUDA events (p50 / p99 over the repeats)
         lat1 = None
-        if args.latency_repeats > 0:
+        if args.latency_repeats > 0 or not args.no_split:
             g.keygen_softmax(n, 1)
+        if args.latency_repeats > 0:
             x1 = attention_logits(g.n0 // n, n, seed=seeds["inputs"] + 1000)
             src1 = g.encrypt(x1, n, 1, pl["M"], seeds["encrypt"] + 1000)
             work1 = g.like(src1)
@@ -488,6 +490,47 @@ def main():
             lat1 = {"workload": "1 ciphertext, 128 Softmax of dim 256", "repeats": args.latency_repeats,
                     "p50_ms": ts[len(ts) // 2], "p99_ms": ts[min(len(ts) - 1, -(-99 * len(ts) // 100) - 1)],
                     "max_ms": ts[-1]}
+
+        # the paper's split packing (Sec. 4.2, first paragraph of the many-ciphertext case): the
+        # same L Softmax as m independent one-ciphertext problems of N0/n Softmax, each with its
+        # own auxiliary thread (log n rotations per round instead of log(n/m)); timed as one
+        # grouped batched pass (he_softmax_grouped, m groups of one ciphertext)
+        split = None
+        if not args.no_split:
+            rows = g.n0 // n
+            parts = [g.encrypt(x[i * rows:(i + 1) * rows], n, 1, pl["M"], seeds["encrypt"] + 2000 + i)
+                     for i in range(m)]
+            ssrc = he.Ciphertexts(g, torch.cat([p_.tensor for p_ in parts]), parts[0].level, parts[0].scale, m)
+            del parts
+            swork = g.like(ssrc)
+
+            def split_step():
+                swork.tensor.copy_(ssrc.tensor)
+                swork.level, swork.scale, swork.n_ct = ssrc.level, ssrc.scale, ssrc.n_ct
+                g.softmax_grouped(swork, pl, m)
+
+            split_step()
+            barrier()
+            ts_ = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ts_[0].record(stream)
+            split_step()
+            ts_[1].record(stream)
+            barrier()
+            w1 = 2 * (swork.level + 1) * g.n
+            serr = 0.0
+            for i in range(m):
+                one_ct = he.Ciphertexts(g, swork.tensor[i * w1:(i + 1) * w1], swork.level, swork.scale, 1)
+                yi = g.decrypt(one_ct, n)
+                xi = x[i * rows:(i + 1) * rows]
+                ei = np.exp(xi - xi.max(axis=1, keepdims=True))
+                serr = max(serr, float(np.abs(yi - ei / ei.sum(axis=1, keepdims=True)).max()))
+            split = {"workload": "%d one-ciphertext problems of %d Softmax (split packing)" % (m, rows),
+                     "grouped_ms_per_softmax": ts_[0].elapsed_time(ts_[1]) / L,
+                     "precision_bits_vs_fp64": -math.log2(serr) if serr > 0 else None}
+            if lat1:
+                # one problem at a time: the single-ciphertext latency times m, per Softmax
+                split["sequential_ms_per_softmax"] = lat1["p50_ms"] * m / L
+            del ssrc, swork
 
     ms_step, e2e_ms = shard.max_over_ranks([total_ms / args.steps, e2e_ms], dist)
     if rank != 0:
@@ -521,6 +564,7 @@ def main():
         "roofline": roof,
         "breakdown_one_step": breakdown,
         "single_ct_latency": lat1,
+        "split_packing": split,
         "e2e": {"value": e2e_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": src.tensor.numel() * 8,
                 "d2h_bytes_per_step": out_words * 8},
     }
