@@ -72,6 +72,7 @@ def lib():
         L.orc_tensor.argtypes = [C.c_void_p, u64p, u64p, C.c_int, u64p]
         L.orc_relin.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
         L.orc_relin_rescale.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
+        L.orc_modup.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
         L.orc_hmult.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, u64p, C.c_int, C.c_double,
                                 u64p, intp, dblp]
         L.orc_galois_for_rot.argtypes = [C.c_void_p, C.c_long]
@@ -228,6 +229,14 @@ class Oracle:
     def relin(self, d012, level):
         out = np.zeros((2, level + 1, self.n), dtype=np.uint64)
         self._chk(lib().orc_relin(self.ptr, P(_u64(d012)), level, P(out)))
+        return out
+
+    def modup(self, d, level):
+        """ModUp of a coefficient-form polynomial d [level+1][N]: [ndigit][level+1+n_p][N]
+        (extended limb level+1+k is the special prime p_k)."""
+        nd = -(-(level + 1) // self.chain["alpha"])
+        out = np.zeros((nd, level + 1 + len(self.chain["p"]), self.n), dtype=np.uint64)
+        self._chk(lib().orc_modup(self.ptr, P(_u64(d)), level, P(out)))
         return out
 
     def relin_rescale(self, d012, level):

@@ -217,6 +217,17 @@ int orc_relin(orc_ctx *c, const uint64_t *d012, int level, uint64_t *out) {
     return 0;
 }
 
+/* ModUp of key switching (Sec. 2.2; see ckks.c): d [level+1][N] coefficient form ->
+ * out [ndigit][(level+1) + n_p][N], extended limb index level+1+k being p_k. */
+int orc_modup(orc_ctx *c, const uint64_t *d, int level, uint64_t *out) {
+    if (level < 0 || level >= c->nq) return -1;
+    int L = level + 1, nl = L + c->np, nd = (L + c->alpha - 1) / c->alpha;
+    uint64_t *dig = modup(c, d, level);
+    memcpy(out, dig, sizeof(uint64_t) * (size_t)nd * nl * c->n);
+    free(dig);
+    return 0;
+}
+
 int orc_hmult(orc_ctx *c, const uint64_t *a, int la, double sa, const uint64_t *b, int lb, double sb,
               uint64_t *out, int *lout, double *sout) {
     orc_ct x = wrap(c, a, la, sa), y = wrap(c, b, lb, sb), z;

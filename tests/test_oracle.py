@@ -196,6 +196,41 @@ def test_rescale_is_rounded_division(params):
     assert r.scale == 2.0 ** 40 / o.q[lv]
 
 
+def test_modup_is_crt_lift_plus_small_multiple(params):
+    """ModUp of hybrid key switching (Sec. 2.2): for every digit D (alpha consecutive primes),
+    limbs inside D are copied, and every other limb t (Q or P) holds Y mod m_t for ONE integer
+    Y = X + u Q_D, X the centred CRT value of the digit's residues (|X| <= Q_D / 2) and u small:
+    the fast basis conversion with centred representatives has |Y| <= |D| Q_D / 2.  Centring
+    also makes u average about 0 (representatives in [0, q_i) would put Y in [0, |D| Q_D) and
+    give u a mean near |D| / 2)."""
+    o = small_oracle(params, log_n=8, nq=8)
+    rng = np.random.default_rng(9)
+    lv, alpha = 6, o.chain["alpha"]
+    d = np.stack([rng.integers(0, o.q[t], o.n, dtype=np.uint64) for t in range(lv + 1)])
+    out = o.modup(d, lv)
+    mods = list(o.q[:lv + 1]) + [int(v) for v in o.chain["p"]]
+    assert out.shape == (-(-(lv + 1) // alpha), len(mods), o.n)
+    us = []
+    for j in range(out.shape[0]):
+        D = list(range(j * alpha, min((j + 1) * alpha, lv + 1)))
+        for k in range(o.n):
+            X, QD = crt([int(d[i, k]) for i in D], [o.q[i] for i in D])
+            X = centred(X, QD)
+            bound = len(D) // 2 + 1
+            u_seen = set()
+            for t, mt in enumerate(mods):
+                v = int(out[j, t, k])
+                if t in D:
+                    assert v == int(d[t, k])
+                    continue
+                cand = [u for u in range(-bound, bound + 1) if (X + u * QD - v) % mt == 0]
+                assert len(cand) == 1, (j, k, t)
+                u_seen.add(cand[0])
+            assert len(u_seen) == 1, (j, k, u_seen)   # one integer Y on every limb
+            us.append(u_seen.pop())
+    assert abs(np.mean(us)) < 0.2
+
+
 def test_relinearisation_noise_is_small(params):
     o = small_oracle(params, log_n=6)
     rng = np.random.default_rng(6)
