@@ -38,7 +38,7 @@ typedef struct he_ctx he_ctx;
 /* CKKS parameters (Sec. 2.2; Table 4 for the 128-bit-security size).  Q = q_0 ... q_{n_q-1},
  * P = p_0 ... p_{n_p-1}; alpha = n_p primes per key-switching digit. */
 typedef struct {
-    int log_n;                 /* ring degree N = 2^log_n, N/2 slots */
+    int log_n;                 /* ring degree N = 2^log_n, N/2 slots; 12 or 16 (HE_EINVAL otherwise) */
     int n_q;
     const uint64_t *q;         /* n_q primes, q_i = 1 mod 2N, < 2^60 */
     int n_p;

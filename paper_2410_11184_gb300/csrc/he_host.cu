@@ -81,8 +81,8 @@ struct he_ctx {
     std::vector<uint64_t> mods;
     std::vector<ModC> modc;
     ModC *d_mods = nullptr;
-    uint64_t *d_tw = nullptr, *d_ninv = nullptr;
-    ulonglong2 *d_tw2 = nullptr;   // the same twiddles as (w, w') pairs for the register-blocked passes
+    uint64_t *d_ninv = nullptr;
+    ulonglong2 *d_tw2 = nullptr;   // per modulus: N (w, w') forward twiddle pairs, then N inverse pairs
     std::vector<std::vector<size_t>> cv_off;
     uint64_t *d_cv = nullptr;
     uint64_t *d_mdcv = nullptr, *d_pinv = nullptr, *d_qlinv = nullptr;
@@ -263,48 +263,22 @@ static LimbMap single(int p) {
 
 // ------------------------------------------------------------------------- NTT launches
 // NTT of `count` limbs in place, or out of place from src (limb l of polynomial i at
-// src + i src_stride + l N) when src is given
-static bool ntt_rb(const he_ctx *c) { return c->logN == 16 || c->logN == 12; }
-
-// fuse (register-blocked sizes only): neighbours of a forward transform, see NttFuse
+// src + i src_stride + l N) when src is given; register-blocked passes of 8 (N = 2^12) or 16
+// (N = 2^16) coefficients per thread, the only ring sizes a context accepts.
+// fuse: neighbours of a forward transform, see NttFuse
 static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long poly_stride, bool inverse,
                 const char *site = "ntt", const uint64_t *src = nullptr, long src_stride = 0,
                 const NttFuse *fuse = nullptr) {
     if (count <= 0) return;
-    bool rb = ntt_rb(c);
-    REQUIRE(!fuse || (rb && !inverse), HE_EINVAL, "fused transform: forward, register-blocked sizes only");
-    if (src && !rb) {
-        CK(cudaMemcpy2DAsync(base, (size_t)poly_stride * 8, src, (size_t)src_stride * 8, (size_t)map.nper * c->N * 8,
-                             count / map.nper, cudaMemcpyDeviceToDevice, c->st));
-        src = nullptr;
-    }
-    int logN1 = c->logN / 2;
-    int N1 = 1 << logN1, N2 = c->N >> logN1;
-    int C = std::min(16, N2);
-    int R = std::max(1, std::min(N1, 2048 / N2));
-    dim3 g1(N2 / C, count), g2(N1 / R, count);
-    size_t sm1 = (size_t)N1 * C * 8, sm2 = (size_t)R * N2 * 8;
+    REQUIRE(!fuse || !inverse, HE_EINVAL, "fused transform: forward only");
     // algorithmic bytes: the transform's read + write, plus what a fused ModDown epilogue reads
     double extra = !fuse ? 0.0
                    : fuse->kind == 1 ? 8.0 * count * c->N * (fuse->add ? 2 : 1)
                    : fuse->kind == 3 ? 16.0 * count * c->N : 0.0;
     ProfScope ps(c, site, 16.0 * count * c->N + extra);
     c->launches++;
-    if (rb) {
-        // register-blocked passes: 16 (N = 2^16) or 8 (N = 2^12) coefficients per thread
-        launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
-                      c->d_ninv, c->logN, c->st, src, src_stride, fuse);
-        LAUNCH_CHECK();
-        return;
-    }
-    if (!inverse) {
-        k_ntt_cols_fwd<<<g1, 256, sm1, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, C);
-        k_ntt_rows_fwd<<<g2, 256, sm2, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, R);
-    } else {
-        k_ntt_rows_inv<<<g2, 256, sm2, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->logN, logN1, R);
-        k_ntt_cols_inv<<<g1, 256, sm1, c->st>>>(base, map.nper, poly_stride, map, c->d_mods, c->d_tw, c->d_ninv,
-                                                 c->logN, logN1, C);
-    }
+    launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
+                  c->d_ninv, c->logN, c->st, src, src_stride, fuse);
     LAUNCH_CHECK();
 }
 
@@ -437,35 +411,16 @@ static DCt rescale(he_ctx *c, const DCt &a) {
     DPtr last = dalloc(c, (size_t)npoly * c->N);
     ntt(c, last.get(), npoly, single(l), c->N, true, "ntt_rescale", a.d + (long)l * c->N, (long)L * c->N);
     DPtr tmp = dalloc(c, (size_t)npoly * l * c->N);
-    if (ntt_rb(c)) {
-        // spread of the centred last limb and the final (x - t) q_l^{-1} fused into the transform
-        DCt y = ct_new(c, l - 1, a.nct, a.scale / (double)c->mods[l]);
-        NttFuse F{};
-        F.kind = 2;
-        F.x = a.d;
-        F.out = y.d;
-        F.cst = c->d_qlinv + (size_t)l * 2 * c->nq;
-        F.last = last.get();
-        F.ql = c->mods[l];
-        ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false, "ntt_rescale", nullptr, 0, &F);
-        c->cnt[3]++;
-        return y;
-    }
-    long tot = (long)npoly * l << c->logN;
-    {
-        ProfScope ps_(c, "rescale", 8.0 * c->N * npoly * (1 + l));
-        k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp.get(), last.get(), npoly, l, qmap(l), c->d_mods,
-                                                               c->mods[l], c->logN);
-    }
-    LAUNCH_CHECK();
-    ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false, "ntt_rescale");
+    // spread of the centred last limb and the final (x - t) q_l^{-1} fused into the transform
     DCt y = ct_new(c, l - 1, a.nct, a.scale / (double)c->mods[l]);
-    {
-        ProfScope ps_(c, "rescale", 8.0 * c->N * npoly * 3.0 * l);
-        k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, a.d, tmp.get(), npoly, L, qmap(l), c->d_mods,
-                                                            c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
-    }
-    LAUNCH_CHECK();
+    NttFuse F{};
+    F.kind = 2;
+    F.x = a.d;
+    F.out = y.d;
+    F.cst = c->d_qlinv + (size_t)l * 2 * c->nq;
+    F.last = last.get();
+    F.ql = c->mods[l];
+    ntt(c, tmp.get(), npoly * l, qmap(l), (long)l * c->N, false, "ntt_rescale", nullptr, 0, &F);
     c->cnt[3]++;
     return y;
 }
@@ -573,7 +528,6 @@ static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, 
     int al = c->alpha, nl = L + al;
     ntt(c, acc + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true, "ntt_moddown");
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
-    long tot = (long)2 * nct * L << c->logN;
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (al + L));
         k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc, 2 * nct, L, al, qmap(L),
@@ -581,27 +535,17 @@ static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, 
                                                                                   c->nq, c->logN);
     }
     LAUNCH_CHECK();
-    if (ntt_rb(c)) {
-        // (x - conv) P^{-1} (+ add) fused into the transform of conv
-        NttFuse F{};
-        F.kind = 1;
-        F.alpha = al;
-        F.x = acc;
-        F.out = out;
-        F.so = so;
-        F.add = add;
-        F.sadd = sadd;
-        F.cst = c->d_pinv;
-        ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown", nullptr, 0, &F);
-        return;
-    }
-    ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown");
-    {
-        ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * L * (add ? 4 : 3));
-        k_moddown_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, so, acc, conv.get(), 2 * nct, L, al, qmap(L),
-                                                            c->d_mods, c->d_pinv, c->logN, add, sadd);
-    }
-    LAUNCH_CHECK();
+    // (x - conv) P^{-1} (+ add) fused into the transform of conv
+    NttFuse F{};
+    F.kind = 1;
+    F.alpha = al;
+    F.x = acc;
+    F.out = out;
+    F.so = so;
+    F.add = add;
+    F.sadd = sadd;
+    F.cst = c->d_pinv;
+    ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown", nullptr, 0, &F);
 }
 
 // one key switch: inner product and ModDown into out (see ks_moddown for add)
@@ -675,26 +619,16 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     LAUNCH_CHECK();
     DCt y = ct_new(c, l - 1, nct, scale / (double)c->mods[l]);
     const uint64_t *cst = c->d_rrpq + (size_t)l * c->nq * 4;
-    if (ntt_rb(c)) {
-        NttFuse F{};
-        F.kind = 3;
-        F.alpha = nd;
-        F.x = acc.get();
-        F.add = d;
-        F.sadd = 3L * L * c->N;
-        F.out = y.d;
-        F.so = y.cs(c);
-        F.cst = cst;
-        ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown", nullptr, 0, &F);
-    } else {
-        ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown");
-        {
-            ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * l * 4);
-            k_relin_rescale_fin<<<grid_for(c, (long)2 * nct * l << c->logN), 256, 0, c->st>>>(
-                y.d, acc.get(), nl, d, conv.get(), 2 * nct, l, qmap(l), c->d_mods, cst, c->logN);
-        }
-        LAUNCH_CHECK();
-    }
+    NttFuse F{};
+    F.kind = 3;
+    F.alpha = nd;
+    F.x = acc.get();
+    F.add = d;
+    F.sadd = 3L * L * c->N;
+    F.out = y.d;
+    F.so = y.cs(c);
+    F.cst = cst;
+    ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown", nullptr, 0, &F);
     c->cnt[3]++;
     return y;
 }
@@ -1796,8 +1730,6 @@ static void build_tables(he_ctx *c) {
         ninv[2 * t] = ni;
         ninv[2 * t + 1] = h_shoup(ni, q);
     }
-    CK(cudaMalloc(&c->d_tw, tw.size() * 8));
-    CK(cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
     {
         std::vector<ulonglong2> tw2((size_t)nm * 2 * N);
         for (int t = 0; t < nm; t++) {
@@ -1984,15 +1916,8 @@ static void build_tables(he_ctx *c) {
     // the conversion and inner-product kernels hold alpha residues and ndig key words per
     // thread, and their 128-bit sums must stay below q 2^64
     REQUIRE(al >= 1 && al <= 8 && c->ndig_top <= 8, HE_EINVAL, "alpha and the digit count must be at most 8");
-    // dynamic shared memory of the column pass (N1 * 16 words)
-    int logN1 = c->logN / 2;
-    size_t sm1 = (size_t)(1 << logN1) * std::min(16, N >> logN1) * 8;
     // linear-transform inner sums: up to HE_LT_MAXPT staged plaintext tiles of HE_LT_KT words
     CK(cudaFuncSetAttribute(k_lt_bsgs, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_LT_MAXPT * HE_LT_KT * 8));
-    if (sm1 > 48 * 1024) {
-        CK(cudaFuncSetAttribute(k_ntt_cols_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-        CK(cudaFuncSetAttribute(k_ntt_cols_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-    }
 }
 
 // ------------------------------------------------------------------------- C ABI
@@ -2014,7 +1939,8 @@ extern "C" {
 int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out) {
     if (!p || !out) return HE_EINVAL;
     *out = nullptr;
-    if (p->log_n < 4 || p->log_n > 17 || p->n_q < 1 || p->n_p < 1 || p->n_q + p->n_p > HE_MAX_MODS ||
+    // ring degree: the register-blocked NTT passes exist for N = 2^12 and N = 2^16
+    if ((p->log_n != 12 && p->log_n != 16) || p->n_q < 1 || p->n_p < 1 || p->n_q + p->n_p > HE_MAX_MODS ||
         p->n_q > HE_MAX_LIMBS - p->n_p || !p->q || !p->p || p->h < 1 || p->h > (1 << p->log_n))
         return HE_EINVAL;
     he_ctx *c = new he_ctx();
@@ -2090,7 +2016,7 @@ void he_context_destroy(he_ctx *c) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
-    void *ptrs[] = {c->d_mods, c->d_tw, c->d_tw2, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx,
+    void *ptrs[] = {c->d_mods, c->d_tw2, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx,
                     c->d_rrcv, c->d_rrpq, c->d_rridx, c->d_zeta,
                     c->d_rg, c->d_cdt, c->d_radix, c->d_radinv, c->d_qd, c->d_s, c->d_pk};
     for (void *q : ptrs)

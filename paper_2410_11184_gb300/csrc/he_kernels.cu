@@ -6,132 +6,6 @@
 #include "he_kernels.cuh"
 
 // ------------------------------------------------------------------------------------------
-// Negacyclic NTT (Cooley-Tukey with merged psi twist; output in bit-reversed order:
-// a_hat[k] = a(psi^(2 brv(k) + 1))) and its Gentleman-Sande inverse.  N = N1 * N2: the first
-// log2(N1) stages act on the N2 columns {c + N2 r}, the rest on the N1 rows of N2 contiguous
-// coefficients; each pass stages one tile in shared memory.
-// tw layout per modulus: [psi_rev | psi_rev_shoup | ipsi_rev | ipsi_rev_shoup], each N long.
-
-__global__ void k_ntt_cols_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, int logN, int logN1, int C) {
-    extern __shared__ uint64_t sm[];
-    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
-    const int l = blockIdx.y, p = map.prime[l % nper];
-    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
-    const uint64_t q = mods[p].q;
-    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
-    const int c0 = blockIdx.x * C;
-    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
-        int r = idx / C, c = idx % C;
-        sm[idx] = a[(long)r * N2 + c0 + c];
-    }
-    __syncthreads();
-    for (int m = 1, t = N1 >> 1; m < N1; m <<= 1, t >>= 1) {
-        for (int b = threadIdx.x; b < (N1 >> 1) * C; b += blockDim.x) {
-            int c = b % C, j = b / C;
-            int i = j / t, r = 2 * i * t + (j % t);
-            uint64_t w = psi[m + i], wp = psip[m + i];
-            uint64_t u = sm[r * C + c], v = mul_shoup(sm[(r + t) * C + c], w, wp, q);
-            sm[r * C + c] = add_mod(u, v, q);
-            sm[(r + t) * C + c] = sub_mod(u, v, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
-        int r = idx / C, c = idx % C;
-        a[(long)r * N2 + c0 + c] = sm[idx];
-    }
-}
-
-__global__ void k_ntt_rows_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, int logN, int logN1, int R) {
-    extern __shared__ uint64_t sm[];
-    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1, h2 = N2 >> 1;
-    const int l = blockIdx.y, p = map.prime[l % nper];
-    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
-    const uint64_t q = mods[p].q;
-    const uint64_t *psi = tw + (long)p * 4 * N, *psip = psi + N;
-    const int row0 = blockIdx.x * R;
-    uint64_t *g = a + (long)row0 * N2;
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = g[idx];
-    __syncthreads();
-    for (int m = N1, t = h2; m < N; m <<= 1, t >>= 1) {
-        for (int b = threadIdx.x; b < R * h2; b += blockDim.x) {
-            int rr = b / h2, j = b % h2;
-            int il = j / t, ci = 2 * il * t + (j % t);
-            int ig = (row0 + rr) * (m >> logN1) + il;
-            uint64_t w = psi[m + ig], wp = psip[m + ig];
-            uint64_t *s = sm + rr * N2;
-            uint64_t u = s[ci], v = mul_shoup(s[ci + t], w, wp, q);
-            s[ci] = add_mod(u, v, q);
-            s[ci + t] = sub_mod(u, v, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) g[idx] = sm[idx];
-}
-
-__global__ void k_ntt_rows_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, int logN, int logN1, int R) {
-    extern __shared__ uint64_t sm[];
-    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1, h2 = N2 >> 1;
-    const int l = blockIdx.y, p = map.prime[l % nper];
-    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
-    const uint64_t q = mods[p].q;
-    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
-    const int row0 = blockIdx.x * R;
-    uint64_t *g = a + (long)row0 * N2;
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = g[idx];
-    __syncthreads();
-    for (int t = 1, h = N >> 1; t < N2; t <<= 1, h >>= 1) {
-        for (int b = threadIdx.x; b < R * h2; b += blockDim.x) {
-            int rr = b / h2, j = b % h2;
-            int il = j / t, ci = 2 * il * t + (j % t);
-            int ig = (row0 + rr) * (h >> logN1) + il;
-            uint64_t w = ipsi[h + ig], wp = ipsip[h + ig];
-            uint64_t *s = sm + rr * N2;
-            uint64_t u = s[ci], v = s[ci + t];
-            s[ci] = add_mod(u, v, q);
-            s[ci + t] = mul_shoup(sub_mod(u, v, q), w, wp, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) g[idx] = sm[idx];
-}
-
-__global__ void k_ntt_cols_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, const uint64_t *ninv, int logN, int logN1, int C) {
-    extern __shared__ uint64_t sm[];
-    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
-    const int l = blockIdx.y, p = map.prime[l % nper];
-    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
-    const uint64_t q = mods[p].q;
-    const uint64_t *ipsi = tw + (long)p * 4 * N + 2 * N, *ipsip = ipsi + N;
-    const int c0 = blockIdx.x * C;
-    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
-        int r = idx / C, c = idx % C;
-        sm[idx] = a[(long)r * N2 + c0 + c];
-    }
-    __syncthreads();
-    for (int t = 1, h = N1 >> 1; h >= 1; t <<= 1, h >>= 1) {
-        for (int b = threadIdx.x; b < (N1 >> 1) * C; b += blockDim.x) {
-            int c = b % C, j = b / C;
-            int i = j / t, r = 2 * i * t + (j % t);
-            uint64_t w = ipsi[h + i], wp = ipsip[h + i];
-            uint64_t u = sm[r * C + c], v = sm[(r + t) * C + c];
-            sm[r * C + c] = add_mod(u, v, q);
-            sm[(r + t) * C + c] = mul_shoup(sub_mod(u, v, q), w, wp, q);
-        }
-        __syncthreads();
-    }
-    const uint64_t ni = ninv[2 * p], nip = ninv[2 * p + 1];
-    for (int idx = threadIdx.x; idx < N1 * C; idx += blockDim.x) {
-        int r = idx / C, c = idx % C;
-        a[(long)r * N2 + c0 + c] = mul_shoup(sm[idx], ni, nip, q);
-    }
-}
-
-// ------------------------------------------------------------------------------------------
 // Elementwise kernels over a batch (count limbs, addressing as above).
 #define EW_PROLOGUE                                                                           \
     const int N = 1 << logN;                                                                  \
@@ -167,25 +41,6 @@ __global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa,
     EW_PROLOGUE
     long off = (long)li * N + k;
     out[po * so + off] = mul_mod(a[po * sa + off], scal.v[li], m);
-    }
-}
-
-// relinearisation + rescale, final step where the transform is not fused (see NttFuse kind 3):
-// out_i = (P d_i + K_i - conv_i) (P q_l)^{-1} for the npoly output polynomials of l limbs
-__global__ void k_relin_rescale_fin(uint64_t *out, const uint64_t *K, int nl, const uint64_t *d, const uint64_t *conv,
-                                    int npoly, int l, LimbMap qmap, const ModC *mods, const uint64_t *cst, int logN) {
-    const int N = 1 << logN;
-    long total = (long)npoly * l << logN;
-    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
-        int r = (int)(id >> logN), k = (int)(id & (N - 1));
-        int i = r % l, pl = r / l;
-        const uint64_t q = mods[qmap.prime[i]].q;
-        const uint64_t *e = cst + 4 * i;
-        uint64_t y = add_mod(mul_shoup(d[(long)(pl / 2) * 3 * (l + 1) * N + (long)(pl % 2) * (l + 1) * N + (long)i * N + k],
-                                       e[0], e[1], q),
-                             K[(long)pl * nl * N + (long)i * N + k], q);
-        out[(long)(pl / 2) * 2 * l * N + (long)(pl % 2) * l * N + (long)i * N + k] =
-            mul_shoup(sub_mod(y, conv[(long)r * N + k], q), e[2], e[3], q);
     }
 }
 
@@ -485,25 +340,6 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
             }
             o[(long)i * N] = redc(lo, hi, mi);
         }
-    }
-}
-
-// out_i = (x_i - conv_i) * pinv_i for the Q limbs of every polynomial; accumulate adds to out
-__global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
-                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN,
-                              const uint64_t *add, long sadd) {
-    const int N = 1 << logN;
-    long total = (long)npoly * L << logN;
-    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
-        int l = (int)(id >> logN), k = (int)(id & (N - 1));
-        int i = l % L, pl = l / L;
-        const ModC mi = mods[qmap.prime[i]];
-        uint64_t v = sub_mod(x[(long)pl * (L + alpha) * N + (long)i * N + k], conv[(long)pl * L * N + (long)i * N + k], mi.q);
-        v = mul_shoup(v, pinv[2 * qmap.prime[i]], pinv[2 * qmap.prime[i] + 1], mi.q);
-        long o = (long)(pl / 2) * so + (long)(pl % 2) * L * N + (long)i * N + k;
-        // add (may be out itself): polynomial p of ciphertext c at add + c sadd + p L N
-        if (add) v = add_mod(add[(long)(pl / 2) * sadd + (long)(pl % 2) * L * N + (long)i * N + k], v, mi.q);
-        out[o] = v;
     }
 }
 
@@ -870,6 +706,10 @@ __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_i
 }
 
 // ------------------------------------------------------------------------------------------
+// Negacyclic NTT (Cooley-Tukey with merged psi twist; output in bit-reversed order:
+// a_hat[k] = a(psi^(2 brv(k) + 1))) and its Gentleman-Sande inverse, for N = 2^12 and 2^16.
+// Twiddles per modulus p: N (psi^brv(k), Shoup companion) pairs at tw2 + 2 N p, then the N
+// inverse pairs.
 // Register-blocked NTT passes.  A pass runs LOGS = 2*LOGE stages on sub-transforms of size
 // S = 2^LOGS; each thread holds E = 2^LOGE elements of one sub-transform in registers.
 // First LOGE stages: thread lane k holds elements k + E*j (pairs (j, j + 2^p) are its own);

@@ -74,14 +74,6 @@ struct LcArgs {
     int nt;
 };
 
-__global__ void k_ntt_cols_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, int logN, int logN1, int C);
-__global__ void k_ntt_rows_fwd(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, int logN, int logN1, int R);
-__global__ void k_ntt_rows_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, int logN, int logN1, int R);
-__global__ void k_ntt_cols_inv(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods,
-                               const uint64_t *tw, const uint64_t *ninv, int logN, int logN1, int C);
 __global__ void k_add(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
                       int count, int nper, LimbMap map, const ModC *mods, int logN, int sub);
 __global__ void k_mul(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
@@ -93,8 +85,6 @@ __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int npe
 __global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
                          int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
 __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN);
-__global__ void k_relin_rescale_fin(uint64_t *out, const uint64_t *K, int nl, const uint64_t *d, const uint64_t *conv,
-                                    int npoly, int l, LimbMap qmap, const ModC *mods, const uint64_t *cst, int logN);
 __global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal, int count, int nper,
                               LimbMap map, const ModC *mods, int logN);
 __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, LimbMap map,
@@ -109,9 +99,6 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
                             int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN);
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN);
-__global__ void k_moddown_fin(uint64_t *out, long so, const uint64_t *x, const uint64_t *conv, int npoly, int L,
-                              int alpha, LimbMap qmap, const ModC *mods, const uint64_t *pinv, int logN,
-                              const uint64_t *add, long sadd);
 
 __global__ void k_ks_inner_sum(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig,
                                int L, int alpha, LimbMap tmap, const ModC *mods, int key_nlimb, int nq_all, int logN,
