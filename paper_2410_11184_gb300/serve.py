@@ -15,6 +15,7 @@ drives the GPU through the C ABI.
 from __future__ import annotations
 
 import collections
+import itertools
 import threading
 import time
 
@@ -22,11 +23,10 @@ import time
 class Request:
     """One encrypted Softmax request (host buffers; results are written into host_out)."""
 
-    _ids = 0
+    _ids = itertools.count(1)   # next() on a count is atomic: submit() may run on many threads
 
     def __init__(self, plan, n_ct, level, scale, host_in, host_out, words):
-        Request._ids += 1
-        self.rid = Request._ids
+        self.rid = next(Request._ids)
         self.plan = plan            # plan name
         self.n_ct = n_ct
         self.level = level
@@ -193,6 +193,9 @@ class Server:
     # ---- worker
     def _loop(self):
         while True:
+            # cleared before the arrivals are drained: a submit() after this point sets it again,
+            # so the wait below returns at once instead of sleeping through its timeout
+            self.wake.clear()
             with self.lock:
                 while self.arrivals:
                     self.waiting.append(self.arrivals.popleft())
@@ -205,7 +208,6 @@ class Server:
             if not self.running and not (self.waiting or self.admitted or self.inflight or self.arrivals):
                 return
             self.wake.wait(0.0002 if self.inflight else 0.01)
-            self.wake.clear()
 
     def _launch(self, batch):
         torch, g = self.torch, self.g

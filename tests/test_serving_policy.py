@@ -62,3 +62,24 @@ def test_percentile_nearest_rank():
     assert percentile(xs, 50) == 50 and percentile(xs, 99) == 99 and percentile(xs, 100) == 100
     assert percentile([7.0], 99) == 7.0
     assert percentile([3, 1, 2], 50) == 2
+
+
+def test_request_ids_unique_across_threads():
+    """submit() may run on many client threads: every request gets its own id."""
+    import threading
+
+    from paper_2410_11184_gb300.serve import Request
+
+    ids, lock = [], threading.Lock()
+
+    def make():
+        got = [Request("p", 1, 0, 1.0, None, None, 1).rid for _ in range(2000)]
+        with lock:
+            ids.extend(got)
+
+    ts = [threading.Thread(target=make) for _ in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert len(ids) == len(set(ids)) == 16000
