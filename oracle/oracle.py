@@ -388,6 +388,39 @@ def simulate(x, plan):
     return y, sums
 
 
+def simulate_b(x, plan):
+    """Alg. 4 (version B) in FP64 with the plan's polynomials (no encryption error).
+    lambda accumulates lambda_j = P_j(gain_s S_j) gain_s^(1/2^j), which is S_j^(-1/2^j) for
+    exact P_j; z = lambda y^(0) and y^(j) = z^(2^j) by j squarings.  x: [L][n] inputs in
+    [-M, 0]; returns y^(k) and the per-round sums of squares S_j."""
+    x = np.asarray(x, dtype=np.float64)
+    M, k = plan["M"], plan["k"]
+    ec = [float.fromhex(h) for h in plan["exp"]["coeffs"]]
+    y0 = cheb_eval(ec, 2.0 * x / M + 1.0)
+    lam = np.ones(x.shape[:-1] + (1,))
+    y, sums = y0, []
+    for j, it in enumerate(plan["iters"][:k], start=1):
+        c = [float.fromhex(h) for h in it["coeffs"]]
+        S = np.sum(y * y, axis=-1, keepdims=True)
+        sums.append(S[..., 0])
+        v = it["gain_s"] * S
+        u = (2.0 * v - it["a"] - it["b"]) / (it["b"] - it["a"])
+        lam = lam * cheb_eval(c, u) * it["gain_s"] ** it["exponent"]
+        y = lam * y0
+        for _ in range(j):
+            y = y * y
+    return y, sums
+
+
+def load_plans_b():
+    """The Alg. 4 plans (params/plans_b.json), or {} where they have not been generated."""
+    path = os.path.join(os.path.dirname(HERE), "paper_2410_11184_gb300", "params", "plans_b.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return json.load(fh)
+
+
 def pack(x, m, n0):
     """Sec. 4.2 packing: x [L][n] -> m slot vectors; slot t*L + l of ct c holds x[l][c*(n/m) + t]."""
     x = np.asarray(x, dtype=np.float64)

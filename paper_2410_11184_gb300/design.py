@@ -283,6 +283,51 @@ def design_softmax(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
     }
 
 
+def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
+    """Polynomials of Alg. 4 (version B) for inputs in [-M, 0]^n with k rounds.
+
+    Round j needs lambda_j = S_j^(-1/2^j), S_j = sum (y^(j-1))^2 (the reading under which every
+    round normalises), as a weighted minimax P_j of v^(-1/2^j), min ||P_j(v) v^(1/2^j) - 1||.
+    A relative error eps_j of lambda_j becomes (1 + eps_j)^(2^j) - 1 =: delta_j in y^(j), since
+    y^(j) = (lambda y^(0))^(2^j); the next round starts from a vector whose sum is within
+    delta_j of 1, so its S lies in [(1 - delta_j)^2 / n, (1 + delta_j)^2].  Round 1 takes
+    v = S_1 / n in [e^(-2A), 1], A = M / 2^k, and lambda_1 = P_1(v) n^(-1/2)."""
+    A = M / 2.0 ** k
+    ce, ee = weighted_minimax(lambda u: np.exp(A * (u - 1.0) / 2.0), lambda u: np.ones_like(u),
+                              -1.0, 1.0, exp_deg)
+    iters = []
+    lo, hi = math.exp(-2.0 * A) * (1.0 - ee) ** 2, (1.0 + ee) ** 2
+    delta = None
+    for j, d in enumerate(inv_degs, start=1):
+        e = 2.0 ** -j
+        if j > 1:
+            if delta >= 1.0:
+                raise ValueError("round %d: delta %.3g >= 1 leaves no interval" % (j - 1, delta))
+            lo, hi = (1.0 - delta) ** 2 / n, (1.0 + delta) ** 2
+        a, b = lo * (1.0 - margin), hi * (1.0 + margin)
+        c, eps = weighted_minimax(lambda v, e=e: v ** -e, lambda v, e=e: v ** e, a, b, d)
+        delta = (1.0 + eps) ** (2 ** j) - 1.0
+        iters.append({"deg": d, "a": a, "b": b, "coeffs": hexlist(c), "eps": eps, "delta": delta,
+                      "exponent": e, "gain_s": 1.0 / n if j == 1 else 1.0})
+    return {"name": name, "chain": chain_name, "version": "B", "n": n, "M": M, "k": k, "A": A,
+            "exp": {"kind": "exp", "a": -1.0, "b": 1.0, "deg": exp_deg, "coeffs": hexlist(ce), "err": ee},
+            "iters": iters}
+
+
+def build_b(write=True):
+    """Alg. 4 plans (params/plans_b.json).  n = 256 on [-128, 0] with k = 4: the main thread
+    uses ceil(log2 16) = 4 levels for exp, 1 for z = lambda y0 and k for z^(2^k), 9 in all,
+    which the N = 2^16 chain has between its top user level 12 and its bootstrapping input
+    level 3, so the main thread is never bootstrapped.  A = 8 makes round 1's interval
+    [e^-16, 1]: degree 1023 keeps delta_1 below 1 (0.85); degree 127 then suffices."""
+    plans = {"n256_M128_B": design_softmax_b("n256_M128_B", "fgb16", 256, 128.0, 4, 15, [1023, 127, 127, 127])}
+    if write:
+        os.makedirs(PARAMS_DIR, exist_ok=True)
+        with open(os.path.join(PARAMS_DIR, "plans_b.json"), "w") as fh:
+            json.dump(plans, fh, indent=1)
+    return plans
+
+
 def design_evalmod(K, r, deg):
     """cos(2 pi (K u - 1/4) / 2^r) on u in [-1, 1]; r double angles give sin(2 pi K u)."""
     g = lambda u: np.cos(2.0 * np.pi * (K * u - 0.25) / 2.0 ** r)
@@ -338,6 +383,14 @@ def load_params():
 
 
 if __name__ == "__main__":
+    import sys
+
+    if "--version-b" in sys.argv:
+        # Alg. 4 plans only (params/plans_b.json); the other parameter files stay as they are
+        for p in build_b(write=True).values():
+            print(p["name"], "k=%d exp_err=%.3g" % (p["k"], p["exp"]["err"]),
+                  [("%d" % it["deg"], "%.3g" % it["eps"], "%.3g" % it["delta"]) for it in p["iters"]])
+        sys.exit(0)
     chains, plans, evalmod = build_all(write=True)
     for c in chains.values():
         print(c["name"], "logQP=%.2f" % c["log_qp"], "nq=%d np=%d" % (len(c["q"]), len(c["p"])))

@@ -1,0 +1,95 @@
+"""Alg. 4 (version B) in FP64: the reading of its lambda_j, the designed polynomials, and the
+level budget that lets the many-ciphertext main thread run without bootstrapping.
+
+Alg. 4 prints lambda_j = (sum (y^(j-1))^2)^(-2^-(j-1)).  With that exponent round 1 gives
+sum y^(1) = 1 / S_1, not 1.  The reading lambda_j = S_j^(-1/2^j) normalises every round:
+lambda^(2^j) sum (y^(0))^(2^j) = 1, and y^(k) = Softmax(x) (Sec. 4.3)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2410_11184_gb300 import workloads as W
+
+
+def _alg4_exact(x, k, exponent):
+    """Alg. 4 with exact exp and exact powers; exponent(j) is the power applied to S_j."""
+    y0 = np.exp(x / 2.0 ** k)
+    lam = np.ones((x.shape[0], 1))
+    y, sums = y0, []
+    for j in range(1, k + 1):
+        S = np.sum(y * y, axis=1, keepdims=True)
+        lam = lam * S ** exponent(j)
+        y = (lam * y0) ** (2 ** j)
+        sums.append(np.sum(y, axis=1))
+    return y, sums
+
+
+def test_reading_normalises_every_round_and_gives_softmax():
+    x = W.uniform_inputs(200, 64, seed=2, M=32.0)
+    y, sums = _alg4_exact(x, 4, lambda j: -(2.0 ** -j))
+    for s in sums:
+        assert np.allclose(s, 1.0, atol=1e-12)
+    assert np.abs(y - O.softmax_fp64(x)).max() < 1e-12
+    # the printed exponent -2^-(j-1): the first round already misses the normalisation
+    _, printed = _alg4_exact(x, 4, lambda j: -(2.0 ** -(j - 1)))
+    assert np.abs(printed[0] - 1.0).min() > 1e-3
+
+
+def test_simulation_with_exact_polynomials_is_softmax(params):
+    """simulate_b with near-exact polynomials (degree-120 interpolants of v^(-1/2^j) on wide
+    intervals, exp of degree 40) reproduces Softmax: pins the simulation's bookkeeping (gains,
+    the accumulated lambda, the squarings) independently of the designed minimax."""
+    from paper_2410_11184_gb300 import design as D
+
+    n, M, k = 16, 8.0, 3
+    A = M / 2.0 ** k
+    ce, _ = D.cheb_interp(lambda u: np.exp(A * (u - 1.0) / 2.0), 40)
+    iters = []
+    for j in range(1, k + 1):
+        e = 2.0 ** -j
+        a, b = (math.exp(-2 * A) * 0.9, 1.1) if j == 1 else (0.5 / n, 1.5)
+        c, _ = D.cheb_interp(lambda u, a=a, b=b, e=e: (0.5 * (b - a) * u + 0.5 * (a + b)) ** -e, 120)
+        iters.append({"a": a, "b": b, "coeffs": D.hexlist(c), "exponent": e, "gain_s": 1.0 / n if j == 1 else 1.0})
+    plan = {"n": n, "M": M, "k": k, "exp": {"coeffs": D.hexlist(ce)}, "iters": iters}
+    x = W.uniform_inputs(300, n, seed=3, M=M)
+    y, _ = O.simulate_b(x, plan)
+    assert np.abs(y - O.softmax_fp64(x)).max() < 1e-9
+
+
+plans_b = O.load_plans_b()
+
+
+@pytest.mark.skipif("n256_M128_B" not in plans_b, reason="params/plans_b.json not generated")
+def test_designed_plan_precision():
+    """The stored n = 256, [-128, 0] plan (k = 4) against FP64 Softmax on the three input
+    models: at least 20 bits (the circuit then loses a few more to encryption noise)."""
+    plan = plans_b["n256_M128_B"]
+    for it in plan["iters"]:
+        assert it["delta"] < 1.0 and it["a"] < it["b"]
+    assert plan["iters"][-1]["delta"] < 2.0 ** -20
+    M = plan["M"]
+    for x in (W.attention_logits(300, 256, seed=5), W.paper_normal_inputs(300, 256, 6, M),
+              W.uniform_inputs(300, 256, 7, M)):
+        y, sums = O.simulate_b(x, plan)
+        assert -math.log2(np.abs(y - O.softmax_fp64(x)).max()) >= 20.0
+        # every S_j lies in the interval its polynomial was designed for
+        for it, S in zip(plan["iters"], sums):
+            v = it["gain_s"] * S
+            assert v.min() >= it["a"] and v.max() <= it["b"]
+
+
+@pytest.mark.skipif("n256_M128_B" not in plans_b, reason="params/plans_b.json not generated")
+def test_main_thread_fits_the_chain_without_bootstrapping(params):
+    """Main thread: exp (ceil(log2(deg + 1)) levels), z = lambda y0 (1), y^(j) = z^(2^j) (j).
+    The output y^(k) needs a level >= 0; the last auxiliary input (y^(k-1))^2 is summed and
+    bootstrapped, so it must stay at or above the level the bootstrapping starts from."""
+    plan = plans_b["n256_M128_B"]
+    ch = params[0][plan["chain"]]
+    top, bts = ch["user_top_level"], ch["bts_min_level"]
+    z_level = top - math.ceil(math.log2(plan["exp"]["deg"] + 1)) - 1
+    k = plan["k"]
+    assert z_level - k >= 0                   # y^(k), the output
+    assert z_level - (k - 1) - 1 >= bts       # (y^(k-1))^2, summed into S_k and bootstrapped
+    assert z_level - (5 - 1) - 1 < bts        # k = 5 (Thm 3.3's k for M = 128, n = 256) would not fit
