@@ -290,7 +290,7 @@ def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
     round normalises), as a weighted minimax P_j of v^(-1/2^j), min ||P_j(v) v^(1/2^j) - 1||.
     A relative error eps_j of lambda_j becomes (1 + eps_j)^(2^j) - 1 =: delta_j in y^(j), since
     y^(j) = (lambda y^(0))^(2^j); the next round starts from a vector whose sum is within
-    delta_j of 1, so its S lies in [(1 - delta_j)^2 / n, (1 + delta_j)^2].  Round 1 takes
+    delta_j of 1, so its S lies in [(1 - delta_j)^2 / n, (1 + delta_j)^2].  Iteration 1 takes
     v = S_1 / n in [e^(-2A), 1], A = M / 2^k, and lambda_1 = P_1(v) n^(-1/2)."""
     A = M / 2.0 ** k
     ce, ee = weighted_minimax(lambda u: np.exp(A * (u - 1.0) / 2.0), lambda u: np.ones_like(u),
@@ -318,7 +318,7 @@ def build_b(write=True):
     """Alg. 4 plans (params/plans_b.json).  n = 256 on [-128, 0] with k = 4: the main thread
     uses ceil(log2 16) = 4 levels for exp, 1 for z = lambda y0 and k for z^(2^k), 9 in all,
     which the N = 2^16 chain has between its top user level 12 and its bootstrapping input
-    level 3, so the main thread is never bootstrapped.  A = 8 makes round 1's interval
+    level 3, so the main thread is never bootstrapped.  A = 8 makes iteration 1's interval
     [e^-16, 1]: degree 1023 keeps delta_1 below 1 (0.85); degree 127 then suffices."""
     plans = {"n256_M128_B": design_softmax_b("n256_M128_B", "fgb16", 256, 128.0, 4, 15, [1023, 127, 127, 127])}
     if write:

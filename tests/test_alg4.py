@@ -1,7 +1,7 @@
 """Alg. 4 (version B) in FP64: the reading of its lambda_j, the designed polynomials, and the
 level budget that lets the many-ciphertext main thread run without bootstrapping.
 
-Alg. 4 prints lambda_j = (sum (y^(j-1))^2)^(-2^-(j-1)).  With that exponent round 1 gives
+Alg. 4 prints lambda_j = (sum (y^(j-1))^2)^(-2^-(j-1)).  With that exponent iteration 1 gives
 sum y^(1) = 1 / S_1, not 1.  The reading lambda_j = S_j^(-1/2^j) normalises every round:
 lambda^(2^j) sum (y^(0))^(2^j) = 1, and y^(k) = Softmax(x) (Sec. 4.3)."""
 import math
