@@ -73,6 +73,7 @@ def lib():
         L.orc_relin.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
         L.orc_relin_rescale.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
         L.orc_modup.argtypes = [C.c_void_p, u64p, C.c_int, u64p]
+        L.orc_add_const.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double]
         L.orc_hmult.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, u64p, C.c_int, C.c_double,
                                 u64p, intp, dblp]
         L.orc_galois_for_rot.argtypes = [C.c_void_p, C.c_long]
@@ -210,6 +211,12 @@ class Oracle:
         lib().orc_add(self.ptr, P(a.data), P(b.data), a.level, P(out))
         return Ct(out, a.level, a.scale)
 
+    def add_const(self, a, value):
+        """a + value on every slot: round(value * scale) added to c0's constant coefficient."""
+        out = a.data.copy()
+        self._chk(lib().orc_add_const(self.ptr, P(out), a.level, value * a.scale))
+        return Ct(out, a.level, a.scale)
+
     def mul_plain(self, a, pt):
         out = np.zeros_like(a.data)
         self._chk(lib().orc_mul_plain(self.ptr, P(a.data), a.level, P(_u64(pt)), P(out)))
@@ -295,8 +302,12 @@ class Oracle:
         em = np.array([float.fromhex(h) for h in evalmod["coeffs"]], dtype=np.float64)
         return bi, bd, em
 
-    def bootstrap(self, a, evalmod, gain=1.0):
+    def bootstrap(self, a, evalmod, gain=1.0, out_scale=None):
+        """Bootstrapping to user_top_level: the output encrypts gain * message at out_scale
+        (default Delta = 2^log_scale)."""
         bi, bd, em = self.bts_args(evalmod)
+        if out_scale is not None:
+            bd[1] = out_scale
         ut = self.chain["user_top_level"]
         out = np.zeros((2, ut + 1, self.n), dtype=np.uint64)
         lo = C.c_int()
@@ -335,6 +346,101 @@ class Oracle:
             flat = buf[i].reshape(-1)[: 2 * (lv + 1) * self.n]
             out.append(Ct(flat.reshape(2, lv + 1, self.n).copy(), lv, so.value))
         return out
+
+    def softmax_b(self, cts, plan, evalmod):
+        """Alg. 4 (version B) with the auxiliary thread of Alg. 3 on the m ciphertexts cts
+        (packing of Sec. 4.2; all at user_top_level with scale (2/M) q_top).  Python over the
+        oracle's operations; every scale is chosen so that the next polynomial input lands
+        exactly at the scale of its level's prime and every bootstrapping input at Delta.
+
+          u = 2x/M + 1 (scale bookkeeping and a constant), y0_c = P_exp(u) at scale
+              sqrt(Delta q) so that S_1 = sum_c y0_c^2 comes out at Delta
+          for j = 1..k:
+            S_j  = RotSum(relinearised sum_c y_c (x) y_c), y = y0 (j = 1) or y^(j-1)
+            v    = Bootstrap(gain_s S_j) at scale (2/(b_j - a_j)) q_top; u = affine(v)
+            lam  = P_j(u) gain_s^(1/2^j) (the gain folded into the coefficients)
+            Lam  = lam (j = 1) or Lam * lam, bootstrapped with gain 1/Lmax_j (compact: one
+                   value per Softmax in slots [0, L))
+            lr   = RotSum(Lam (.) mask), mask = 1 on slots [0, L), encoded at the scale that
+                   makes z land where the j squarings need it
+            z_c  = lr * y0_c, y^(j)_c = z_c^(2^j) (j squarings)
+        Returns the m output ciphertexts y^(k)."""
+        ch = self.chain
+        m, n, M, k = len(cts), plan["n"], plan["M"], plan["k"]
+        top = ch["user_top_level"]
+        delta = 2.0 ** ch["log_scale"]
+        boost = plan.get("bts_boost", 16.0)
+        stride, nrot = m * self.n0 // n, int(round(math.log2(n // m)))
+        q = [float(v) for v in self.q]
+
+        def bts(x, gain, out_scale):
+            y = self.bootstrap(x, evalmod, gain * boost, out_scale / boost)
+            y.scale *= boost
+            return y
+
+        def rotsum(x):
+            for i in range(nrot):
+                x = self.add(x, self.rotate(x, stride << i))
+            return x
+
+        def square_sum(ys):
+            lv = ys[0].level
+            qs = np.array(self.q[:lv + 1], dtype=object)[None, :, None]
+            d = sum(self.tensor(y, y).astype(object) for y in ys) % qs
+            out = self.relin_rescale(d.astype(np.uint64), lv)
+            return rotsum(Ct(out, lv - 1, ys[0].scale * ys[0].scale / q[lv]))
+
+        def cheb(c):
+            return [float.fromhex(h) for h in c]
+
+        # exp
+        ec = cheb(plan["exp"]["coeffs"])
+        de = int(math.ceil(math.log2(plan["exp"]["deg"] + 1)))
+        ly0 = cts[0].level - de
+        y0 = []
+        for x in cts:
+            u = Ct(x.data, x.level, x.scale / (2.0 / M))
+            u = self.add_const(u, 1.0)
+            y0.append(self.poly_eval(u, ec, ly0, math.sqrt(delta * q[ly0])))
+        ys, lam_c = y0, None
+        A = M / 2.0 ** k
+        for j, it in enumerate(plan["iters"][:k], start=1):
+            S = square_sum(ys)
+            a, b = it["a"], it["b"]
+            v = bts(S, it["gain_s"], (2.0 / (b - a)) * q[top])
+            v = Ct(v.data, v.level, v.scale / (2.0 / (b - a)))
+            v = self.add_const(v, -(a + b) / (b - a))
+            c = np.array(cheb(it["coeffs"])) * it["gain_s"] ** it["exponent"]
+            dj = int(math.ceil(math.log2(len(c))))
+            lp = top - dj
+            if lam_c is None:
+                lam = self.poly_eval(v, c, lp, delta)
+            else:
+                lam = self.poly_eval(v, c, lp, (delta * q[lp]) / lam_c.scale)
+                lam = self.hmult(lam_c, lam)
+            lmax = 1.1 * n ** -it["exponent"] * math.exp(A)
+            lam_c = bts(lam, 1.0 / lmax, delta)
+            lam_c = Ct(lam_c.data, lam_c.level, lam_c.scale * (1.0 / lmax))   # encrypts Lam / lmax at delta
+            # where z lands and the scale it needs there: j squarings then (j < k) one more for S
+            lz = ly0 - 1
+            s = delta
+            for i in range(j if j == k else j + 1, 0, -1):
+                s = math.sqrt(s * q[lz - i + 1])
+            s_lr = s * q[ly0] / y0[0].scale
+            mask = np.zeros(self.n0, dtype=complex)
+            mask[:stride] = 1.0
+            sm = s_lr * q[lam_c.level] / lam_c.scale
+            pt = self.encode(mask, sm, lam_c.level)
+            lr = self.mul_plain(lam_c, pt)
+            lr = Ct(lr.data, lr.level, lr.scale * sm)
+            lr = rotsum(self.rescale(lr))
+            ys = []
+            for y in y0:
+                z = self.hmult(lr, y)
+                for _ in range(j):
+                    z = self.hmult(z, z)
+                ys.append(z)
+        return ys
 
     def counters(self):
         a = (C.c_long * 5)()

@@ -228,6 +228,16 @@ int orc_modup(orc_ctx *c, const uint64_t *d, int level, uint64_t *out) {
     return 0;
 }
 
+/* adds round(v) to the constant coefficient of c0 (the constant v / scale on every slot) of the
+ * coefficient-form ciphertext a [2][level+1][N], in place */
+int orc_add_const(orc_ctx *c, uint64_t *a, int level, double v) {
+    if (level < 0 || level >= c->nq) return -1;
+    orc_ct x = wrap(c, a, level, 1.0);
+    ct_add_const_int(c, &x, round_to_i128(v));
+    unwrap(c, &x, a, NULL, NULL);
+    return 0;
+}
+
 int orc_hmult(orc_ctx *c, const uint64_t *a, int la, double sa, const uint64_t *b, int lb, double sb,
               uint64_t *out, int *lout, double *sout) {
     orc_ct x = wrap(c, a, la, sa), y = wrap(c, b, lb, sb), z;

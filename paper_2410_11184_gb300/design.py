@@ -314,13 +314,26 @@ def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
             "iters": iters}
 
 
-def build_b(write=True):
+def build_b(write=True, names=None):
     """Alg. 4 plans (params/plans_b.json).  n = 256 on [-128, 0] with k = 4: the main thread
     uses ceil(log2 16) = 4 levels for exp, 1 for z = lambda y0 and k for z^(2^k), 9 in all,
     which the N = 2^16 chain has between its top user level 12 and its bootstrapping input
     level 3, so the main thread is never bootstrapped.  A = 8 makes iteration 1's interval
     [e^-16, 1]: degree 1023 keeps delta_1 below 1 (0.85); degree 127 then suffices."""
-    plans = {"n256_M128_B": design_softmax_b("n256_M128_B", "fgb16", 256, 128.0, 4, 15, [1023, 127, 127, 127])}
+    specs = {
+        "n256_M128_B": ("fgb16", 256, 128.0, 4, 15, [1023, 127, 127, 127]),
+        # the same level map at N = 2^12 (toybts: user levels 12 ... 4), for the oracle's
+        # ciphertext circuit: A = 2 keeps every interval narrow enough for degree 63
+        "toybts_n16_M32_B": ("toybts", 16, 32.0, 4, 15, [63, 63, 63, 63]),
+    }
+    path = os.path.join(PARAMS_DIR, "plans_b.json")
+    plans = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            plans = json.load(fh)
+    for name, spec in specs.items():
+        if names is None or name in names:
+            plans[name] = design_softmax_b(name, *spec)
     if write:
         os.makedirs(PARAMS_DIR, exist_ok=True)
         with open(os.path.join(PARAMS_DIR, "plans_b.json"), "w") as fh:
@@ -386,8 +399,10 @@ if __name__ == "__main__":
     import sys
 
     if "--version-b" in sys.argv:
-        # Alg. 4 plans only (params/plans_b.json); the other parameter files stay as they are
-        for p in build_b(write=True).values():
+        # Alg. 4 plans only (params/plans_b.json); the other parameter files stay as they are.
+        # Further arguments name the plans to (re)design; the others are kept from the file.
+        names = [a for a in sys.argv[1:] if not a.startswith("--")] or None
+        for p in build_b(write=True, names=names).values():
             print(p["name"], "k=%d exp_err=%.3g" % (p["k"], p["exp"]["err"]),
                   [("%d" % it["deg"], "%.3g" % it["eps"], "%.3g" % it["delta"]) for it in p["iters"]])
         sys.exit(0)

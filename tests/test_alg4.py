@@ -93,3 +93,27 @@ def test_main_thread_fits_the_chain_without_bootstrapping(params):
     assert z_level - k >= 0                   # y^(k), the output
     assert z_level - (k - 1) - 1 >= bts       # (y^(k-1))^2, summed into S_k and bootstrapped
     assert z_level - (5 - 1) - 1 < bts        # k = 5 (Thm 3.3's k for M = 128, n = 256) would not fit
+
+
+@pytest.mark.skipif("toybts_n16_M32_B" not in plans_b, reason="params/plans_b.json not generated")
+def test_ciphertext_circuit_toy(params):
+    """Alg. 4 as a ciphertext circuit in the oracle (N = 2^12, m = 2 ciphertexts of 256 Softmax
+    of dimension 16 on [-32, 0], k = 4): within 2^-15 of FP64 Softmax, the outputs at the
+    bootstrapping input level (9 main-thread levels below the top), and only the auxiliary
+    thread bootstraps: two bootstrappings per iteration whatever m is."""
+    chains, _, evalmod = params
+    chain, em = chains["toybts"], evalmod["toybts"]
+    plan = plans_b["toybts_n16_M32_B"]
+    o = O.Oracle(chain)
+    o.keygen(11)
+    m, n, M = 2, plan["n"], plan["M"]
+    x = W.uniform_inputs(m * o.n0 // n, n, seed=5, M=M)
+    top = chain["user_top_level"]
+    slots = O.pack(x, m, o.n0)
+    cts = [o.encrypt(slots[i], top, (2 / M) * o.q[top], 21, i) for i in range(m)]
+    o.reset_counters()
+    outs = o.softmax_b(cts, plan, em)
+    assert [c.level for c in outs] == [chain["bts_min_level"]] * m
+    assert o.counters()["bts"] == 2 * plan["k"]
+    y = O.unpack(np.stack([o.decrypt(c).real for c in outs]), n)
+    assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
