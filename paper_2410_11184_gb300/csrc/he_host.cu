@@ -1966,7 +1966,6 @@ int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out) {
     c->st = (cudaStream_t)cuda_stream;
     for (int i = 0; i < p->n_q; i++) c->mods.push_back(p->q[i]);
     for (int i = 0; i < p->n_p; i++) c->mods.push_back(p->p[i]);
-    he_ctx *ctx = c;
     try {
         if (p->bootstrap) {
             REQUIRE(p->em_coeffs && p->em_deg >= 1, HE_EINVAL, "EvalMod coefficients missing");
@@ -1985,7 +1984,7 @@ int he_context_create(const he_params *p, void *cuda_stream, he_ctx **out) {
         CK(cudaGetSymbolAddress((void **)&c->noalloc_scratch, g_rescale_scratch));
     } catch (const HeErr &e) {
         fprintf(stderr, "he_context_create: %s\n", e.msg.c_str());
-        delete c;
+        he_context_destroy(c);   // frees whatever build_tables allocated before the failure
         return e.code;
     }
     *out = c;
