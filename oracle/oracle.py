@@ -367,7 +367,7 @@ class Oracle:
         Returns the m output ciphertexts y^(k)."""
         ch = self.chain
         m, n, M, k = len(cts), plan["n"], plan["M"], plan["k"]
-        top = ch["user_top_level"]
+        top, bts_min = ch["user_top_level"], ch["bts_min_level"]
         delta = 2.0 ** ch["log_scale"]
         boost = plan.get("bts_boost", 16.0)
         stride, nrot = m * self.n0 // n, int(round(math.log2(n // m)))
@@ -413,7 +413,9 @@ class Oracle:
             c = np.array(cheb(it["coeffs"])) * it["gain_s"] ** it["exponent"]
             dj = int(math.ceil(math.log2(len(c))))
             lp = top - dj
-            if lam_c is None:
+            if lam_c is None and lp < bts_min:
+                lam = self._split_eval(v, c, dj, bts, delta)
+            elif lam_c is None:
                 lam = self.poly_eval(v, c, lp, delta)
             else:
                 lam = self.poly_eval(v, c, lp, (delta * q[lp]) / lam_c.scale)
@@ -441,6 +443,34 @@ class Oracle:
                     z = self.hmult(z, z)
                 ys.append(z)
         return ys
+
+    def _split_eval(self, v, c, dj, bts, delta):
+        """p(u) = sum c_i T_i(u) of depth dj = bootstrapping input level + 1 below the top, as
+        A(u) + T_h(u) B(u) with h = 2^(dj-1) and A, B of degree < h (T_h T_j = (T_(h+j) +
+        T_(h-j)) / 2): A, B and T_(h/2) take dj - 1 levels each; T_(h/2) and B are bootstrapped,
+        T_h = 2 T_(h/2)^2 - 1, and the product T_h B joins A at the bootstrapping input level."""
+        q = [float(x) for x in self.q]
+        top = v.level
+        h, d = 1 << (dj - 1), len(c) - 1
+        a_c, b_c = c[:h].copy(), np.zeros(d - h + 1)
+        b_c[0] = c[h]
+        for j in range(1, d - h + 1):
+            b_c[j] = 2.0 * c[h + j]
+            a_c[h - j] -= c[h + j]
+        lo = top - (dj - 1)
+        e = np.zeros(h // 2 + 1)
+        e[-1] = 1.0
+        s_t = math.sqrt(2.0 * q[top] * delta)
+        t = bts(self.poly_eval(v, e, lo, delta), 1.0, s_t)
+        th = self.hmult(t, t)                                   # t^2 at 2 delta = 2 t^2 at delta
+        th = self.add_const(Ct(th.data, th.level, th.scale / 2.0), -1.0)
+        uu = np.cos(np.linspace(0.0, np.pi, 20001))
+        bmax = 1.1 * float(np.max(np.abs(cheb_eval(list(b_c), uu))))
+        bb = bts(self.poly_eval(v, b_c, lo, delta), 1.0 / bmax, q[top - 1] * bmax)
+        bb = Ct(bb.data, bb.level, bb.scale / bmax)             # B at scale q_(top-1)
+        prod = self.hmult(th, bb)
+        a = self.poly_eval(v, a_c, lo, prod.scale)
+        return self.add(Ct(prod.data[:, :lo + 1].copy(), lo, prod.scale), a)
 
     def counters(self):
         a = (C.c_long * 5)()

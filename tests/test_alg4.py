@@ -117,3 +117,33 @@ def test_ciphertext_circuit_toy(params):
     assert o.counters()["bts"] == 2 * plan["k"]
     y = O.unpack(np.stack([o.decrypt(c).real for c in outs]), n)
     assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
+
+
+@pytest.mark.skipif("toybts_n16_M32_B" not in plans_b, reason="params/plans_b.json not generated")
+def test_ciphertext_circuit_split_first_polynomial(params):
+    """A first polynomial one level deeper than the room above the bootstrapping input (degree
+    1023: a Chebyshev interpolant of the same v^(-1/2) on the same interval) is evaluated as
+    A + T_512 B with T_256 and B bootstrapped: same precision, two more bootstrappings."""
+    import copy
+
+    from paper_2410_11184_gb300 import design as D
+
+    chains, _, evalmod = params
+    chain, em = chains["toybts"], evalmod["toybts"]
+    plan = copy.deepcopy(plans_b["toybts_n16_M32_B"])
+    it = plan["iters"][0]
+    a, b = it["a"], it["b"]
+    c, _ = D.cheb_interp(lambda u: (0.5 * (b - a) * u + 0.5 * (a + b)) ** -0.5, 1023)
+    it["coeffs"] = D.hexlist(c)
+    o = O.Oracle(chain)
+    o.keygen(11)
+    m, n, M = 2, plan["n"], plan["M"]
+    x = W.uniform_inputs(m * o.n0 // n, n, seed=5, M=M)
+    top = chain["user_top_level"]
+    slots = O.pack(x, m, o.n0)
+    cts = [o.encrypt(slots[i], top, (2 / M) * o.q[top], 21, i) for i in range(m)]
+    o.reset_counters()
+    outs = o.softmax_b(cts, plan, em)
+    assert o.counters()["bts"] == 2 * plan["k"] + 2
+    y = O.unpack(np.stack([o.decrypt(c_).real for c_ in outs]), n)
+    assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
