@@ -358,9 +358,10 @@ class Oracle:
           for j = 1..k:
             S_j  = RotSum(relinearised sum_c y_c (x) y_c), y = y0 (j = 1) or y^(j-1)
             v    = Bootstrap(gain_s S_j) at scale (2/(b_j - a_j)) q_top; u = affine(v)
-            lam  = P_j(u) gain_s^(1/2^j) (the gain folded into the coefficients)
-            Lam  = lam (j = 1) or Lam * lam, bootstrapped with gain 1/Lmax_j (compact: one
-                   value per Softmax in slots [0, L))
+            lam  = P_j(u) gain_s^(1/2^j) (the gain folded into the coefficients), bootstrapped
+                   with a gain from its own range
+            Lam  = lam (j = 1) or Lam * lam (compact: one value per Softmax in slots [0, L);
+                   one level lower every iteration)
             lr   = RotSum(Lam (.) mask), mask = 1 on slots [0, L), encoded at the scale that
                    makes z land where the j squarings need it
             z_c  = lr * y0_c, y^(j)_c = z_c^(2^j) (j squarings)
@@ -413,16 +414,20 @@ class Oracle:
             c = np.array(cheb(it["coeffs"])) * it["gain_s"] ** it["exponent"]
             dj = int(math.ceil(math.log2(len(c))))
             lp = top - dj
-            if lam_c is None and lp < bts_min:
+            if lp < bts_min:
                 lam = self._split_eval(v, c, dj, bts, delta)
-            elif lam_c is None:
-                lam = self.poly_eval(v, c, lp, delta)
             else:
-                lam = self.poly_eval(v, c, lp, (delta * q[lp]) / lam_c.scale)
-                lam = self.hmult(lam_c, lam)
-            lmax = 1.1 * n ** -it["exponent"] * math.exp(A)
-            lam_c = bts(lam, 1.0 / lmax, delta)
-            lam_c = Ct(lam_c.data, lam_c.level, lam_c.scale * (1.0 / lmax))   # encrypts Lam / lmax at delta
+                lam = self.poly_eval(v, c, lp, delta)
+            # lambda_j alone is bootstrapped, with a gain from its own range: iteration 1 spans
+            # [n^-1/2, n^-1/2 e^A] (its bootstrapping error is removed by iteration 2, which
+            # normalises the vector this very ciphertext produced), later ones lie within
+            # [b_j^(-1/2^j), a_j^(-1/2^j)], narrow enough to keep the error that z^(2^j) amplifies
+            # small.  Lam = Lam * lambda_j then loses one level per iteration and stays compact.
+            lmax = 1.1 * (n ** -it["exponent"] * math.exp(A) if j == 1 else a ** -it["exponent"])
+            lam_lv = top if lam_c is None else lam_c.level
+            lb = bts(lam, 1.0 / lmax, q[lam_lv] * lmax)
+            lb = Ct(lb.data, lb.level, lb.scale / lmax)          # lambda_j at scale q[lam_lv]
+            lam_c = lb if lam_c is None else self.hmult(lam_c, lb)   # Lam keeps the scale q_top
             # where z lands and the scale it needs there: j squarings then (j < k) one more for S
             lz = ly0 - 1
             s = delta
