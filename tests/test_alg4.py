@@ -5,6 +5,7 @@ Alg. 4 prints lambda_j = (sum (y^(j-1))^2)^(-2^-(j-1)).  With that exponent iter
 sum y^(1) = 1 / S_1, not 1.  The reading lambda_j = S_j^(-1/2^j) normalises every round:
 lambda^(2^j) sum (y^(0))^(2^j) = 1, and y^(k) = Softmax(x) (Sec. 4.3)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -146,4 +147,28 @@ def test_ciphertext_circuit_split_first_polynomial(params):
     outs = o.softmax_b(cts, plan, em)
     assert o.counters()["bts"] == 2 * plan["k"] + 2
     y = O.unpack(np.stack([o.decrypt(c_).real for c_ in outs]), n)
+    assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("HE_RUN_SLOW") != "1" or "n256_M128_B" not in plans_b,
+                    reason="N = 2^16 oracle circuit: about 17 minutes on 8 cores (HE_RUN_SLOW=1)")
+def test_full_size_ciphertext_circuit(params):
+    """The N = 2^16 plan (k = 4, degree-1023 first polynomial evaluated split) on one ciphertext
+    of 128 Softmax of dimension 256 (attention logits): within 2^-15 of FP64 Softmax, output at
+    the bootstrapping input level, and ten bootstrappings, all of the auxiliary ciphertext."""
+    chains, _, evalmod = params
+    chain, em = chains["fgb16"], evalmod["fgb16"]
+    plan = plans_b["n256_M128_B"]
+    o = O.Oracle(chain)
+    o.keygen(11)
+    n, M = plan["n"], plan["M"]
+    x = W.attention_logits(o.n0 // n, n, seed=5)
+    top = chain["user_top_level"]
+    ct = o.encrypt(O.pack(x, 1, o.n0)[0], top, (2 / M) * o.q[top], 21, 0)
+    o.reset_counters()
+    out = o.softmax_b([ct], plan, em)[0]
+    assert out.level == chain["bts_min_level"]
+    assert o.counters()["bts"] == 2 * plan["k"] + 2
+    y = O.unpack(o.decrypt(out).real[None, :], n)
     assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
