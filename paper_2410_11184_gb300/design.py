@@ -322,6 +322,10 @@ def build_b(write=True, names=None):
     [e^-16, 1]: degree 1023 keeps delta_1 below 1 (0.85); degree 127 then suffices."""
     specs = {
         "n256_M128_B": ("fgb16", 256, 128.0, 4, 15, [1023, 127, 127, 127]),
+        # [-64, 0] (the LLaMa-shape workload's n = 128 and the serving plan's n = 256): A = 4,
+        # iteration 1's interval [e^-8, 1] needs degree 255 only (depth 8: no split)
+        "n128_M64_B": ("fgb16", 128, 64.0, 4, 15, [255, 127, 127, 127]),
+        "n256_M64_B": ("fgb16", 256, 64.0, 4, 15, [255, 127, 127, 127]),
         # the same level map at N = 2^12 (toybts: user levels 12 ... 4), for the oracle's
         # ciphertext circuit: A = 2 keeps every interval narrow enough for degree 63
         "toybts_n16_M32_B": ("toybts", 16, 32.0, 4, 15, [63, 63, 63, 63]),

@@ -62,17 +62,21 @@ def test_simulation_with_exact_polynomials_is_softmax(params):
 plans_b = O.load_plans_b()
 
 
-@pytest.mark.skipif("n256_M128_B" not in plans_b, reason="params/plans_b.json not generated")
-def test_designed_plan_precision():
-    """The stored n = 256, [-128, 0] plan (k = 4) against FP64 Softmax on the three input
-    models: at least 20 bits (the circuit then loses a few more to encryption noise)."""
-    plan = plans_b["n256_M128_B"]
+FULL_SIZE = sorted(k for k, p in plans_b.items() if p["chain"] == "fgb16")
+
+
+@pytest.mark.skipif(not FULL_SIZE, reason="params/plans_b.json not generated")
+@pytest.mark.parametrize("name", FULL_SIZE)
+def test_designed_plan_precision(name):
+    """Each stored N = 2^16 plan (k = 4) against FP64 Softmax on the three input models: at
+    least 20 bits (the circuit then loses a few more to encryption noise)."""
+    plan = plans_b[name]
     for it in plan["iters"]:
         assert it["delta"] < 1.0 and it["a"] < it["b"]
     assert plan["iters"][-1]["delta"] < 2.0 ** -20
-    M = plan["M"]
-    for x in (W.attention_logits(300, 256, seed=5), W.paper_normal_inputs(300, 256, 6, M),
-              W.uniform_inputs(300, 256, 7, M)):
+    n, M = plan["n"], plan["M"]
+    for x in (W.attention_logits(300, n, seed=5, M=M), W.paper_normal_inputs(300, n, 6, M),
+              W.uniform_inputs(300, n, 7, M)):
         y, sums = O.simulate_b(x, plan)
         assert -math.log2(np.abs(y - O.softmax_fp64(x)).max()) >= 20.0
         # every S_j lies in the interval its polynomial was designed for
@@ -81,12 +85,13 @@ def test_designed_plan_precision():
             assert v.min() >= it["a"] and v.max() <= it["b"]
 
 
-@pytest.mark.skipif("n256_M128_B" not in plans_b, reason="params/plans_b.json not generated")
-def test_main_thread_fits_the_chain_without_bootstrapping(params):
+@pytest.mark.skipif(not FULL_SIZE, reason="params/plans_b.json not generated")
+@pytest.mark.parametrize("name", FULL_SIZE)
+def test_main_thread_fits_the_chain_without_bootstrapping(params, name):
     """Main thread: exp (ceil(log2(deg + 1)) levels), z = lambda y0 (1), y^(j) = z^(2^j) (j).
     The output y^(k) needs a level >= 0; the last auxiliary input (y^(k-1))^2 is summed and
     bootstrapped, so it must stay at or above the level the bootstrapping starts from."""
-    plan = plans_b["n256_M128_B"]
+    plan = plans_b[name]
     ch = params[0][plan["chain"]]
     top, bts = ch["user_top_level"], ch["bts_min_level"]
     z_level = top - math.ceil(math.log2(plan["exp"]["deg"] + 1)) - 1
@@ -94,6 +99,10 @@ def test_main_thread_fits_the_chain_without_bootstrapping(params):
     assert z_level - k >= 0                   # y^(k), the output
     assert z_level - (k - 1) - 1 >= bts       # (y^(k-1))^2, summed into S_k and bootstrapped
     assert z_level - (5 - 1) - 1 < bts        # k = 5 (Thm 3.3's k for M = 128, n = 256) would not fit
+    # polynomials deeper than the room above the bootstrapping input are evaluated split
+    # (one level deeper at most)
+    for it in plan["iters"]:
+        assert math.ceil(math.log2(it["deg"] + 1)) <= (top - bts) + 1
 
 
 @pytest.mark.skipif("toybts_n16_M32_B" not in plans_b, reason="params/plans_b.json not generated")
