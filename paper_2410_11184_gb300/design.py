@@ -328,6 +328,9 @@ def build_b(write=True, names=None):
         "n256_M64_B": ("fgb16", 256, 64.0, 4, 15, [255, 127, 127, 127]),
         # n = 1024: S_j / n spans a ratio near 1000 after iteration 1, so degree 255 throughout
         "n1024_M64_B": ("fgb16", 1024, 64.0, 4, 15, [255, 255, 255, 255]),
+        # n = 4096 (which Alg. 2 cannot serve on this chain): degree 511 after iteration 1, whose
+        # depth 9 just fits above the bootstrapping input because each lambda_j is bootstrapped alone
+        "n4096_M64_B": ("fgb16", 4096, 64.0, 4, 15, [255, 511, 511, 511]),
         # the same level map at N = 2^12 (toybts: user levels 12 ... 4), for the oracle's
         # ciphertext circuit: A = 2 keeps every interval narrow enough for degree 63
         "toybts_n16_M32_B": ("toybts", 16, 32.0, 4, 15, [63, 63, 63, 63]),
