@@ -160,24 +160,27 @@ def test_ciphertext_circuit_split_first_polynomial(params):
 
 
 @pytest.mark.slow
-@pytest.mark.skipif(os.environ.get("HE_RUN_SLOW") != "1" or "n256_M128_B" not in plans_b,
+@pytest.mark.skipif(os.environ.get("HE_RUN_SLOW") != "1" or not FULL_SIZE,
                     reason="N = 2^16 oracle circuit: about 17 minutes on 8 cores (HE_RUN_SLOW=1)")
-def test_full_size_ciphertext_circuit(params):
-    """The N = 2^16 plan (k = 4, degree-1023 first polynomial evaluated split) on one ciphertext
-    of 128 Softmax of dimension 256 (attention logits): within 2^-15 of FP64 Softmax, output at
-    the bootstrapping input level, and ten bootstrappings, all of the auxiliary ciphertext."""
+@pytest.mark.parametrize("name", ["n256_M128_B", "n4096_M64_B"])
+def test_full_size_ciphertext_circuit(params, name):
+    """An N = 2^16 plan (k = 4) on one ciphertext of N0/n Softmax of dimension n (attention
+    logits): within 2^-15 of FP64 Softmax, output at the bootstrapping input level, and only
+    the auxiliary ciphertext bootstrapped (2 per iteration, 2 more for a split polynomial)."""
     chains, _, evalmod = params
     chain, em = chains["fgb16"], evalmod["fgb16"]
-    plan = plans_b["n256_M128_B"]
+    plan = plans_b[name]
     o = O.Oracle(chain)
     o.keygen(11)
     n, M = plan["n"], plan["M"]
-    x = W.attention_logits(o.n0 // n, n, seed=5)
+    room = chain["user_top_level"] - chain["bts_min_level"]
+    split = sum(math.ceil(math.log2(it["deg"] + 1)) > room for it in plan["iters"])
+    x = W.attention_logits(o.n0 // n, n, seed=5, M=M)
     top = chain["user_top_level"]
     ct = o.encrypt(O.pack(x, 1, o.n0)[0], top, (2 / M) * o.q[top], 21, 0)
     o.reset_counters()
     out = o.softmax_b([ct], plan, em)[0]
     assert out.level == chain["bts_min_level"]
-    assert o.counters()["bts"] == 2 * plan["k"] + 2
+    assert o.counters()["bts"] == 2 * plan["k"] + 2 * split
     y = O.unpack(o.decrypt(out).real[None, :], n)
     assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
