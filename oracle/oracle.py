@@ -83,6 +83,8 @@ def lib():
                                     C.c_double, u64p, dblp]
         L.orc_lintrans.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
                                    C.c_double, C.c_double, u64p, dblp]
+        L.orc_lintrans_unrescaled.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                              C.c_double, C.c_double, C.c_int, u64p, dblp]
         L.orc_bootstrap.argtypes = [C.c_void_p, intp, dblp, dblp, u64p, C.c_int, C.c_double, C.c_double,
                                     u64p, intp, dblp]
         L.orc_softmax.argtypes = [C.c_void_p, intp, dblp, dblp, dblp, intp, dblp, dblp, u64p, C.c_int,
@@ -293,6 +295,16 @@ class Oracle:
                                      gain, pt_scale, P(out), C.byref(so)))
         return Ct(out, a.level - 1, so.value)
 
+    def lintrans_unrescaled(self, a, nlev, inverse, which, gain, pt_scale, textbook=False):
+        """One linear-transform level without its final rescale (output at a.level): the giant
+        steps' key switches share one ModDown, or (textbook) each giant step is a complete
+        rotation with its own ModDown."""
+        out = np.zeros_like(a.data)
+        so = C.c_double()
+        self._chk(lib().orc_lintrans_unrescaled(self.ptr, P(a.data), a.level, a.scale, nlev, 1 if inverse else 0,
+                                                which, gain, pt_scale, 1 if textbook else 0, P(out), C.byref(so)))
+        return Ct(out, a.level, so.value)
+
     def bts_args(self, evalmod):
         ch = self.chain
         top = len(self.q) - 1
@@ -370,7 +382,7 @@ class Oracle:
         m, n, M, k = len(cts), plan["n"], plan["M"], plan["k"]
         top, bts_min = ch["user_top_level"], ch["bts_min_level"]
         delta = 2.0 ** ch["log_scale"]
-        boost = plan.get("bts_boost", 16.0)
+        boost = plan["bts_boost"]
         stride, nrot = m * self.n0 // n, int(round(math.log2(n // m)))
         q = [float(v) for v in self.q]
 
@@ -404,7 +416,6 @@ class Oracle:
             u = self.add_const(u, 1.0)
             y0.append(self.poly_eval(u, ec, ly0, math.sqrt(delta * q[ly0])))
         ys, lam_c = y0, None
-        A = M / 2.0 ** k
         for j, it in enumerate(plan["iters"][:k], start=1):
             S = square_sum(ys)
             a, b = it["a"], it["b"]
@@ -415,7 +426,7 @@ class Oracle:
             dj = int(math.ceil(math.log2(len(c))))
             lp = top - dj
             if lp < bts_min:
-                lam = self._split_eval(v, c, dj, bts, delta)
+                lam = self._split_eval(v, c, dj, bts, delta, it["b_max"])
             else:
                 lam = self.poly_eval(v, c, lp, delta)
             # lambda_j alone is bootstrapped, with a gain from its own range: iteration 1 spans
@@ -423,7 +434,9 @@ class Oracle:
             # normalises the vector this very ciphertext produced), later ones lie within
             # [b_j^(-1/2^j), a_j^(-1/2^j)], narrow enough to keep the error that z^(2^j) amplifies
             # small.  Lam = Lam * lambda_j then loses one level per iteration and stays compact.
-            lmax = 1.1 * (n ** -it["exponent"] * math.exp(A) if j == 1 else a ** -it["exponent"])
+            # The plan holds that bound with a 10 % margin: lam_max = 1.1 n^(-1/2) e^A (j = 1),
+            # 1.1 a_j^(-1/2^j) after that.
+            lmax = it["lam_max"]
             lam_lv = top if lam_c is None else lam_c.level
             lb = bts(lam, 1.0 / lmax, q[lam_lv] * lmax)
             lb = Ct(lb.data, lb.level, lb.scale / lmax)          # lambda_j at scale q[lam_lv]
@@ -449,11 +462,13 @@ class Oracle:
                 ys.append(z)
         return ys
 
-    def _split_eval(self, v, c, dj, bts, delta):
+    def _split_eval(self, v, c, dj, bts, delta, bmax):
         """p(u) = sum c_i T_i(u) of depth dj = bootstrapping input level + 1 below the top, as
         A(u) + T_h(u) B(u) with h = 2^(dj-1) and A, B of degree < h (T_h T_j = (T_(h+j) +
         T_(h-j)) / 2): A, B and T_(h/2) take dj - 1 levels each; T_(h/2) and B are bootstrapped,
-        T_h = 2 T_(h/2)^2 - 1, and the product T_h B joins A at the bootstrapping input level."""
+        T_h = 2 T_(h/2)^2 - 1, and the product T_h B joins A at the bootstrapping input level.
+        bmax (from the plan) bounds |B| on [-1, 1] with a 10 % margin: B is bootstrapped with
+        gain 1 / bmax."""
         q = [float(x) for x in self.q]
         top = v.level
         h, d = 1 << (dj - 1), len(c) - 1
@@ -469,8 +484,6 @@ class Oracle:
         t = bts(self.poly_eval(v, e, lo, delta), 1.0, s_t)
         th = self.hmult(t, t)                                   # t^2 at 2 delta = 2 t^2 at delta
         th = self.add_const(Ct(th.data, th.level, th.scale / 2.0), -1.0)
-        uu = np.cos(np.linspace(0.0, np.pi, 20001))
-        bmax = 1.1 * float(np.max(np.abs(cheb_eval(list(b_c), uu))))
         bb = bts(self.poly_eval(v, b_c, lo, delta), 1.0 / bmax, q[top - 1] * bmax)
         bb = Ct(bb.data, bb.level, bb.scale / bmax)             # B at scale q_(top-1)
         prod = self.hmult(th, bb)

@@ -291,6 +291,21 @@ int orc_lintrans(orc_ctx *c, const uint64_t *a, int level, double scale, int nle
     return 0;
 }
 
+/* one linear-transform level without its final rescale: textbook = 0 as lt_eval_level (giant
+ * steps share one ModDown), 1 in the textbook form (one ModDown per giant step); out at `level` */
+int orc_lintrans_unrescaled(orc_ctx *c, const uint64_t *a, int level, double scale, int nlev, int inverse, int which,
+                            double gain, double pt_scale, int textbook, uint64_t *out, double *sout) {
+    orc_lt_level lv[16];
+    lt_levels(c, nlev, inverse, lv);
+    orc_ct x = wrap(c, a, level, scale);
+    cplx g; g.re = gain; g.im = 0.0;
+    int rc = textbook ? lt_eval_level_textbook(c, &x, &lv[which], g, pt_scale)
+                      : lt_eval_level_ex(c, &x, &lv[which], g, pt_scale, 0);
+    if (rc) { ct_free(&x); return rc; }
+    unwrap(c, &x, out, NULL, sout);
+    return 0;
+}
+
 static void fill_bts(orc_bts *b, const int *bi, const double *bd, const double *em_c) {
     b->stc_levels = bi[0];
     b->cts_levels = bi[1];

@@ -128,7 +128,7 @@ static int diag_nonzero(const cplx *d, int n0) {
     return 0;
 }
 
-int lt_eval_level(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale) {
+int lt_eval_level_ex(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale, int do_rescale) {
     int n0 = c->n0, E, hmin;
     cplx *diag = lt_diagonals(c, lv, gain, &E, &hmin);
     int g = bsgs_g(lv->nstage);
@@ -215,7 +215,71 @@ int lt_eval_level(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, doub
     free(diag);
     ct_free(x);
     *x = acc;
-    return rescale(c, x);
+    return do_rescale ? rescale(c, x) : 0;
+}
+
+int lt_eval_level(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale) {
+    return lt_eval_level_ex(c, x, lv, gain, pt_scale, 1);
+}
+
+/* The same level in the textbook baby-step/giant-step form, for tests of the shared ModDown:
+ * every giant step is a complete rotation (its own key switch and ModDown) added to the sum,
+ * and the sum is not rescaled.  Its result differs from lt_eval_level_ex's (unrescaled) only by
+ * the rounding of the ModDowns: under decryption by at most (giant steps) (1 + h)(alpha + 1)/2
+ * per coefficient. */
+int lt_eval_level_textbook(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale) {
+    int n0 = c->n0, E, hmin;
+    cplx *diag = lt_diagonals(c, lv, gain, &E, &hmin);
+    int g = bsgs_g(lv->nstage);
+    int level = x->level;
+    orc_ct acc = ct_alloc(c, level);
+    acc.scale = x->scale * pt_scale;
+    uint64_t *pt = malloc(sizeof(uint64_t) * (size_t)(level + 1) * c->n);
+    cplx *rd = malloc(sizeof(cplx) * n0);
+    int rc = 0;
+    for (int a = floordiv(-E, g); a <= floordiv(E, g) && !rc; a++) {
+        orc_ct inner = ct_alloc(c, level);
+        inner.scale = acc.scale;
+        int have_inner = 0;
+        for (int b = 0; b < g && !rc; b++) {
+            int e = a * g + b;
+            if (e < -E || e > E) continue;
+            const cplx *dv = diag + (size_t)(e + E) * n0;
+            if (!diag_nonzero(dv, n0)) continue;
+            long sh = (long)a * g * hmin;
+            for (int i = 0; i < n0; i++) rd[i] = dv[(((i - sh) % n0) + n0) % n0];
+            encode(c, rd, pt_scale, level, pt);
+            orc_ct r;
+            if (b == 0) r = ct_copy(c, x);
+            else rc = rotate(c, x, galois_for_rot(c, (long)b * hmin), &r);
+            if (rc) break;
+            ct_mul_plain(c, &r, pt, level);
+            r.scale = acc.scale;
+            ct_add(c, &inner, &r);
+            ct_free(&r);
+            have_inner = 1;
+        }
+        if (have_inner && !rc) {
+            if (a == 0) {
+                ct_add(c, &acc, &inner);
+            } else {
+                orc_ct r;
+                rc = rotate(c, &inner, galois_for_rot(c, (long)a * g * hmin), &r);
+                if (!rc) {
+                    r.scale = acc.scale;
+                    ct_add(c, &acc, &r);
+                    ct_free(&r);
+                }
+            }
+        }
+        ct_free(&inner);
+    }
+    free(pt);
+    free(rd);
+    free(diag);
+    ct_free(x);
+    *x = acc;
+    return rc;
 }
 
 int lt_rotations(const orc_ctx *c, const orc_lt_level *lv, int *gal, int max) {

@@ -149,6 +149,8 @@ typedef struct {
 } orc_lt_level;
 int lt_levels(const orc_ctx *c, int nlev, int inverse, orc_lt_level *out);
 int lt_eval_level(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale);
+int lt_eval_level_ex(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale, int do_rescale);
+int lt_eval_level_textbook(orc_ctx *c, orc_ct *x, const orc_lt_level *lv, cplx gain, double pt_scale);
 int lt_rotations(const orc_ctx *c, const orc_lt_level *lv, int *gal, int max);
 
 /* poly.c */

@@ -314,6 +314,45 @@ def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
             "iters": iters}
 
 
+def cheb_eval_rec(c, u):
+    """sum_k c_k T_k(u) by the three-term recurrence (FP64)."""
+    t0, t1 = np.ones_like(u), u
+    acc = c[0] * t0
+    if len(c) > 1:
+        acc = acc + c[1] * t1
+    for ck in c[2:]:
+        t0, t1 = t1, 2.0 * u * t1 - t0
+        acc = acc + ck * t1
+    return acc
+
+
+def bts_gains_b(plan, chain):
+    """Bootstrapping gains of Alg. 4's auxiliary thread, stored in the plan so that every
+    evaluator reads the same numbers: lam_max_j bounds lambda_j on its interval with a 10 %
+    margin (iteration 1: n^(-1/2) e^A, the top of [n^-1/2, n^-1/2 e^A]; later ones a_j^(-1/2^j),
+    the top of [b_j^(-1/2^j), a_j^(-1/2^j)]); b_max_j bounds the upper half B of a polynomial
+    that is too deep to end above the bootstrapping input level and is evaluated split as
+    A + T_h B (0 where no split is needed), on a grid of 20001 Chebyshev-spaced points."""
+    n, A = plan["n"], plan["A"]
+    top, bts_min = chain["user_top_level"], chain["bts_min_level"]
+    plan["bts_boost"] = 16.0   # the input gain inside every bootstrapping (as for Alg. 2)
+    uu = np.cos(np.linspace(0.0, np.pi, 20001))
+    for j, it in enumerate(plan["iters"], start=1):
+        e = it["exponent"]
+        it["lam_max"] = 1.1 * (n ** -e * math.exp(A) if j == 1 else it["a"] ** -e)
+        c = np.array([float.fromhex(h) for h in it["coeffs"]]) * it["gain_s"] ** e
+        dj = int(math.ceil(math.log2(len(c))))
+        it["b_max"] = 0.0
+        if top - dj < bts_min:
+            h, d = 1 << (dj - 1), len(c) - 1
+            b_c = np.zeros(d - h + 1)
+            b_c[0] = c[h]
+            for i in range(1, d - h + 1):
+                b_c[i] = 2.0 * c[h + i]
+            it["b_max"] = 1.1 * float(np.max(np.abs(cheb_eval_rec(list(b_c), uu))))
+    return plan
+
+
 def build_b(write=True, names=None):
     """Alg. 4 plans (params/plans_b.json).  n = 256 on [-128, 0] with k = 4: the main thread
     uses ceil(log2 16) = 4 levels for exp, 1 for z = lambda y0 and k for z^(2^k), 9 in all,
@@ -343,6 +382,9 @@ def build_b(write=True, names=None):
     for name, spec in specs.items():
         if names is None or name in names:
             plans[name] = design_softmax_b(name, *spec)
+    chains = load_params()[0]
+    for p in plans.values():
+        bts_gains_b(p, chains[p["chain"]])
     if write:
         os.makedirs(PARAMS_DIR, exist_ok=True)
         with open(os.path.join(PARAMS_DIR, "plans_b.json"), "w") as fh:
@@ -411,6 +453,8 @@ if __name__ == "__main__":
         # Alg. 4 plans only (params/plans_b.json); the other parameter files stay as they are.
         # Further arguments name the plans to (re)design; the others are kept from the file.
         names = [a for a in sys.argv[1:] if not a.startswith("--")] or None
+        if "--gains-only" in sys.argv:
+            names = []   # keep every polynomial, recompute only the bootstrapping gains
         for p in build_b(write=True, names=names).values():
             print(p["name"], "k=%d exp_err=%.3g" % (p["k"], p["exp"]["err"]),
                   [("%d" % it["deg"], "%.3g" % it["eps"], "%.3g" % it["delta"]) for it in p["iters"]])

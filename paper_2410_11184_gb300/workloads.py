@@ -33,5 +33,10 @@ def attention_logits(L, n, seed, M=128.0, d=64, bound=8.0, sigma=None, rows_per_
         s = np.repeat(rng.uniform(0.5, 1.5, (heads, 1)), rows_per_head, axis=0)[:L]
     q = rng.standard_normal((L, 1, d)) * s[:, :, None]
     k = rng.standard_normal((L, n, d)) * s[:, :, None]
-    logits = np.einsum("lid,ljd->lj", q, k) / np.sqrt(d)
+    # q.k summed over the head dimension in a fixed order (elementwise products and additions,
+    # no BLAS), so that the same seed gives the same bits on every host
+    dot = np.zeros((L, n))
+    for t in range(d):
+        dot += q[:, :, t] * k[:, :, t]
+    logits = dot / np.sqrt(d)
     return np.clip(logits - bound, -M, 0.0)

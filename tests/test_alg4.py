@@ -5,6 +5,7 @@ Alg. 4 prints lambda_j = (sum (y^(j-1))^2)^(-2^-(j-1)).  With that exponent iter
 sum y^(1) = 1 / S_1, not 1.  The reading lambda_j = S_j^(-1/2^j) normalises every round:
 lambda^(2^j) sum (y^(0))^(2^j) = 1, and y^(k) = Softmax(x) (Sec. 4.3)."""
 import math
+import time
 import os
 
 import numpy as np
@@ -145,6 +146,8 @@ def test_ciphertext_circuit_split_first_polynomial(params):
     a, b = it["a"], it["b"]
     c, _ = D.cheb_interp(lambda u: (0.5 * (b - a) * u + 0.5 * (a + b)) ** -0.5, 1023)
     it["coeffs"] = D.hexlist(c)
+    D.bts_gains_b(plan, chain)   # the split's B now needs a bootstrapping gain
+    assert it["b_max"] > 0
     o = O.Oracle(chain)
     o.keygen(11)
     m, n, M = 2, plan["n"], plan["M"]
@@ -179,8 +182,15 @@ def test_full_size_ciphertext_circuit(params, name):
     top = chain["user_top_level"]
     ct = o.encrypt(O.pack(x, 1, o.n0)[0], top, (2 / M) * o.q[top], 21, 0)
     o.reset_counters()
+    t0 = time.time()
     out = o.softmax_b([ct], plan, em)[0]
+    dt = time.time() - t0
     assert out.level == chain["bts_min_level"]
-    assert o.counters()["bts"] == 2 * plan["k"] + 2 * split
+    nbts = o.counters()["bts"]
+    assert nbts == 2 * plan["k"] + 2 * split
     y = O.unpack(o.decrypt(out).real[None, :], n)
-    assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
+    bits = -math.log2(np.abs(y - O.softmax_fp64(x)).max())
+    print("%s: %.2f bits against FP64 Softmax, %d bootstrappings, %.0f s on %d host threads"
+          % (name, bits, nbts, dt, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))))
+    # measured on this seed: 18.8 bits (n = 256) and 19.7 bits (n = 4096); half a bit of margin
+    assert bits > {"n256_M128_B": 18.3, "n4096_M64_B": 19.2}[name]

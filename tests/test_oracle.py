@@ -339,6 +339,46 @@ def test_stc_places_slots_in_coefficients(toybts_oracle):
     assert np.abs(m[o.n0:]).max() < 2 ** -24
 
 
+@pytest.mark.parametrize("inverse,which,level", [(False, 0, 3), (True, 1, 23)])
+def test_shared_giant_step_moddown(toybts_oracle, inverse, which, level):
+    """A linear-transform level whose giant-step rotations share one ModDown (their key-switch
+    inner products summed over Q_l u P and divided by P once) against the textbook evaluation of
+    the same level (every giant step a complete rotation with its own ModDown), both before the
+    level's rescale.  Under exact decryption (c0 + c1 s per limb) the two differ only by the
+    ModDowns' rounding: the same small integer on every limb, at most
+    (giant steps) (1 + h)(alpha + 1)/2 in size.  A dropped key-switch term, a wrong sign or a
+    wrong Galois element would put a residue of size ~q in the difference."""
+    o = toybts_oracle
+    rng = np.random.default_rng(12 + level)
+    a = o.encrypt(rng.uniform(-1, 1, o.n0) + 1j * rng.uniform(-1, 1, o.n0), level, 2.0 ** 42, 13)
+    pt_scale = float(o.q[level])
+    shared = o.lintrans_unrescaled(a, 3, inverse, which, 1.0, pt_scale)
+    text = o.lintrans_unrescaled(a, 3, inverse, which, 1.0, pt_scale, textbook=True)
+    assert shared.scale == text.scale
+    s = o.secret().astype(np.int64)
+    deltas = []
+    for t in range(level + 1):
+        q = o.q[t]
+        st = np.mod(s, q).astype(np.uint64)
+        dec = []
+        for ct in (shared, text):
+            c0, c1 = ct.data[0, t].astype(object), o.polymul(t, ct.data[1, t], st).astype(object)
+            dec.append((c0 + c1) % q)
+        d = (dec[0] - dec[1]) % q
+        deltas.append(np.where(d > q // 2, d - q, d).astype(np.int64))
+    for t in range(1, level + 1):
+        assert np.array_equal(deltas[t], deltas[0]), t    # one small integer polynomial
+    # the 11 stages at N = 2^12 form levels of 4, 4, 3 stages (SlotToCoeff) and 3, 4, 4
+    # (CoeffToSlot); both levels tested have r = 4 stages and several non-zero giant steps
+    r = 4
+    E, g = (1 << r) - 1, 1 << ((r + 2) // 2)
+    giants = E // g + (E + g - 1) // g + 1
+    bound = giants * (1 + o.chain["h"]) * (o.chain["alpha"] + 1) / 2
+    assert 0 < np.abs(deltas[0]).max() <= bound, (np.abs(deltas[0]).max(), bound)
+    # the shared form and the rescaling entry point agree after the rescale
+    assert np.array_equal(o.rescale(shared).data, o.lintrans(a, 3, inverse, which, 1.0, pt_scale).data)
+
+
 def test_bootstrap_precision(toybts_oracle, params):
     o = toybts_oracle
     em = params[2]["toybts"]
