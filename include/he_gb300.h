@@ -55,7 +55,12 @@ typedef struct {
     const double *em_coeffs;   /* em_deg + 1 coefficients */
 } he_params;
 
-/* Softmax circuit parameters (Alg. 2 / Alg. 3; Sec. 5.1.2 for the polynomials). */
+#define HE_SOFTMAX_ALG2 0   /* Alg. 2 with the auxiliary thread of Alg. 3 (Sec. 4.2) */
+#define HE_SOFTMAX_ALG4 1   /* Alg. 4, version B (Sec. 4.3), with the auxiliary thread of Alg. 3 */
+
+/* Softmax circuit parameters (Alg. 2 / Alg. 3 / Alg. 4; Sec. 5.1.2 for the polynomials).  All
+ * arrays are host memory of k entries (inv_coeffs: the k coefficient lists back to back), read
+ * during the call only. */
 typedef struct {
     int n;                     /* Softmax dimension (power of two dividing N/2) */
     int k;                     /* normalize-and-square rounds */
@@ -63,10 +68,18 @@ typedef struct {
     int exp_deg;
     const double *exp_coeffs;  /* exp(x/2^k) in the Chebyshev basis of u = 2x/M + 1 */
     const int *inv_deg;        /* k degrees */
-    const double *inv_coeffs;  /* concatenated Chebyshev coefficients of x^{-1/2} per round */
+    const double *inv_coeffs;  /* round j: Chebyshev coefficients of v^{-1/2} (Alg. 2) or of
+                                  v^{-exponent_j} (Alg. 4) on [inv_a_j, inv_b_j], mapped to [-1, 1] */
     const double *inv_a, *inv_b;     /* interval of round j */
-    const double *gain_s, *gain_l;   /* input gain of round j, bootstrapping gain of lambda_j */
+    const double *gain_s, *gain_l;   /* input gain of round j; bootstrapping gain of lambda_j
+                                        (Alg. 2 only: gain_l may be NULL for Alg. 4) */
     double bts_boost;          /* input gain applied inside every bootstrapping */
+    int method;                /* HE_SOFTMAX_ALG2 or HE_SOFTMAX_ALG4 (HE_EINVAL otherwise) */
+    /* Alg. 4 only (NULL for Alg. 2): lambda_j = S_j^(-exponent_j), exponent_j = 2^-j; lambda_j is
+     * bootstrapped with gain 1/lam_max_j; b_max_j > 0 bounds the upper half B of a round-j
+     * polynomial too deep to end above the bootstrapping input level, which is then evaluated
+     * as A + T_h B (0: no split). */
+    const double *exponent, *lam_max, *b_max;
 } he_softmax_plan;
 
 typedef struct {
@@ -90,7 +103,10 @@ int he_params_insecure(const he_params *p);
 
 /* KeyGen (Sec. 2.2): secret, public key, relinearisation and conjugation keys, rotation keys
  * for the n_rot slot rotations in rot_steps, and (if bootstrapping) every rotation key that
- * SlotToCoeff / CoeffToSlot need.  Randomness: counter-based SplitMix64 keyed by seed. */
+ * SlotToCoeff / CoeffToSlot need.  Randomness: counter-based SplitMix64 keyed by seed.
+ * Calling it again replaces the secret: every evaluation key of the previous secret is freed
+ * (he_keygen_softmax must be called again) and every graph captured by he_softmax_graph is
+ * dropped, so ciphertexts of the old secret no longer decrypt. */
 int he_keygen(he_ctx *ctx, uint64_t seed, const int *rot_steps, int n_rot);
 /* Rotation keys a Softmax of dimension n over m ciphertexts needs (strides L 2^i, Alg. 3). */
 int he_keygen_softmax(he_ctx *ctx, int n, int m);
@@ -107,10 +123,13 @@ int he_decrypt_slots(he_ctx *ctx, const he_ct *cts, int ct, double *slots);
 int he_encrypt_slots(he_ctx *ctx, const double *slots, int level, double scale, uint64_t seed, int ct_index,
                      he_ct *out, int ct);
 
-/* Softmax (Alg. 2 with Alg. 3, many-ciphertext form of Sec. 4.2) on the m = cts->n_ct
- * ciphertexts, in place: the output level is lower, data is overwritten, level/scale updated.
- * batched = 1: every operation runs over all m ciphertexts in one launch (key read once);
- * batched = 0: the same operation list, one ciphertext at a time. */
+/* Softmax (Alg. 2 with Alg. 3, or Alg. 4 with Alg. 3, as plan->method says; many-ciphertext
+ * form of Sec. 4.2) on the m = cts->n_ct ciphertexts, in place: the output level is lower, data
+ * is overwritten, level/scale updated.  batched = 1: every operation runs over all m ciphertexts
+ * in one launch (key read once); batched = 0: the same operation list, one ciphertext at a time.
+ * Alg. 4 bootstraps only the auxiliary ciphertext (2 per round, 2 more per split polynomial);
+ * it needs a bootstrapping context (HE_EINVAL otherwise).  HE_EINVAL for a NULL plan array the
+ * method reads, n not a power of two dividing N/2, or m not dividing n. */
 int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched);
 /* groups independent Softmax batches in one batched pass: the n_ct ciphertexts are groups
  * consecutive groups of m = n_ct / groups ciphertexts, each packed as in Sec. 4.2 (its own
@@ -163,15 +182,17 @@ int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out);
  * callers that cannot allocate once they are running: a server that reserved its whole HBM
  * budget at start-up and admits work against it, or a host program whose memory pool is
  * fixed and must not grow on the request path).  The caller passes the input batch a and an
- * output buffer out->data of n_ct * 2 * level * N words that must not alias a->data; level,
- * scale and n_ct of *out are written.  Results equal he_rescale's bit for bit.
+ * output buffer out->data of n_ct * 2 * level * N words whose bytes must not overlap a's
+ * n_ct * 2 * (level+1) * N words at all (HE_EINVAL otherwise); level, scale and n_ct of *out
+ * are written.  Results equal he_rescale's bit for bit.
  * Scratch: a fixed device array of 2^21 words (16 MiB) compiled into the library, held by
  * every device that loads it until the process exits; its device address is looked up once
  * per context, at he_context_create, with the context's device current.  Inputs needing more
  * than 2 n_ct (level+1) N = 2^21 words are rejected with HE_EINVAL before any launch.  Every
  * call shares that one array and leaves its contents behind: calls whose executions overlap
  * on the GPU (several streams, or several contexts on one device) race on it, so serialise
- * them.  Errors as he_rescale. */
+ * them.  Errors: HE_EINVAL for a NULL pointer, n_ct < 1, a level outside [0, n_q), an
+ * overlap of out with a or a size beyond the scratch; HE_ELEVEL at level 0. */
 int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out);
 /* Mult (Sec. 2.2, Functionalities): tensor product, relinearisation with the hybrid key
  * switch, and rescale (relinearisation and rescale as one division by P q_level), out at
@@ -223,7 +244,11 @@ int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes
  * synchronises and writes one text line "family launches total_ms bytes" (bytes: the
  * algorithmic bytes of those launches, 0 where not stated) per kernel family (ntt,
  * modup, ks_inner, moddown, tensor, rescale, lintrans, elementwise, automorph, modraise, encode, decode,
- * keygen, copy) into buf (len bytes, NUL-terminated), then resets.  HE_EINVAL if buf is too small. */
+ * keygen, copy) into buf (len bytes, NUL-terminated), then one line "phase:P launches total_ms 0"
+ * per phase of the Softmax circuit the launches belonged to (main: the m main-thread ciphertexts;
+ * aux: the auxiliary thread of Alg. 3 outside bootstrapping; bootstrap: every bootstrapping;
+ * other: launches outside a Softmax), then resets.  HE_EINVAL if buf is too small.  The phases are
+ * also NVTX ranges of the same names. */
 int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len);
 /* bounded device wait self test: a kernel polls a flag nobody sets for at most max_iter polls
  * and returns HE_ETIMEOUT; the context stays usable. */

@@ -15,6 +15,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "he_kernels.cuh"
 #include "../../include/he_gb300.h"
 
@@ -140,7 +142,9 @@ struct he_ctx {
     std::string prof_name;   // a family name, or "all"
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     std::vector<const char *> prof_fam;   // family of each recorded launch
+    std::vector<const char *> prof_ph;    // circuit phase of each recorded launch
     std::vector<double> prof_b;           // its algorithmic bytes
+    const char *phase = "other";          // circuit phase of the launches being issued (PhaseScope)
     size_t prof_used = 0;
     double prof_bytes = 0;
 };
@@ -172,10 +176,12 @@ struct ProfScope {
             cudaEventCreate(&b);
             c->prof_ev.push_back({a, b});
             c->prof_fam.push_back(nullptr);
+            c->prof_ph.push_back(nullptr);
             c->prof_b.push_back(0);
         }
         slot = c->prof_used++;
         c->prof_fam[slot] = name;
+        c->prof_ph[slot] = c->phase;
         c->prof_b[slot] = bytes;
         c->prof_bytes += bytes;
         cudaEventRecord(c->prof_ev[slot].first, c->st);
@@ -194,10 +200,30 @@ struct ProfScope {
     }
 };
 
+// Marks the launches issued in its lifetime as one phase of the Softmax circuit (main thread,
+// auxiliary thread, bootstrapping): an NVTX range for profilers, and the phase recorded with
+// every launch timed by ProfScope (he_profile_breakdown sums per phase).  Nested scopes take
+// over and hand back.
+struct PhaseScope {
+    struct he_ctx *c;
+    const char *prev;
+    PhaseScope(struct he_ctx *c_, const char *name);
+    ~PhaseScope();
+};
+
 struct HeErr {
     int code;
     std::string msg;
 };
+
+PhaseScope::PhaseScope(he_ctx *c_, const char *name) : c(c_), prev(c_->phase) {
+    c->phase = name;
+    nvtxRangePushA(name);
+}
+PhaseScope::~PhaseScope() {
+    nvtxRangePop();
+    c->phase = prev;
+}
 
 #define CK(call)                                                                                     \
     do {                                                                                             \
@@ -1440,6 +1466,7 @@ static std::vector<int> lt_rotation_steps(he_ctx *c, const LtDesc &lv) {
 
 // ------------------------------------------------------------------------- bootstrapping
 static DCt bootstrap(he_ctx *c, const DCt &x, double gain, double out_scale) {
+    PhaseScope ph(c, "bootstrap");
     REQUIRE(c->bootstrap, HE_EINVAL, "bootstrapping not enabled");
     REQUIRE(x.level >= c->stc_levels, HE_ELEVEL, "bootstrap: level too low");
     DCt y = ct_drop(c, x, c->stc_levels);
@@ -1478,12 +1505,13 @@ static DCt bootstrap(he_ctx *c, const DCt &x, double gain, double out_scale) {
 
 // ------------------------------------------------------------------------- Softmax circuit
 struct Plan {
-    int n, k, exp_deg;
+    int n, k, exp_deg, method = 0;   // method 0: Alg. 2 + Alg. 3; 1: Alg. 4 (version B)
     double M, boost;
     std::vector<double> exp_c;
     std::vector<int> inv_deg;
     std::vector<std::vector<double>> inv_c;
     std::vector<double> a, b, gs, gl;
+    std::vector<double> expo, lam_max, b_max;   // Alg. 4 only
 };
 
 static double qd(he_ctx *c, int l) { return (double)c->mods[l]; }
@@ -1544,6 +1572,68 @@ static void dbg_dump(he_ctx *c, const char *what, int j, const DCt &x) {
     fclose(f);
 }
 
+// S = Relin(sum_c y_c (x) y_c), relinearised and rescaled (one sum per group): ys holds the m
+// main-thread ciphertexts as one batch (or m batches of one); with G > 1 ys[0] holds G groups
+static DCt square_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
+    int ly = ys[0].level;
+    int L = ly + 1;
+    DPtr d = dalloc(c, (size_t)G * 3 * L * c->N);
+    PhaseScope ph(c, "main");   // per-ciphertext tensors and their sum
+    bool first = true;
+    if (G > 1) {
+        const DCt &y = ys[0];
+        long t3 = 3L * L * c->N;
+        DPtr dd = m > 1 ? dalloc(c, (size_t)y.nct * t3) : DPtr();
+        tensor_into(c, m > 1 ? dd.get() : d.get(), y, y, ly, false);
+        // group g: d[g] = sum_i dd[g m + i] (3 polynomials of L limbs each)
+        for (int g = 0; m > 1 && g < G; g++) {
+            for (int i = 1; i < m; i++) {
+                const uint64_t *acc = i == 1 ? dd.get() + (long)g * m * t3 : d.get() + g * t3;
+                {
+                    ProfScope ps_(c, "elementwise", 0);
+                    k_add<<<grid_for(c, t3), 256, 0, c->st>>>(d.get() + g * t3, (long)L * c->N, acc, (long)L * c->N,
+                                                               dd.get() + ((long)g * m + i) * t3, (long)L * c->N,
+                                                               3 * L, L, qmap(L), c->d_mods, c->logN, 0);
+                }
+                LAUNCH_CHECK();
+            }
+        }
+        first = false;
+    }
+    for (auto &y : ys) {
+        if (G > 1) break;
+        if (y.nct == 1) {
+            tensor_into(c, d.get(), y, y, ly, !first);
+            first = false;
+        } else {
+            // sum of the per-ciphertext tensors of the batch
+            DPtr dd = dalloc(c, (size_t)y.nct * 3 * L * c->N);
+            tensor_into(c, dd.get(), y, y, ly, false);
+            for (int i = 0; i < y.nct; i++) {
+                int cnt = 3 * L;
+                long tot = (long)cnt << c->logN;
+                if (first && i == 0)
+                    {
+                        ProfScope ps_(c, "copy", 0);
+                        CK(cudaMemcpyAsync(d.get(), dd.get(), (size_t)3 * L * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
+                    }
+                else {
+                    ProfScope ps_(c, "elementwise", 0);
+                    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), (long)L * c->N, d.get(), (long)L * c->N,
+                                                                dd.get() + (long)i * 3 * L * c->N, (long)L * c->N,
+                                                                cnt, L, qmap(L), c->d_mods, c->logN, 0);
+                }
+                LAUNCH_CHECK();
+            }
+            first = false;
+        }
+    }
+    PhaseScope pa(c, "aux");    // one relinearisation of the sum
+    DCt S = relin_rescale(c, d.get(), ly, G, ys[0].scale * ys[0].scale);
+    c->cnt[2]++;
+    return S;
+}
+
 // ys: the m main-thread ciphertexts, as one batch (batched) or m batches of one; with G > 1
 // (batched only) ys[0] holds G independent groups of m ciphertexts each (G m ciphertexts): the
 // sum of squares stays inside each group and the auxiliary thread runs over a batch of G
@@ -1554,10 +1644,13 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
     int nrot = ilog2c(n / m);
     int ut = c->user_top;
     double delta = std::ldexp(1.0, c->log_scale);
-    for (auto &y : ys) {
-        affine_to_unit(c, y, -p.M, 0.0);
-        int lvl = y.level - ilog2c(p.exp_deg + 1);
-        y = poly_eval(c, y, p.exp_c, lvl, y_target(c, p, 0, lvl));
+    {
+        PhaseScope ph(c, "main");
+        for (auto &y : ys) {
+            affine_to_unit(c, y, -p.M, 0.0);
+            int lvl = y.level - ilog2c(p.exp_deg + 1);
+            y = poly_eval(c, y, p.exp_c, lvl, y_target(c, p, 0, lvl));
+        }
     }
     dbg_dump(c, "y0", 0, ys[0]);
     for (int j = 0; j < p.k; j++) {
@@ -1568,60 +1661,8 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
             ly = ys[0].level;
             dbg_dump(c, "ybts", j, ys[0]);
         }
-        // S = Relin(sum_c y_c (x) y_c), one sum per group
-        int L = ly + 1;
-        DPtr d = dalloc(c, (size_t)G * 3 * L * c->N);
-        bool first = true;
-        if (G > 1) {
-            const DCt &y = ys[0];
-            long t3 = 3L * L * c->N;
-            DPtr dd = m > 1 ? dalloc(c, (size_t)y.nct * t3) : DPtr();
-            tensor_into(c, m > 1 ? dd.get() : d.get(), y, y, ly, false);
-            // group g: d[g] = sum_i dd[g m + i] (3 polynomials of L limbs each)
-            for (int g = 0; m > 1 && g < G; g++) {
-                for (int i = 1; i < m; i++) {
-                    const uint64_t *acc = i == 1 ? dd.get() + (long)g * m * t3 : d.get() + g * t3;
-                    {
-                        ProfScope ps_(c, "elementwise", 0);
-                        k_add<<<grid_for(c, t3), 256, 0, c->st>>>(d.get() + g * t3, (long)L * c->N, acc, (long)L * c->N,
-                                                                   dd.get() + ((long)g * m + i) * t3, (long)L * c->N,
-                                                                   3 * L, L, qmap(L), c->d_mods, c->logN, 0);
-                    }
-                    LAUNCH_CHECK();
-                }
-            }
-            first = false;
-        }
-        for (auto &y : ys) {
-            if (G > 1) break;
-            if (y.nct == 1) {
-                tensor_into(c, d.get(), y, y, ly, !first);
-                first = false;
-            } else {
-                // sum of the per-ciphertext tensors of the batch
-                DPtr dd = dalloc(c, (size_t)y.nct * 3 * L * c->N);
-                tensor_into(c, dd.get(), y, y, ly, false);
-                for (int i = 0; i < y.nct; i++) {
-                    int cnt = 3 * L;
-                    long tot = (long)cnt << c->logN;
-                    if (first && i == 0)
-                        {
-                            ProfScope ps_(c, "copy", 0);
-                            CK(cudaMemcpyAsync(d.get(), dd.get(), (size_t)3 * L * c->N * 8, cudaMemcpyDeviceToDevice, c->st));
-                        }
-                    else {
-                        ProfScope ps_(c, "elementwise", 0);
-                        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), (long)L * c->N, d.get(), (long)L * c->N,
-                                                                    dd.get() + (long)i * 3 * L * c->N, (long)L * c->N,
-                                                                    cnt, L, qmap(L), c->d_mods, c->logN, 0);
-                    }
-                    LAUNCH_CHECK();
-                }
-                first = false;
-            }
-        }
-        DCt S = relin_rescale(c, d.get(), ly, G, ys[0].scale * ys[0].scale);
-        c->cnt[2]++;
+        DCt S = square_sum(c, ys, m, G);
+        PhaseScope ph_aux(c, "aux");
         S = rotsum(c, S, stride, nrot);
         dbg_dump(c, "S", j, S);
         int dj = ilog2c(p.inv_deg[j] + 1);
@@ -1674,12 +1715,134 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         if (lam_bts) lam.scale = lam.scale * p.gl[j];
         dbg_dump(c, "lamf", j, lam);
         double soz = zb ? sqrt(y_target(c, p, j + 1, ut - 1) * qd(c, ut)) : 0.0;
+        PhaseScope ph_main(c, "main");
         for (auto &y : ys) {
             DCt z = G > 1 && m > 1 ? hmult_grouped(c, lam, y, m) : hmult(c, lam, y);
             if (zb) z = bts_boosted(c, p, z, 1.0, soz);
             y = hmult(c, z, z);
         }
         dbg_dump(c, "y", j, ys[0]);
+    }
+    return ys;
+}
+
+// Alg. 4 (version B, Sec. 4.3) with the auxiliary thread of Alg. 3 on the many-ciphertext
+// packing of Sec. 4.2.  lambda_j = S_j^(-1/2^j) with S_j = sum (y^(j-1))^2 (the reading under which
+// every round normalises: lambda_1 ... lambda_j applied to y^(0) and squared j times gives y^(j));
+// the main thread never bootstraps, the auxiliary ciphertext does (S_j and lambda_j, each alone):
+//   u = 2x/M + 1; y0 = P_exp(u) at scale sqrt(Delta q_ly0), so that S_1 lands at Delta
+//   for j = 1..k:
+//     S_j  = RotSum(relinearised sum_c y_c (x) y_c)      (y = y0 for j = 1, y^(j-1) after)
+//     v    = Bootstrap(gain_s S_j) on [a_j, b_j], mapped to [-1, 1]
+//     lam  = P_j(v) gain_s^(1/2^j) (gain folded into the coefficients; a polynomial too deep to
+//            end above the bootstrapping input level is evaluated split, split_eval)
+//     lam  is bootstrapped with gain 1/lam_max_j, then Lam = Lam * lam (Lam = lam for j = 1):
+//            one value per Softmax in slots [0, L), one level lower every iteration
+//     lr   = RotSum(Lam (.) mask) with the mask 1 on [0, L) encoded at the scale that makes z
+//            land where its j squarings need it
+//     z_c  = lr * y0_c; y^(j)_c = z_c^(2^j) (j squarings)
+// Every free scale is chosen so that the next polynomial input sits at the scale of its level's
+// prime and every bootstrapping input at Delta.
+static DCt split_eval(he_ctx *c, const Plan &p, const DCt &v, const std::vector<double> &cf, int dj, double delta,
+                      double bmax) {
+    // p(u) = A(u) + T_h(u) B(u), h = 2^(dj-1), A and B of degree < h (T_h T_i = (T_(h+i) + T_(h-i))/2):
+    // A, B and T_(h/2) take dj - 1 levels each; T_(h/2) and B are bootstrapped, T_h = 2 T_(h/2)^2 - 1,
+    // and T_h B joins A at the bootstrapping input level
+    REQUIRE(bmax > 0, HE_EINVAL, "split polynomial: the plan gives no bound for its upper half");
+    int top = v.level, h = 1 << (dj - 1), d = (int)cf.size() - 1;
+    std::vector<double> a_c(cf.begin(), cf.begin() + h), b_c(d - h + 1, 0.0);
+    b_c[0] = cf[h];
+    for (int i = 1; i <= d - h; i++) {
+        b_c[i] = 2.0 * cf[h + i];
+        a_c[h - i] = a_c[h - i] - cf[h + i];
+    }
+    int lo = top - (dj - 1);
+    std::vector<double> e(h / 2 + 1, 0.0);
+    e[h / 2] = 1.0;
+    double s_t = sqrt(2.0 * qd(c, top) * delta);
+    DCt t = bts_boosted(c, p, poly_eval(c, v, e, lo, delta), 1.0, s_t);
+    DCt th = hmult(c, t, t);                  // t^2 at 2 Delta = 2 t^2 - 1 + 1 at Delta
+    th.scale = th.scale / 2.0;
+    ct_add_const(c, th, h_round(-1.0 * th.scale));
+    DCt bb = bts_boosted(c, p, poly_eval(c, v, b_c, lo, delta), 1.0 / bmax, qd(c, top - 1) * bmax);
+    bb.scale = bb.scale / bmax;               // B at scale q_(top-1)
+    DCt prod = hmult(c, th, bb);
+    DCt a = poly_eval(c, v, a_c, lo, prod.scale);
+    DCt out = ct_drop(c, prod, lo);
+    ct_add_inplace(c, out, a);
+    return out;
+}
+
+// the mask (value mval on slots [0, stride), 0 elsewhere) encoded at `scale` for `level`,
+// once per (stride, level, value, scale)
+static const uint64_t *mask_pt(he_ctx *c, int stride, int level, double mval, double scale) {
+    char mkey[128];
+    snprintf(mkey, sizeof mkey, "mask:%d:%d:%a:%a", stride, level, mval, scale);
+    auto mit = c->pt_cache.find(mkey);
+    if (mit == c->pt_cache.end()) {
+        std::vector<double2> mk(c->n0, make_double2(0.0, 0.0));
+        for (int i = 0; i < stride; i++) mk[i].x = mval;
+        mit = c->pt_cache.emplace(mkey, encode(c, mk, scale, level)).first;
+    }
+    return mit->second.get();
+}
+
+static std::vector<DCt> softmax_run_b(he_ctx *c, const Plan &p, std::vector<DCt> ys, int m, int G = 1) {
+    REQUIRE(G == 1 || (ys.size() == 1 && ys[0].nct == G * m), HE_EINVAL, "softmax: groups need one batch");
+    REQUIRE(c->bootstrap, HE_EINVAL, "Alg. 4 needs bootstrapping");
+    int n0 = c->n0, n = p.n;
+    int stride = (int)((long)m * n0 / n);
+    int nrot = ilog2c(n / m);
+    int top = c->user_top;
+    double delta = std::ldexp(1.0, c->log_scale);
+    int ly0 = ys[0].level - ilog2c(p.exp_deg + 1);
+    {
+        PhaseScope ph(c, "main");
+        for (auto &y : ys) {
+            affine_to_unit(c, y, -p.M, 0.0);
+            y = poly_eval(c, y, p.exp_c, ly0, sqrt(delta * qd(c, ly0)));
+        }
+    }
+    const std::vector<DCt> y0 = ys;
+    const double y0_scale = y0[0].scale;
+    DCt lam_c;
+    bool have_lam = false;
+    for (int j = 1; j <= p.k; j++) {
+        const int jj = j - 1;   // plan index
+        DCt S = square_sum(c, ys, m, G);
+        PhaseScope ph_aux(c, "aux");
+        S = rotsum(c, S, stride, nrot);
+        double a = p.a[jj], b = p.b[jj];
+        DCt v = bts_boosted(c, p, S, p.gs[jj], (2.0 / (b - a)) * qd(c, top));
+        affine_to_unit(c, v, a, b);
+        std::vector<double> cf = p.inv_c[jj];
+        double g = pow(p.gs[jj], p.expo[jj]);
+        for (auto &x : cf) x = x * g;
+        int dj = ilog2c((int)cf.size());
+        int lp = top - dj;
+        DCt lam = lp < c->bts_min ? split_eval(c, p, v, cf, dj, delta, p.b_max[jj]) : poly_eval(c, v, cf, lp, delta);
+        double lmax = p.lam_max[jj];
+        int lam_lv = have_lam ? lam_c.level : top;
+        DCt lb = bts_boosted(c, p, lam, 1.0 / lmax, qd(c, lam_lv) * lmax);
+        lb.scale = lb.scale / lmax;           // lambda_j at scale q_(lam_lv)
+        lam_c = have_lam ? hmult(c, lam_c, lb) : lb;
+        have_lam = true;
+        // where z lands and the scale it needs there: j squarings, then (j < k) one more for S
+        int lz = ly0 - 1;
+        double sz = delta;
+        for (int i = (j == p.k ? j : j + 1); i >= 1; i--) sz = sqrt(sz * qd(c, lz - i + 1));
+        double s_lr = (sz * qd(c, ly0)) / y0_scale;
+        double sm = (s_lr * qd(c, lam_c.level)) / lam_c.scale;
+        DCt lr = ct_copy(c, lam_c);
+        ct_mul_plain(c, lr, mask_pt(c, stride, lam_c.level, 1.0, sm));
+        lr.scale = lr.scale * sm;
+        lr = rotsum(c, rescale(c, lr), stride, nrot);
+        PhaseScope ph_main(c, "main");
+        for (size_t i = 0; i < ys.size(); i++) {
+            DCt z = G > 1 && m > 1 ? hmult_grouped(c, lr, y0[i], m) : hmult(c, lr, y0[i]);
+            for (int t = 0; t < j; t++) z = hmult(c, z, z);
+            ys[i] = z;
+        }
     }
     return ys;
 }
@@ -2040,9 +2203,28 @@ int he_params_insecure(const he_params *p) {
     return (p->log_n < 16 || p->h < 192 || log_qp > bound) ? 1 : 0;
 }
 
+// Drops every evaluation key and every captured Softmax graph (whose kernels read those keys):
+// a new secret makes all of them stale.  Encoded plaintexts (diagonals, masks) do not depend on
+// the secret and stay.
+static void drop_keys(he_ctx *c) {
+    CK(cudaStreamSynchronize(c->st));
+    if (c->gstream) CK(cudaStreamSynchronize(c->gstream));
+    for (auto &kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (auto &r : kv.second.prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+    }
+    c->graphs.clear();
+    for (auto &kv : c->keys) cudaFree(kv.second);
+    c->keys.clear();
+}
+
 int he_keygen(he_ctx *ctx, uint64_t seed, const int *rot_steps, int n_rot) {
     if (!ctx || n_rot < 0 || (n_rot > 0 && !rot_steps)) return HE_EINVAL;
     API_BEGIN
+    if (ctx->have_keys) drop_keys(ctx);
     keygen(ctx, seed);
     make_key(ctx, 0);
     make_key(ctx, 2 * ctx->N - 1);
@@ -2142,6 +2324,7 @@ static Plan plan_of(he_ctx *c, const he_softmax_plan *hp) {
     p.M = hp->M;
     p.boost = hp->bts_boost > 0 ? hp->bts_boost : 1.0;
     p.exp_deg = hp->exp_deg;
+    p.method = hp->method;
     p.exp_c.assign(hp->exp_coeffs, hp->exp_coeffs + hp->exp_deg + 1);
     const double *cp = hp->inv_coeffs;
     for (int j = 0; j < p.k; j++) {
@@ -2151,7 +2334,13 @@ static Plan plan_of(he_ctx *c, const he_softmax_plan *hp) {
         p.a.push_back(hp->inv_a[j]);
         p.b.push_back(hp->inv_b[j]);
         p.gs.push_back(hp->gain_s[j]);
-        p.gl.push_back(hp->gain_l[j]);
+        if (p.method == HE_SOFTMAX_ALG4) {
+            p.expo.push_back(hp->exponent[j]);
+            p.lam_max.push_back(hp->lam_max[j]);
+            p.b_max.push_back(hp->b_max[j]);
+        } else {
+            p.gl.push_back(hp->gain_l[j]);
+        }
     }
     (void)c;
     return p;
@@ -2166,6 +2355,20 @@ static int softmax_check(he_ctx *ctx, const he_softmax_plan *plan, const he_ct *
     int m = cts->n_ct / groups, n = plan->n;
     if (n < 1 || (n & (n - 1)) || n % m || ctx->n0 % n) {
         ctx->err = "n must be a power of two dividing N/2, and m must divide n";
+        return HE_EINVAL;
+    }
+    if (plan->method != HE_SOFTMAX_ALG2 && plan->method != HE_SOFTMAX_ALG4) {
+        ctx->err = "plan method must be HE_SOFTMAX_ALG2 or HE_SOFTMAX_ALG4";
+        return HE_EINVAL;
+    }
+    if (!plan->exp_coeffs || !plan->inv_deg || !plan->inv_coeffs || !plan->inv_a || !plan->inv_b ||
+        !plan->gain_s || (plan->method == HE_SOFTMAX_ALG2 && !plan->gain_l) ||
+        (plan->method == HE_SOFTMAX_ALG4 && (!plan->exponent || !plan->lam_max || !plan->b_max))) {
+        ctx->err = "plan: a coefficient or gain array is missing";
+        return HE_EINVAL;
+    }
+    if (plan->method == HE_SOFTMAX_ALG4 && !ctx->bootstrap) {
+        ctx->err = "Alg. 4 needs a context with bootstrapping";
         return HE_EINVAL;
     }
     return HE_OK;
@@ -2183,7 +2386,8 @@ static void softmax_inplace(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts
         REQUIRE(groups == 1, HE_EINVAL, "groups need the batched form");
         for (int i = 0; i < m; i++) ys.push_back(ct_copy(ctx, ct_sub(ctx, in, i)));
     }
-    ys = softmax_run(ctx, p, ys, m, batched ? groups : 1);
+    ys = p.method == HE_SOFTMAX_ALG4 ? softmax_run_b(ctx, p, ys, m, batched ? groups : 1)
+                                     : softmax_run(ctx, p, ys, m, batched ? groups : 1);
     int lo = ys[0].level;
     long cs = 2L * (lo + 1) * ctx->N;
     if (batched) {
@@ -2232,7 +2436,14 @@ static uint64_t plan_hash(const he_softmax_plan *hp) {
     mix(hp->inv_a, sizeof(double) * hp->k);
     mix(hp->inv_b, sizeof(double) * hp->k);
     mix(hp->gain_s, sizeof(double) * hp->k);
-    mix(hp->gain_l, sizeof(double) * hp->k);
+    mix(&hp->method, sizeof hp->method);
+    if (hp->method == HE_SOFTMAX_ALG4) {
+        mix(hp->exponent, sizeof(double) * hp->k);
+        mix(hp->lam_max, sizeof(double) * hp->k);
+        mix(hp->b_max, sizeof(double) * hp->k);
+    } else {
+        mix(hp->gain_l, sizeof(double) * hp->k);
+    }
     return h;
 }
 
@@ -2390,15 +2601,25 @@ int he_rescale(he_ctx *ctx, const he_ct *a, he_ct *out) {
 
 int he_rescale_noalloc(he_ctx *ctx, const he_ct *a, he_ct *out) {
     if (!ctx || !a || !out || !a->data || !out->data || a->n_ct < 1) return HE_EINVAL;
-    if (a->level < 1 || a->level >= ctx->nq) {
-        ctx->err = "he_rescale_noalloc: level must be in [1, n_q)";
-        return HE_ELEVEL;
-    }
-    if (out->data == a->data) {
-        ctx->err = "he_rescale_noalloc: output must not alias the input";
+    if (a->level < 0 || a->level >= ctx->nq) {
+        ctx->err = "he_rescale_noalloc: level must be in [0, n_q)";
         return HE_EINVAL;
     }
+    if (a->level == 0) {
+        ctx->err = "he_rescale_noalloc: rescale at level 0";
+        return HE_ELEVEL;
+    }
     size_t need = (size_t)2 * a->n_ct * (a->level + 1) * ctx->N;
+    {
+        // the final pass reads a with stride level+1 limbs and writes out with stride level:
+        // any overlap of the two byte ranges would let it overwrite limbs not yet read
+        uintptr_t a0 = (uintptr_t)a->data, a1 = a0 + need * 8;
+        uintptr_t o0 = (uintptr_t)out->data, o1 = o0 + (size_t)2 * a->n_ct * a->level * ctx->N * 8;
+        if (o0 < a1 && a0 < o1) {
+            ctx->err = "he_rescale_noalloc: output must not overlap the input";
+            return HE_EINVAL;
+        }
+    }
     if (need > HE_NOALLOC_SCRATCH_WORDS) {
         char b[160];
         snprintf(b, sizeof b, "he_rescale_noalloc: needs %zu scratch words, the fixed scratch holds %u "
@@ -2530,6 +2751,9 @@ int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len) {
         std::get<0>(f)++;
         std::get<1>(f) += ms;
         std::get<2>(f) += ctx->prof_b[i];
+        auto &ph = fam[std::string("phase:") + ctx->prof_ph[i]];
+        std::get<0>(ph)++;
+        std::get<1>(ph) += ms;
     }
     for (auto &kv : ctx->graphs) {
         if (!kv.second.replayed) continue;

@@ -30,10 +30,14 @@ class he_params(C.Structure):
                 ("em_coeffs", dblp)]
 
 
+HE_SOFTMAX_ALG2, HE_SOFTMAX_ALG4 = 0, 1
+
+
 class he_softmax_plan(C.Structure):
     _fields_ = [("n", C.c_int), ("k", C.c_int), ("M", C.c_double), ("exp_deg", C.c_int), ("exp_coeffs", dblp),
                 ("inv_deg", intp), ("inv_coeffs", dblp), ("inv_a", dblp), ("inv_b", dblp), ("gain_s", dblp),
-                ("gain_l", dblp), ("bts_boost", C.c_double)]
+                ("gain_l", dblp), ("bts_boost", C.c_double), ("method", C.c_int), ("exponent", dblp),
+                ("lam_max", dblp), ("b_max", dblp)]
 
 
 class he_ct(C.Structure):
@@ -200,9 +204,14 @@ class Context:
     def keygen_softmax(self, n, m):
         self.check(lib().he_keygen_softmax(self.h, n, m))
 
-    def encrypt(self, x, n, m, M, seed):
+    def encrypt(self, x, n, m, M, seed, out=None):
+        """he_encrypt of x [L][n] into m ciphertexts (a new buffer, or `out`'s, which must hold
+        m ciphertexts at the top user level)."""
         x = np.ascontiguousarray(x, dtype=np.float64)
-        out = self.alloc(self.chain["user_top_level"], m)
+        if out is None:
+            out = self.alloc(self.chain["user_top_level"], m)
+        elif out.tensor.numel() < m * 2 * (self.chain["user_top_level"] + 1) * self.n:
+            raise ValueError("encrypt: output buffer too small")
         h = out.c()
         self.check(lib().he_encrypt(self.h, x.ctypes.data_as(dblp), x.size, n, m, M, seed, C.byref(h)))
         out.update(h)
@@ -362,20 +371,38 @@ class Context:
         return lib().he_selftest_bounded_wait(self.h, max_iter)
 
 
+def load_plans_b():
+    """The Alg. 4 (version B) plans, params/plans_b.json."""
+    with open(os.path.join(PARAMS_DIR, "plans_b.json")) as fh:
+        return json.load(fh)
+
+
 class Plan:
-    """he_softmax_plan built from a plan dict (params/plans.json); keeps the arrays alive."""
+    """he_softmax_plan built from a plan dict (params/plans.json for Alg. 2, params/plans_b.json
+    for Alg. 4, version "B"); keeps the arrays alive."""
 
     def __init__(self, plan):
         its = plan["iters"][: plan["k"]]
+        alg4 = plan.get("version") == "B"
         self.exp = _hex(plan["exp"]["coeffs"])
         self.deg = np.array([it["deg"] for it in its], dtype=np.int32)
         self.inv = np.concatenate([_hex(it["coeffs"]) for it in its])
         self.a = np.array([it["a"] for it in its])
         self.b = np.array([it["b"] for it in its])
         self.gs = np.array([it["gain_s"] for it in its])
-        self.gl = np.array([it["gain_l"] for it in its])
+        none = C.cast(None, dblp)
+        if alg4:
+            self.e = np.array([it["exponent"] for it in its])
+            self.lm = np.array([it["lam_max"] for it in its])
+            self.bm = np.array([it["b_max"] for it in its])
+            gl, ex, lm, bm = none, self.e.ctypes.data_as(dblp), self.lm.ctypes.data_as(dblp), \
+                self.bm.ctypes.data_as(dblp)
+        else:
+            self.gl = np.array([it["gain_l"] for it in its])
+            gl, ex, lm, bm = self.gl.ctypes.data_as(dblp), none, none, none
         self.s = he_softmax_plan(plan["n"], plan["k"], plan["M"], plan["exp"]["deg"],
                                  self.exp.ctypes.data_as(dblp), self.deg.ctypes.data_as(intp),
                                  self.inv.ctypes.data_as(dblp), self.a.ctypes.data_as(dblp),
                                  self.b.ctypes.data_as(dblp), self.gs.ctypes.data_as(dblp),
-                                 self.gl.ctypes.data_as(dblp), float(plan.get("bts_boost", 1.0)))
+                                 gl, float(plan["bts_boost"] if alg4 else plan.get("bts_boost", 1.0)),
+                                 HE_SOFTMAX_ALG4 if alg4 else HE_SOFTMAX_ALG2, ex, lm, bm)

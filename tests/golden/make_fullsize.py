@@ -1,7 +1,8 @@
 """Writes tests/golden/fullsize_fgb16.json: the CPU oracle's results at N = 2^16 (the fgb16
 chain: log QP <= 1555, h = 192, bootstrapping) for cases too slow to recompute inside the GPU
 tests, as SHA-256 hashes of every output limb (coefficient form, canonical residues in
-[0, q_i), little-endian uint64) plus the output level and scale.
+[0, q_i), little-endian uint64) plus the output level (level_out) and scale (scale, as a hex
+float).
 
 Calls only oracle/ (and the seeded input generators, which hold none of the method's
 arithmetic).  The oracle's results are the same on x86-64 and AArch64 hosts (every double
@@ -41,7 +42,7 @@ KEY_SEED = 2024
 
 # input recipes (shared with tests/test_gpu_fullsize.py through this file's JSON)
 CASES = {
-    "bootstrap": {"kind": "bootstrap", "slots_seed": 31, "level": 3, "scale": 2.0 ** 42, "enc_seed": 41,
+    "bootstrap": {"kind": "bootstrap", "slots_seed": 31, "level": 3, "in_scale": 2.0 ** 42, "enc_seed": 41,
                   "gain": 16.0, "out_scale": 2.0 ** 42},
     "softmax1_alg2": {"kind": "softmax", "plan": "n256_M128", "m": 1, "inputs": "uniform", "input_seed": 5,
                       "enc_seed": 99},
@@ -80,7 +81,7 @@ def run(name, o, em):
     t0 = time.time()
     if case["kind"] == "bootstrap":
         rng = np.random.default_rng(case["slots_seed"])
-        a = o.encrypt(rng.uniform(-1, 1, o.n0), case["level"], case["scale"], case["enc_seed"], 0)
+        a = o.encrypt(rng.uniform(-1, 1, o.n0), case["level"], case["in_scale"], case["enc_seed"], 0)
         outs = [o.bootstrap(a, em, gain=case["gain"], out_scale=case["out_scale"])]
         ins = [a]
     else:
@@ -95,7 +96,7 @@ def run(name, o, em):
         y = O.unpack(np.stack([o.decrypt(c).real for c in outs]), n)
         case = dict(case, bits_vs_fp64=float(-np.log2(np.abs(y - O.softmax_fp64(x)).max())))
     rec = dict(case, key_seed=KEY_SEED, in_hash=limb_hashes(np.stack([c.data for c in ins])),
-               level=outs[0].level, scale=float(outs[0].scale).hex(),
+               level_out=outs[0].level, scale=float(outs[0].scale).hex(),
                out_hash=limb_hashes(np.stack([c.data for c in outs])),
                oracle_seconds=round(time.time() - t0, 1), host_threads=int(os.environ.get("OMP_NUM_THREADS",
                                                                                         os.cpu_count())))

@@ -1,7 +1,12 @@
 """Full-size checks at N = 2^16 (log QP <= 1555, h = 192, bootstrapping), in the launch
-configuration bench.py uses: sampled operations bit-exact with the oracle, and the Softmax
+configuration bench.py uses: operations bit-exact with the oracle (live where the oracle takes
+seconds; against the oracle's per-limb hashes in tests/golden/fullsize_fgb16.json, written by
+tests/golden/make_fullsize.py, for bootstrapping and whole Softmax runs), and the Softmax
 precision bar (>= 15 bits worst case against FP64 Softmax) at any batch size."""
+import hashlib
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -81,3 +86,118 @@ def test_fullsize_serving_plans_grouped_precision(full, params, plan):
         one = he.Ciphertexts(g, batch.tensor[i * w:(i + 1) * w], batch.level, batch.scale, 1)
         err = np.abs(g.decrypt(one, n) - O.softmax_fp64(x)).max()
         assert err < 2 ** -15, (plan, i, -math.log2(err))
+
+
+def _limb_hashes(data):
+    d = np.ascontiguousarray(data, dtype=np.uint64)
+    return [[[hashlib.sha256(d[i, p, t].astype("<u8").tobytes()).hexdigest()[:16] for t in range(d.shape[2])]
+             for p in range(2)] for i in range(d.shape[0])]
+
+
+def test_fullsize_rescale_encode_encrypt_bit_exact(full):
+    """The rescale fused into the N = 2^16 forward transform (two ciphertexts), the encoder and
+    the many-ciphertext encryption (Sec. 4.2 packing) at N = 2^16, limb for limb."""
+    g, ch, em = full
+    o = O.Oracle(ch)
+    o.keygen(2024)
+    rng = np.random.default_rng(3)
+    top = ch["user_top_level"]
+    d = np.zeros((2, 2, top + 1, g.n), dtype=np.uint64)
+    for t in range(top + 1):
+        d[:, :, t] = rng.integers(0, o.q[t], (2, 2, g.n), dtype=np.uint64)
+    gr = g.rescale(g.from_coeff(d, top, 2.0 ** 42))
+    got = g.to_coeff(gr)
+    for i in range(2):
+        r = o.rescale(O.Ct(d[i], top, 2.0 ** 42))
+        assert np.array_equal(got[i], r.data) and gr.scale == r.scale, i
+    z = rng.uniform(-1, 1, o.n0) + 1j * rng.uniform(-1, 1, o.n0)
+    pt = g.encode(z, float(o.q[top]) * 1.5, top)
+    g.ntt(pt, 1, top + 1, inverse=True)
+    assert np.array_equal(pt.cpu().numpy().view(np.uint64).reshape(top + 1, g.n), o.encode(z, float(o.q[top]) * 1.5, top))
+    n, m, M = 256, 2, 128.0
+    x = workloads.uniform_inputs(m * g.n0 // n, n, 4, M)
+    gc = g.to_coeff(g.encrypt(x, n, m, M, 17))
+    slots = O.pack(x, m, o.n0)
+    for i in range(m):
+        assert np.array_equal(gc[i], o.encrypt(slots[i], top, (2 / M) * o.q[top], 17, i).data), i
+
+
+def test_fullsize_lintrans_levels_bit_exact(full):
+    """A SlotToCoeff level on two ciphertexts (16 rows: the staged inner-sum kernel) and a
+    CoeffToSlot level at the top of the chain (50 rows), with their hoisted baby steps and
+    shared giant-step ModDown, limb for limb against the oracle."""
+    g, ch, em = full
+    o = O.Oracle(ch)
+    o.keygen(2024)
+    rng = np.random.default_rng(6)
+    cts = [o.encrypt(rng.uniform(-1, 1, o.n0), 3, 2.0 ** 42, 60 + i) for i in range(2)]
+    ga = g.from_coeff(np.stack([c.data for c in cts]), 3, cts[0].scale)
+    gr = g.to_coeff(g.lintrans(ga, 3, False, 0, 16.0, float(o.q[3])))
+    for i in range(2):
+        assert np.array_equal(gr[i], o.lintrans(cts[i], 3, False, 0, 16.0, float(o.q[3])).data), i
+    top = len(o.q) - 1
+    b = o.encrypt(rng.uniform(-1, 1, o.n0), top, float(o.q[0]), 62)
+    gb = g.lintrans(g.from_coeff(b.data, top, b.scale), 3, True, 0, 1.0, float(o.q[top]))
+    assert np.array_equal(g.to_coeff(gb)[0], o.lintrans(b, 3, True, 0, 1.0, float(o.q[top])).data)
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_fgb16.json")
+
+
+def _golden(name):
+    if not os.path.exists(GOLDEN):
+        pytest.skip("tests/golden/fullsize_fgb16.json not written")
+    with open(GOLDEN) as fh:
+        gold = json.load(fh)
+    if name not in gold:
+        pytest.skip("%s not in tests/golden/fullsize_fgb16.json" % name)
+    return gold[name]
+
+
+def test_fullsize_bootstrap_golden(full):
+    """One bootstrapping at N = 2^16 (SlotToCoeff, ModRaise, CoeffToSlot with 2 m (l+1) > 8 rows,
+    the degree-31 cosine with 4 double angles), input encrypted on the GPU: every input and
+    output limb equals the oracle's (hashes), and the output level and scale."""
+    g, ch, em = full
+    gold = _golden("bootstrap")
+    rng = np.random.default_rng(gold["slots_seed"])
+    z = rng.uniform(-1, 1, g.n0)
+    a = g.encrypt_slots(z, gold["level"], gold["in_scale"], gold["enc_seed"])
+    assert _limb_hashes(g.to_coeff(a)) == gold["in_hash"]
+    r = g.bootstrap(a, gold["gain"], gold["out_scale"])
+    assert r.level == gold["level_out"] and float(r.scale).hex() == gold["scale"]
+    assert _limb_hashes(g.to_coeff(r)) == gold["out_hash"]
+    assert np.abs(g.decrypt_slots(r).real / gold["gain"] - z).max() < 2 ** -20
+
+
+@pytest.mark.parametrize("name", ["softmax1_alg2", "softmax1_alg4", "softmax64_alg2", "softmax64_alg4"])
+def test_fullsize_softmax_golden(full, params, name):
+    """Whole Softmax runs at N = 2^16 against the oracle's per-limb hashes: 1 ciphertext (128
+    Softmax of dim 256) and the 64-ciphertext batch of 8192 (the bench's workload, by graph
+    replay as bench.py times it), each by Alg. 2 and by Alg. 4.  The GPU encryption of the inputs
+    is checked the same way."""
+    g, ch, em = full
+    gold = _golden(name)
+    pl = he.load_plans_b()[gold["plan"]] if gold["plan"].endswith("_B") else params[1][gold["plan"]]
+    n, m, M = pl["n"], gold["m"], pl["M"]
+    L = m * g.n0 // n
+    if gold["inputs"] == "uniform":
+        x = workloads.uniform_inputs(L, n, gold["input_seed"], M)
+    else:
+        x = workloads.attention_logits(L, n, gold["input_seed"], M=M)
+    g.keygen_softmax(n, m)
+    cts = g.encrypt(x, n, m, M, gold["enc_seed"])
+    assert _limb_hashes(g.to_coeff(cts)) == gold["in_hash"]
+    if m > 1:
+        work = g.like(cts)
+        for _ in range(2):
+            work.tensor.copy_(cts.tensor)
+            work.level, work.scale, work.n_ct = cts.level, cts.scale, cts.n_ct
+            g.softmax(work, pl, graph=True)
+        cts = work
+    else:
+        g.softmax(cts, pl, batched=True)
+    assert cts.level == gold["level_out"] and float(cts.scale).hex() == gold["scale"]
+    assert _limb_hashes(g.to_coeff(cts)) == gold["out_hash"]
+    err = np.abs(g.decrypt(cts, n) - O.softmax_fp64(x)).max()
+    assert err < 2 ** -15, -math.log2(err)

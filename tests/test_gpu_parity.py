@@ -269,3 +269,60 @@ def test_large_batch_paths_bit_exact(toybts):
         r = o.bootstrap(b3[i], em, gain=16.0)
         assert gr.level == r.level and gr.scale == r.scale
         assert np.array_equal(got[i], r.data), ("bootstrap", i)
+
+
+def test_second_keygen_replaces_every_key(params):
+    """A second he_keygen with another seed replaces the secret and every evaluation key: a
+    multiplication and a rotation afterwards equal the oracle's under the second seed, limb for
+    limb, and the Softmax rotation keys must be generated again."""
+    ch = params[0]["toy"]
+    g = he.Context(ch)
+    g.keygen(SEED, rot_steps=[1])
+    g.keygen_softmax(16, 1)
+    g.keygen(SEED + 1, rot_steps=[1])
+    o = O.Oracle(ch)
+    o.keygen(SEED + 1)
+    rng = np.random.default_rng(21)
+    a = o.encrypt(rng.uniform(-1, 1, o.n0), 8, 2.0 ** 40, 3, 0)
+    b = o.encrypt(rng.uniform(-1, 1, o.n0), 8, 2.0 ** 40, 3, 1)
+    ga, gb = g.from_coeff(a.data, 8, a.scale), g.from_coeff(b.data, 8, b.scale)
+    assert np.array_equal(g.to_coeff(g.hmult(ga, gb))[0], o.hmult(a, b).data)
+    assert np.array_equal(g.to_coeff(g.rotate(ga, 1))[0], o.rotate(a, 1).data)
+    # the stride-128 rotation key of the first secret's he_keygen_softmax(16, 1) is gone
+    with pytest.raises(RuntimeError, match="-5"):
+        g.rotate(ga, 128)
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain", "graph"])
+def test_softmax_alg4_bit_exact(toybts, params, mode):
+    """Alg. 4 (version B, Sec. 4.3) with the auxiliary thread of Alg. 3, two ciphertexts of the
+    many-ciphertext packing: every output limb equals the oracle's, in the batched form, the
+    per-ciphertext form and by graph replay; only the auxiliary ciphertext is bootstrapped."""
+    g, o, em = toybts
+    pl = he.load_plans_b()["toybts_n16_M32_B"]
+    n, m = pl["n"], 2
+    g.keygen_softmax(n, m)
+    rng = np.random.default_rng(23)
+    L = m * o.n0 // n
+    x = rng.uniform(-pl["M"], 0, (L, n))
+    gc = g.encrypt(x, n, m, pl["M"], 34)
+    top = o.chain["user_top_level"]
+    slots = O.pack(x, m, o.n0)
+    outs = o.softmax_b([o.encrypt(slots[i], top, (2 / pl["M"]) * o.q[top], 34, i) for i in range(m)], pl, em)
+    c0 = g.counters()
+    if mode == "graph":
+        work = g.like(gc)
+        for _ in range(2):
+            work.tensor.copy_(gc.tensor)
+            work.level, work.scale, work.n_ct = gc.level, gc.scale, gc.n_ct
+            g.softmax(work, pl, graph=True)
+        gc = work
+    else:
+        g.softmax(gc, pl, batched=mode == "batched")
+        # bootstrapping calls: S_j and lambda_j in each of the k rounds, nothing of the main thread
+        assert g.counters()["bts"] - c0["bts"] == 2 * pl["k"]
+    assert gc.level == outs[0].level and gc.scale == outs[0].scale
+    got = g.to_coeff(gc)
+    for i in range(m):
+        assert np.array_equal(got[i], outs[i].data), i
+    assert np.abs(g.decrypt(gc, n) - O.softmax_fp64(x)).max() < 2 ** -15
