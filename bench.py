@@ -7,14 +7,22 @@ attention logits q.k/sqrt(64), q, k ~ N(0, 1), shifted by a public bound and cli
 
 A step is one Softmax over the whole batch, ciphertexts already resident in HBM (a pristine
 copy is restored into the working buffer inside the step): he_softmax_graph, i.e. a replay of
-the circuit captured as one CUDA graph in the first warm-up step.  Plain: he_softmax one
-ciphertext at a time, eager.  The timed region is
-bracketed by a barrier and a synchronize, timed with CUDA events on the library's stream.
+the circuit captured as one CUDA graph in the first warm-up step.  --method picks the circuit:
+alg4 (default; Alg. 4 version B with the auxiliary thread of Alg. 3, Sec. 4.3: only the
+auxiliary ciphertext is bootstrapped) or alg2 (Alg. 2 with Alg. 3, Sec. 4.2); the other one is
+timed too (other_method).  Plain: he_softmax one ciphertext at a time, eager.  The timed region
+is bracketed by a barrier and a synchronize, timed with CUDA events on the library's stream.
 e2e: the same metric through he_softmax with the ciphertexts copied from pinned host memory
-to the device and the results copied back, inside the timed region.
+to the device and the results copied back, inside the timed region, every timed step;
+e2e_x_to_y: FP64 inputs in host memory encrypted (he_encrypt), the Softmax, and the outputs
+decrypted into host memory (he_decrypt), every timed step.
+precision: worst/avg/std of the bits of max |error| against FP64 Softmax over seeds 0-4 and
+three input recipes, and (with the CPU leg) the split into polynomial approximation
+(the oracle's FP64 simulation of the circuit against FP64 Softmax) and CKKS noise
+(decryption against that simulation).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                       [--workload m64|m1] [--profile-kernel NAME]
+                       [--workload m64|m1] [--method alg4|alg2] [--profile-kernel NAME]
 Under torchrun each rank runs an independent replica (weak scaling, no collective on the
 data path); rank 0 prints one JSON line.
 """
@@ -109,6 +117,43 @@ class ClockSampler:
 NTT_DRAM_PER_ALG_BYTE = 1.733e6 / (16 * 65536)
 
 
+# integer pipes of the NTT passes (both forward passes of a 320-limb ModUp transform at N = 2^16,
+# weighted by their durations 105 / 131 us; ncu SpeedOfLight / ComputeWorkloadAnalysis /
+# SchedulerStats sections, python -m paper_2410_11184_gb300.profile_case keyswitch):
+# sm__pipe_alu_cycles_active, sm__pipe_fma_cycles_active (IMAD), smsp__issue_active, in % of peak
+NTT_INT_PIPES = {"alu_pct": 51.3, "fma_imad_pct": 38.1, "issue_active_pct": 57.3,
+                 "source": "ncu, k_ntt_{cols,rows}_fwd_rb<4,0> on 320 limbs (profiles/ntt_rb_keyswitch_m64_level12.txt)"}
+
+# circuits: the plan file entry each method evaluates at n = 256 on [-128, 0]
+METHODS = {"alg4": ("n256_M128_B", "Alg. 4 (version B) + Alg. 3 auxiliary thread, Sec. 4.3"),
+           "alg2": ("n256_M128", "Alg. 2 + Alg. 3 auxiliary thread, Sec. 4.2")}
+# ciphertext key switches per step (he_counters of the GPU run) of each method and workload,
+# used by the reference arm's scaling
+KS_PER_STEP = {("alg2", "m64"): 7969, ("alg2", "m1"): 847, ("alg4", "m64"): 2744, ("alg4", "m1"): 1280}
+
+
+def load_plan(he, method):
+    name = METHODS[method][0]
+    return he.load_plans_b()[name] if name.endswith("_B") else he.load_params()[1][name]
+
+
+def bits(err):
+    return -math.log2(err) if err > 0 else None
+
+
+def stats_bits(errs):
+    b = [-math.log2(e) for e in errs if e > 0]
+    return {"worst": min(b), "avg": statistics.mean(b), "std": statistics.pstdev(b), "runs": len(b)} if b else None
+
+
+def recipes(L, n, seed, M):
+    """the three synthetic input recipes (stand-ins for the paper's LLaMa logits)"""
+    from paper_2410_11184_gb300 import workloads as W
+
+    return {"uniform": W.uniform_inputs(L, n, seed, M), "paper_normal": W.paper_normal_inputs(L, n, seed, M),
+            "attention": W.attention_logits(L, n, seed, M=M)}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -118,11 +163,48 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def cpu_simulation(runs, plan):
+    """The CPU leg's second part: the oracle's FP64 simulation of the circuit (its polynomials,
+    no encryption) on the inputs of the precision runs; returns per run (max |O2 - O1|,
+    max |dec - O2|): polynomial approximation and CKKS noise."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    out = []
+    for x, y in runs:
+        o2 = (O.simulate_b(x, plan) if plan.get("version") == "B" else O.simulate(x, plan))[0]
+        out.append((float(np.abs(o2 - O.softmax_fp64(x)).max()), float(np.abs(y - o2).max())))
+    return out
+
+
+def cpu_full_toy_softmax():
+    """One whole Softmax of the oracle at N = 2^12 (128 Softmax of dim 16 on [-8, 0], k = 2, no
+    bootstrapping): a measured full run, not an extrapolation."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    chains, plans, _ = O.load_params()
+    ch, pl = chains["toy"], plans["cfg1_n16_M8"]
+    o = O.Oracle(ch)
+    o.keygen(11)
+    n = pl["n"]
+    x = np.random.default_rng(0).uniform(-pl["M"], 0, (o.n0 // n, n))
+    top = ch["user_top_level"]
+    ct = o.encrypt(O.pack(x, 1, o.n0)[0], top, (2 / pl["M"]) * o.q[top], 5, 0)
+    o.softmax([ct], pl)   # rotation keys made outside the timing
+    t0 = time.perf_counter()
+    o.softmax([ct], pl)
+    dt = time.perf_counter() - t0
+    return {"workload": "N=2^12, 1 ciphertext, 128 Softmax of dim 16, k=2, no bootstrapping",
+            "ms": dt * 1e3, "ms_per_softmax": dt * 1e3 / (o.n0 // n)}
+
+
 def cpu_baseline(steps_unit_ks, ms_per_softmax_scale):
     """Times the CPU oracle (as it stands) on a bounded sample: one relinearised multiplication
     at the top user level and one rotation at the top bootstrapping level of the N = 2^16
     chain; the mean key-switch time is scaled by the circuit's key-switch count per Softmax
-    (counted by the GPU run)."""
+    (counted by the GPU run).  That assumes every key switch of the step costs what these two
+    do (it leaves out plaintext products, encodings and NTT-only work)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
 
@@ -163,7 +245,7 @@ def run_reference(args, wl):
         return
     # ciphertext key switches per Softmax step of this workload (the circuit's operation list, as
     # counted by he_counters on the GPU path: 64-ciphertext batch / one ciphertext)
-    ks_per_step = {"m64": 7969, "m1": 847}[args.workload]
+    ks_per_step = KS_PER_STEP[(args.method, args.workload)]
     L = wl["m"] * 32768 // wl["n"]
     vals = []
     for _ in range(args.warmup + args.steps):
@@ -174,7 +256,8 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/Softmax", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * L, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues)", "data": "synthetic",
-            "config": {"workload": wl["workload"], "n": wl["n"], "m": wl["m"], "softmax_per_step": L},
+            "config": {"workload": wl["workload"], "n": wl["n"], "m": wl["m"], "softmax_per_step": L,
+                       "method": METHODS[args.method][1]},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "ms/Softmax", "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -182,15 +265,18 @@ def run_reference(args, wl):
 
 def run_serve(args):
     """Serving workload: Poisson arrivals of one-ciphertext encrypted Softmax requests whose
-    dimension is drawn from {128, 256, 1024} (inputs uniform on [-64, 0], N = 2^16 with
-    bootstrapping), admitted by HBM budget and batched by shape (serve.Server).  Prints one JSON
-    line with p50/p99 request latency, Softmax/s and the worst-case error per dimension."""
+    dimension is drawn from {128, 256, 1024, 4096} (inputs uniform on [-64, 0], N = 2^16 with
+    bootstrapping), admitted by HBM budget and batched by shape (serve.Server).  Dimensions up to
+    1024 use the Alg. 2 plans, 4096 the Alg. 4 plan (Alg. 2 does not converge there on this
+    chain); 32768 is not served.  Prints one JSON line with p50/p99 request latency, Softmax/s and
+    the worst-case error per dimension."""
     import torch
 
     from paper_2410_11184_gb300 import he, serve, workloads
 
     chains, plans, evalmod = he.load_params()
-    names = ["n128_M64", "n256_M64", "n1024_M64"]
+    plans = dict(plans, **he.load_plans_b())
+    names = ["n128_M64", "n256_M64", "n1024_M64", "n4096_M64_B"]
     g = he.Context(chains["fgb16"], evalmod["fgb16"])
     g.keygen(5)
     for nm in names:
@@ -243,14 +329,15 @@ def run_serve(args):
         worst[n] = max(worst.get(n, 0.0), err)
     softmax_done = sum(g.n0 // plans[k[0]]["n"] for k, _ in handles)
     line = {
-        "metric": "serving: request latency p50/p99 and Softmax/s (n in {128,256,1024}, N=2^16, bootstrapping)",
+        "metric": "serving: request latency p50/p99 and Softmax/s (n in {128,256,1024,4096}, N=2^16, bootstrapping)",
         "value": st["p99_ms"], "unit": "ms (p99 request latency)", "higher_is_better": False,
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
         "softmax_per_s": softmax_done / st["span_s"], "requests": st["requests"], "span_s": st["span_s"],
         "arrival_rate_per_s": args.rate, "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
         "precision_bits_by_n": {str(n): -math.log2(e) if e > 0 else None for n, e in sorted(worst.items())},
         "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
-        "config": {"workload": "Poisson arrivals, one ciphertext per request, dims 128/256/1024 on [-64, 0]",
+        "config": {"workload": "Poisson arrivals, one ciphertext per request, dims 128/256/1024/4096 on [-64, 0] "
+                                "(4096 by Alg. 4; 32768 not served)",
                    "hbm_budget_gb": budget / 1e9, "max_batch_ct": args.max_batch_ct},
     }
     print(json.dumps(line))
@@ -343,6 +430,10 @@ def main():
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-split", action="store_true", help="skip the split-packing (one problem per ciphertext) timing")
     ap.add_argument("--latency-repeats", type=int, default=50, help="single-ciphertext latency repeats (0: off)")
+    ap.add_argument("--method", default="alg4", choices=sorted(METHODS), help="Softmax circuit")
+    ap.add_argument("--no-other", action="store_true", help="skip timing the other method")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch strategies")
+    ap.add_argument("--precision-seeds", type=int, default=5, help="seeds per input recipe of the precision sweep")
     args = ap.parse_args()
     if args.workload == "serve":
         return run_serve(args)
@@ -367,43 +458,58 @@ def main():
     from paper_2410_11184_gb300 import he, shard
 
     chains, plans, evalmod = he.load_params()
-    ch, pl, em = chains["fgb16"], plans["n256_M128"], evalmod["fgb16"]
+    ch, em = chains["fgb16"], evalmod["fgb16"]
+    pl = load_plan(he, args.method)
+    other = "alg2" if args.method == "alg4" else "alg4"
+    pl_other = load_plan(he, other)
     stream = torch.cuda.Stream(dev)
     g = he.Context(ch, em, stream=stream, device=dev)
     m, n = wl["m"], wl["n"]
     L = m * g.n0 // n
+    M = pl["M"]
     seeds = shard.replica_seeds(rank)   # independent replica per rank (weak scaling)
     g.keygen(seeds["key"])
     g.keygen_softmax(n, m)
+    # autotuner: launch strategies timed on the device for every level of the chain and the two
+    # batch sizes the circuit runs (the auxiliary ciphertext and the m main-thread ones)
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        g.autotune(list(range(1, len(ch["q"]))), sorted({1, m}), reps=2)
+        table = g.tune_table()
+        tune = {"seconds": round(time.perf_counter() - t0, 2), "entries": len(table),
+                "keys": "(op, limbs, n_ct) for levels 1..%d and n_ct in %s" % (len(ch["q"]) - 1, sorted({1, m})),
+                "non_default": [e for e in table if e["choice"] != (1 if e["n_ct"] <= 4 else 0)]}
     x = attention_logits(L, n, seed=seeds["inputs"])
-    src = g.encrypt(x, n, m, pl["M"], seeds["encrypt"])
+    src = g.encrypt(x, n, m, M, seeds["encrypt"])
     work = g.like(src)
 
-    def step(batched, graph=None):
+    def step(batched, graph=None, plan=None):
         # batched steps replay the circuit captured as one CUDA graph (captured in the first
         # warm-up step); plain steps run the per-ciphertext operation list eagerly
         work.tensor.copy_(src.tensor)  # (on torch's stream of `stream` below)
         work.level, work.scale, work.n_ct = src.level, src.scale, src.n_ct
-        g.softmax(work, pl, batched=batched, graph=batched if graph is None else graph)
+        g.softmax(work, plan or pl, batched=batched, graph=batched if graph is None else graph)
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def fp64_softmax(xx):
+        e = np.exp(xx - xx.max(axis=1, keepdims=True))
+        return e / e.sum(axis=1, keepdims=True)
+
     with torch.cuda.stream(stream):
-        # the profiled family's events are captured into the graph in the first warm-up step
-        g.profile_kernel(args.profile_kernel)
+        # the headline graph carries no timing events (captured in the first warm-up step)
+        g.profile_kernel("")
         for _ in range(args.warmup):
             step(True)
         torch.cuda.synchronize(dev)
         # precision check of the warm-up output (FP64 Softmax of the same inputs)
-        y = g.decrypt(work, n)
-        e = np.exp(x - x.max(axis=1, keepdims=True))
-        err = float(np.abs(y - e / e.sum(axis=1, keepdims=True)).max())  # vs FP64 Softmax
+        err = float(np.abs(g.decrypt(work, n) - fp64_softmax(x)).max())
         c0 = g.counters()
         l0 = g.launch_count()
-        g.profile_read()  # drop the warm-up timings
         clocks = ClockSampler(local)
         clocks.start()
         barrier()
@@ -418,11 +524,35 @@ def main():
         clk = clocks.stop()
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
-        k_ms, k_launch, k_bytes = g.profile_read()
-        g.profile_kernel("")
         c1 = g.counters()
         launches = g.launch_count() - l0
         ks_per_step = (c1["ks"] - c0["ks"]) // args.steps
+        bts_per_step = (c1["bts"] - c0["bts"]) // args.steps
+        # roofline pass: the same steps on a second buffer, whose graph carries CUDA events around
+        # every launch of the profiled kernel family (the events cost time, so the headline above
+        # is taken without them)
+        work2 = g.like(src)
+
+        def step_prof():
+            work2.tensor.copy_(src.tensor)
+            work2.level, work2.scale, work2.n_ct = src.level, src.scale, src.n_ct
+            g.softmax(work2, pl, graph=True)
+
+        g.profile_kernel(args.profile_kernel)
+        step_prof()   # eager run + capture with the events inside
+        step_prof()
+        barrier()
+        g.profile_read()  # drop the capture-time timings
+        evp = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        evp[0].record(stream)
+        for _ in range(args.steps):
+            step_prof()
+        evp[1].record(stream)
+        barrier()
+        prof_ms_step = evp[0].elapsed_time(evp[1]) / args.steps
+        k_ms, k_launch, k_bytes = g.profile_read()   # the last replay's events
+        g.profile_kernel("")
+        del work2
         # plain mode: the same operation list one ciphertext at a time
         plain_ms = None
         if not args.no_plain:
@@ -434,27 +564,46 @@ def main():
             t[1].record(stream)
             barrier()
             plain_ms = t[0].elapsed_time(t[1])
-        # per-family breakdown of one more (untimed) step: CUDA events around every launch
-        breakdown = None
+        # per-family and per-phase breakdown of one more (untimed) step: CUDA events around every launch
+        breakdown, phases = None, None
         if not args.no_breakdown:
             g.profile_kernel("all")
             step(True, graph=False)
-            breakdown = {}
+            breakdown, phases = {}, {}
             for fam, (nl, ms, b) in g.profile_breakdown().items():
+                if fam.startswith("phase:"):
+                    phases[fam[6:]] = {"launches": nl, "ms": round(ms, 3)}
+                    continue
                 breakdown[fam] = {"launches": nl, "ms": round(ms, 3)}
                 if b > 0 and ms > 0:
                     breakdown[fam]["gbs"] = round(b / (ms * 1e-3) / 1e9, 1)
             g.profile_kernel("")
-        # e2e: pinned host ciphertexts in, results out, through he_softmax
+        # the other method on the same batch: graph replays, one timed step
+        other_line = None
+        if not args.no_other:
+            step(True, plan=pl_other)
+            step(True, plan=pl_other)
+            barrier()
+            to = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            co0 = g.counters()
+            to[0].record(stream)
+            step(True, plan=pl_other)
+            to[1].record(stream)
+            barrier()
+            co1 = g.counters()
+            eo = float(np.abs(g.decrypt(work, n) - fp64_softmax(x)).max())
+            other_line = {"method": METHODS[other][1], "ms_per_softmax": to[0].elapsed_time(to[1]) / L,
+                          "precision_bits_vs_fp64": bits(eo), "key_switches_per_step": co1["ks"] - co0["ks"],
+                          "bootstrappings_per_step": co1["bts"] - co0["bts"]}
+        # e2e: pinned host ciphertexts in, results out, through he_softmax (every timed step)
         host_in = torch.empty_like(src.tensor, device="cpu").pin_memory()
         host_in.copy_(src.tensor)
         host_out = torch.empty_like(src.tensor, device="cpu").pin_memory()
         barrier()
         te = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         te[0].record(stream)
-        e2e_steps = max(1, min(args.steps, 2))
         out_words = 0
-        for _ in range(e2e_steps):
+        for _ in range(args.steps):
             work.tensor.copy_(host_in, non_blocking=True)
             work.level, work.scale, work.n_ct = src.level, src.scale, src.n_ct
             g.softmax(work, pl, batched=True, graph=True)
@@ -462,7 +611,25 @@ def main():
             host_out[:out_words].copy_(work.tensor[:out_words], non_blocking=True)
         te[1].record(stream)
         barrier()
-        e2e_ms = te[0].elapsed_time(te[1]) / e2e_steps
+        e2e_ms = te[0].elapsed_time(te[1]) / args.steps
+        # e2e from FP64 inputs to FP64 outputs in host memory: he_encrypt, he_softmax, he_decrypt
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.encrypt(x, n, m, M, seeds["encrypt"], out=work)
+            g.softmax(work, pl, batched=True, graph=True)
+            y_host = g.decrypt(work, n)
+        barrier()
+        xy_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        # precision over seeds 0-4 and the three input recipes (graph replays on the same buffer)
+        prec_runs, prec_err = [], {}
+        for sd in range(args.precision_seeds):
+            for rname, xx in recipes(L, n, 100 + sd, M).items():
+                g.encrypt(xx, n, m, M, 500 + sd, out=work)
+                g.softmax(work, pl, batched=True, graph=True)
+                yy = g.decrypt(work, n)
+                prec_err.setdefault(rname, []).append(float(np.abs(yy - fp64_softmax(xx)).max()))
+                prec_runs.append((xx, yy))
         # latency of one Softmax call on a single ciphertext (128 Softmax of dim 256): graph
         # replays, each timed with CUDA events (p50 / p99 over the repeats)
         lat1 = None
@@ -470,7 +637,7 @@ def main():
             g.keygen_softmax(n, 1)
         if args.latency_repeats > 0:
             x1 = attention_logits(g.n0 // n, n, seed=seeds["inputs"] + 1000)
-            src1 = g.encrypt(x1, n, 1, pl["M"], seeds["encrypt"] + 1000)
+            src1 = g.encrypt(x1, n, 1, M, seeds["encrypt"] + 1000)
             work1 = g.like(src1)
 
             def one():
@@ -498,8 +665,7 @@ def main():
         split = None
         if not args.no_split:
             rows = g.n0 // n
-            parts = [g.encrypt(x[i * rows:(i + 1) * rows], n, 1, pl["M"], seeds["encrypt"] + 2000 + i)
-                     for i in range(m)]
+            parts = [g.encrypt(x[i * rows:(i + 1) * rows], n, 1, M, seeds["encrypt"] + 2000 + i) for i in range(m)]
             ssrc = he.Ciphertexts(g, torch.cat([p_.tensor for p_ in parts]), parts[0].level, parts[0].scale, m)
             del parts
             swork = g.like(ssrc)
@@ -521,22 +687,18 @@ def main():
             for i in range(m):
                 one_ct = he.Ciphertexts(g, swork.tensor[i * w1:(i + 1) * w1], swork.level, swork.scale, 1)
                 yi = g.decrypt(one_ct, n)
-                xi = x[i * rows:(i + 1) * rows]
-                ei = np.exp(xi - xi.max(axis=1, keepdims=True))
-                serr = max(serr, float(np.abs(yi - ei / ei.sum(axis=1, keepdims=True)).max()))
+                serr = max(serr, float(np.abs(yi - fp64_softmax(x[i * rows:(i + 1) * rows])).max()))
             split = {"workload": "%d one-ciphertext problems of %d Softmax (split packing)" % (m, rows),
-                     "grouped_ms_per_softmax": ts_[0].elapsed_time(ts_[1]) / L,
-                     "precision_bits_vs_fp64": -math.log2(serr) if serr > 0 else None}
+                     "grouped_ms_per_softmax": ts_[0].elapsed_time(ts_[1]) / L, "precision_bits_vs_fp64": bits(serr)}
             if lat1:
                 # one problem at a time: the single-ciphertext latency times m, per Softmax
                 split["sequential_ms_per_softmax"] = lat1["p50_ms"] * m / L
             del ssrc, swork
 
-    ms_step, e2e_ms = shard.max_over_ranks([total_ms / args.steps, e2e_ms], dist)
+    ms_step, e2e_ms, xy_ms = shard.max_over_ranks([total_ms / args.steps, e2e_ms, xy_ms], dist)
     if rank != 0:
         return
-    per_softmax = ms_step / L  # each rank processes L Softmax; value is whole-job (weak scaling)
-    value = ms_step / (L * world)
+    value = ms_step / (L * world)   # each rank processes L Softmax; value is whole-job (weak scaling)
     hbm, peak_kind = peaks()
     roof = None
     if k_launch:
@@ -546,30 +708,54 @@ def main():
                 "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
                 # graph replays: the events inside the graph hold the last timed step
                 "launches_per_step": k_launch, "kernel_ms_per_step": k_ms,
-                "share_of_step": k_ms / ms_step, "timed": "CUDA events inside the captured graph, last timed step"}
+                "share_of_step": k_ms / prof_ms_step, "profiled_ms_per_step": prof_ms_step,
+                "timed": "CUDA events inside a second captured graph of the same step, its last replay of %d"
+                         % args.steps}
+        if args.profile_kernel == "ntt":
+            roof["int_pipes"] = NTT_INT_PIPES
+    all_err = [e for v in prec_err.values() for e in v]
+    precision = {"gate_bits": 15, "vs": "FP64 Softmax, max |error| per run",
+                 "seeds": list(range(100, 100 + args.precision_seeds)), "total": stats_bits(all_err),
+                 "by_recipe": {k: stats_bits(v) for k, v in prec_err.items()},
+                 "all_runs_pass_gate": all(e < 2 ** -15 for e in all_err)}
     line = {
         "metric": METRIC, "value": value, "unit": "ms/Softmax", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
-        "config": {"workload": wl["workload"], "n": n, "m": m, "softmax_per_step": L * world, "M": pl["M"],
-                   "k": pl["k"], "log_qp": round(ch["log_qp"], 2), "h": ch["h"],
+        "config": {"workload": wl["workload"], "n": n, "m": m, "softmax_per_step": L * world, "M": M,
+                   "k": pl["k"], "method": METHODS[args.method][1], "log_qp": round(ch["log_qp"], 2), "h": ch["h"],
                    "l2": "inputs 1.7 GB + evaluation keys > 12 GB per step, larger than L2 (no flush)"},
         "p50_ms_per_step": statistics.median(per), "p99_ms_per_step": max(per),
         "plain_ms_per_softmax": (plain_ms / L) if plain_ms else None,
         "batched_speedup_vs_plain": (plain_ms / ms_step) if plain_ms else None,
-        "precision_bits_vs_fp64": -math.log2(err) if err > 0 else None,
+        "precision_bits_vs_fp64": bits(err),
+        "precision": precision,
         "key_switches_per_step": ks_per_step,
+        "bootstrappings_per_step": bts_per_step,
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
         "breakdown_one_step": breakdown,
+        "phase_ms_one_step": phases,
+        "other_method": other_line,
+        "autotune": tune,
         "single_ct_latency": lat1,
         "split_packing": split,
         "e2e": {"value": e2e_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": src.tensor.numel() * 8,
-                "d2h_bytes_per_step": out_words * 8},
+                "d2h_bytes_per_step": out_words * 8,
+                "path": "pinned host ciphertexts -> he_softmax_graph -> host ciphertexts, every timed step"},
+        "e2e_x_to_y": {"value": xy_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": x.size * 8,
+                       "d2h_bytes_per_step": y_host.size * 8,
+                       "path": "host FP64 x -> he_encrypt -> he_softmax_graph -> he_decrypt -> host FP64 y, "
+                               "every timed step (host wall clock)"},
     }
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(ks_per_step, 1.0 / L)
+        line["cpu_baseline"]["full_toy_softmax"] = cpu_full_toy_softmax()
+        split_err = cpu_simulation(prec_runs, pl)
+        precision["approx"] = stats_bits([a for a, _ in split_err])
+        precision["noise"] = stats_bits([b for _, b in split_err])
+        precision["split"] = "approx: oracle FP64 simulation of the circuit vs FP64 Softmax; noise: decryption vs that simulation"
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -146,6 +146,38 @@ int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int
  * while its graph may be launched. */
 int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts);
 
+/* ---- Alg. 4 split over shares of the m main-thread ciphertexts (Sec. 4.2, Alg. 3 Step 1) ----
+ * For running one many-ciphertext batch on several devices: every device holds a share (a
+ * contiguous run of the m ciphertexts of the packing) and a copy of the keys; the one exchange
+ * per round is the sum of squares, an elementwise integer sum of the shares' tensors (exact in
+ * uint64 for up to 16 shares, since residues are below 2^60); the auxiliary thread then runs on
+ * every device with identical results.  The same calls in the order
+ *   he_softmax_share_exp (each share);
+ *   for j = 1 .. k: he_softmax_share_square_sum (each share, from y0 in round 1, else from the
+ *     previous round's ys), sum the d's, he_softmax_aux_round, he_softmax_share_update (each share)
+ * give every share exactly the ciphertexts he_softmax (Alg. 4, batched) gives those ciphertexts of
+ * the whole batch.  Alg. 4 plans and bootstrapping contexts only (HE_EINVAL otherwise).
+ *
+ * exp: the share's ciphertexts (at user_top_level, scale (2/M) q_top, as from he_encrypt) are
+ * replaced by y0 = P_exp(2x/M + 1) (stored compactly at the lower level; level/scale written). */
+int he_softmax_share_exp(he_ctx *ctx, const he_softmax_plan *plan, he_ct *share);
+/* d (device, [3][ys->level+1][N] words, NTT form, residues in [0, q_i)): the sum over the share's
+ * ciphertexts of y (x) y. */
+int he_softmax_share_square_sum(he_ctx *ctx, const he_ct *ys, uint64_t *d);
+/* Auxiliary thread of round j (1 .. k) for m_total ciphertexts in all: d_sum (device) is the
+ * elementwise integer sum of every share's d (words below 16 q_i; reduced here), taken from
+ * ciphertexts at `level` with scale y_scale; y0_level / y0_scale are those of y0 (from
+ * he_softmax_share_exp).  lam: Lambda = lambda_1 ... lambda_j, one ciphertext, written in round 1
+ * and read and rewritten after (caller-allocated, 2 (user_top_level+1) N words); lr: the
+ * replicated Lambda that the main thread multiplies by (written; same size). */
+int he_softmax_aux_round(he_ctx *ctx, const he_softmax_plan *plan, int j, int m_total, const uint64_t *d_sum,
+                         int level, double y_scale, int y0_level, double y0_scale, he_ct *lam, he_ct *lr);
+/* Main thread of round j: ys = (lr y0)^(2^j) for every ciphertext of the share (y0 from
+ * he_softmax_share_exp; ys caller-allocated, another buffer of at least y0's size; level/scale
+ * written).  After round k, ys holds the share's Softmax outputs. */
+int he_softmax_share_update(he_ctx *ctx, const he_softmax_plan *plan, int j, const he_ct *lr, const he_ct *y0,
+                            he_ct *ys);
+
 /* ---- the hot-path operations, one call each ----
  * Common to the calls below: ciphertext batches are he_ct device buffers as above; a result
  * is formed in library-owned scratch and copied to out->data (caller-allocated, at least
@@ -226,6 +258,32 @@ int he_bootstrap(he_ctx *ctx, const he_ct *a, double gain, double out_scale, he_
 /* ModRaise (bootstrapping's first step): a level-0 batch reinterpreted modulo q_0 ... q_top
  * (centred lift).  HE_EINVAL unless a is at level 0 and top < n_q. */
 int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
+
+/* ---- autotuner: launch strategies (no counterpart in the paper; every variant gives the same
+ * words, so results do not depend on the choices) ----
+ * op: HE_TUNE_MODUP (1: all digits of a ModUp converted in one launch and transformed in one
+ * more; 0: per digit), HE_TUNE_ROT (1: the key switches of several hoisted rotations in one
+ * inner-product launch and one ModDown; 0: one per rotation), HE_TUNE_LT_SMALL (1: one ModUp of all
+ * giant-step sums of a bootstrapping linear-transform level; 0: one per giant step),
+ * HE_TUNE_LT_ROWS (1: linear-transform inner sums without shared-memory staging; 0: staged).
+ * Without a table entry the choice is 1 for batches of at most 4 ciphertexts (8 rows for
+ * HE_TUNE_LT_ROWS).
+ * he_autotune times both variants of every operation on the device (CUDA events on the context
+ * stream, the best of reps runs after one warm-up) for ciphertexts at each of the n_levels levels and
+ * each of the n_ncts batch sizes, on uniformly random residues, and keeps the faster one per
+ * (operation, level + 1 limbs, batch size).  Rotation and linear-transform variants are timed
+ * only in bootstrapping contexts, at the SlotToCoeff / CoeffToSlot levels.  Needs he_keygen first
+ * (HE_ENOKEY).  Synchronises. */
+#define HE_TUNE_MODUP 0
+#define HE_TUNE_ROT 1
+#define HE_TUNE_LT_SMALL 2
+#define HE_TUNE_LT_ROWS 3
+int he_autotune(he_ctx *ctx, const int *levels, int n_levels, const int *ncts, int n_ncts, int reps);
+/* the table as text, one line "op limbs n_ct choice ms_variant0 ms_variant1" per entry, into buf
+ * (len bytes, NUL-terminated; HE_EINVAL if too small) */
+int he_tune_table(const he_ctx *ctx, char *buf, size_t len);
+/* forces variant choice (0 or 1) of op everywhere, or restores the table with choice = -1 */
+int he_tune_force(he_ctx *ctx, int op, int choice);
 
 /* operation counters since creation: [ciphertext key switches (a batched key switch over n
  * ciphertexts counts n), rotation calls, hmult calls, rescale calls, bootstrapping calls] */

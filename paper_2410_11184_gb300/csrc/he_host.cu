@@ -133,6 +133,14 @@ struct he_ctx {
     std::map<std::string, SmGraph> graphs;  // captured Softmax circuits (he_softmax_graph)
     bool capturing = false;
     uint64_t *noalloc_scratch = nullptr;   // device address of g_rescale_scratch on this device
+    // launch-strategy choices of the autotuner (he_autotune): (operation, limbs, ciphertexts) ->
+    // variant; tune_force[op] >= 0 overrides the table (tests); every variant gives the same words
+    struct TuneRec {
+        int choice;
+        float ms[2];
+    };
+    std::map<std::tuple<int, int, int>, TuneRec> tune;
+    int tune_force[4] = {-1, -1, -1, -1};
     cudaStream_t st = nullptr;
     std::string err;
     long cnt[5] = {0, 0, 0, 0, 0};
@@ -252,6 +260,22 @@ static DPtr dalloc(he_ctx *c, size_t words) {
 static dim3 grid_for(he_ctx *c, long total) {
     long b = (total + 255) / 256;
     return dim3((unsigned)std::max(1L, std::min(b, (long)c->max_grid)));
+}
+
+// ------------------------------------------------------------------------- launch strategies
+// Bit-identical alternatives the autotuner chooses between, per (operation, limbs, ciphertexts):
+//   HE_TUNE_MODUP     1: every digit of the ModUp converted in one launch and transformed in one
+//                     more; 0: one conversion and two transforms per digit
+//   HE_TUNE_ROT       1: the key switches of several hoisted rotations in one inner-product launch
+//                     and one ModDown over all; 0: one key switch per rotation
+//   HE_TUNE_LT_SMALL  1: one ModUp of every giant-step sum of a linear-transform level and one
+//                     launch summing their inner products; 0: a ModUp per giant step
+//   HE_TUNE_LT_ROWS   1: inner sums without shared-memory staging; 0: staged diagonal tiles
+// Defaults (no table entry): 1 for batches of at most 4 ciphertexts (8 rows for LT_ROWS).
+static int tune_pick(he_ctx *c, int op, int L, int nct, int dflt) {
+    if (c->tune_force[op] >= 0) return c->tune_force[op];
+    auto it = c->tune.find(std::make_tuple(op, L, nct));
+    return it == c->tune.end() ? dflt : it->second.choice;
 }
 
 // ------------------------------------------------------------------------- limb maps
@@ -485,7 +509,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true, "ntt_modup", x, sx);
     DPtr dig = dalloc(c, (size_t)nct * nd * nl * c->N);
     LimbMap em = extmap(c, L);
-    if (nct <= 4) {
+    if (tune_pick(c, HE_TUNE_MODUP, L, nct, nct <= 4)) {
         // small batches: every digit converted in one launch and transformed in one more (the
         // per-digit launches would each fill a fraction of the GPU); the digit's own limbs are
         // converted too, which reproduces them exactly
@@ -725,7 +749,7 @@ static std::vector<DCt> rotate_hoisted(he_ctx *c, const DCt &x, const std::vecto
     std::vector<int> gs;
     for (int g : gal)
         if (g != 1) gs.push_back(g);
-    if (x.nct <= 4 && gs.size() >= 2 && gs.size() <= 16) {
+    if (gs.size() >= 2 && gs.size() <= 16 && tune_pick(c, HE_TUNE_ROT, L, x.nct, x.nct <= 4)) {
         // small batches: the key switches of all rotations in one inner-product launch and one
         // ModDown over all of them (each separately would fill a fraction of the GPU)
         int al = c->alpha, nd = (L + al - 1) / al, nl = L + al, ng = (int)gs.size();
@@ -1347,7 +1371,7 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
     int na_max = 0;
     for (size_t pi = 0; pi < Lv.pts.size(); pi++)
         if (pi == 0 || Lv.pts[pi].a != Lv.pts[pi - 1].a) na_max++;
-    const bool small = x.nct <= 4 && na_max >= 3;
+    const bool small = na_max >= 3 && na_max <= 17 && tune_pick(c, HE_TUNE_LT_SMALL, L, x.nct, x.nct <= 4);
     DPtr innerbuf = small ? dalloc(c, (size_t)na_max * x.nct * x.cs(c)) : DPtr();
     std::vector<int> gi;
     std::vector<DCt> inner;
@@ -1380,7 +1404,7 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         dim3 grid((unsigned)std::min<long>(tiles, c->max_grid / 4), 1);
         size_t smem = (size_t)A.npt * HE_LT_KT * 8;
         ProfScope ps_(c, "lintrans", 8.0 * c->N * ((double)L * A.npt + (double)x.nct * 2 * L * (A.nb + A.na)));
-        if (2 * x.nct <= 8)   // a few rows: no staging (a staged tile would serve only these rows)
+        if (tune_pick(c, HE_TUNE_LT_ROWS, L, x.nct, 2 * x.nct <= 8))   // a few rows: no staging
             k_lt_bsgs_direct<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods,
                                                                                  c->logN);
         else
@@ -1572,9 +1596,9 @@ static void dbg_dump(he_ctx *c, const char *what, int j, const DCt &x) {
     fclose(f);
 }
 
-// S = Relin(sum_c y_c (x) y_c), relinearised and rescaled (one sum per group): ys holds the m
+// sum_c y_c (x) y_c (degree 2, [G][3][level+1][N], NTT form, one sum per group): ys holds the m
 // main-thread ciphertexts as one batch (or m batches of one); with G > 1 ys[0] holds G groups
-static DCt square_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
+static DPtr tensor_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
     int ly = ys[0].level;
     int L = ly + 1;
     DPtr d = dalloc(c, (size_t)G * 3 * L * c->N);
@@ -1628,10 +1652,20 @@ static DCt square_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
             first = false;
         }
     }
+    return d;
+}
+
+// S = Relin(sum_c y_c (x) y_c) rescaled, from the tensor sum d of ciphertexts at `level` and scale ys
+static DCt relin_sum(he_ctx *c, const uint64_t *d, int level, int G, double ys) {
     PhaseScope pa(c, "aux");    // one relinearisation of the sum
-    DCt S = relin_rescale(c, d.get(), ly, G, ys[0].scale * ys[0].scale);
+    DCt S = relin_rescale(c, d, level, G, ys * ys);
     c->cnt[2]++;
     return S;
+}
+
+static DCt square_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
+    DPtr d = tensor_sum(c, ys, m, G);
+    return relin_sum(c, d.get(), ys[0].level, G, ys[0].scale);
 }
 
 // ys: the m main-thread ciphertexts, as one batch (batched) or m batches of one; with G > 1
@@ -1787,62 +1821,80 @@ static const uint64_t *mask_pt(he_ctx *c, int stride, int level, double mval, do
     return mit->second.get();
 }
 
+// Alg. 4, main thread before the rounds: u = 2x/M + 1, y0 = P_exp(u) at level ly0 with scale
+// sqrt(Delta q_ly0), so that S_1 = sum y0^2 lands at Delta
+static int alg4_ly0(he_ctx *c, const Plan &p, int level_in) { return level_in - ilog2c(p.exp_deg + 1); }
+
+static void alg4_exp(he_ctx *c, const Plan &p, std::vector<DCt> &ys) {
+    PhaseScope ph(c, "main");
+    double delta = std::ldexp(1.0, c->log_scale);
+    int ly0 = alg4_ly0(c, p, ys[0].level);
+    for (auto &y : ys) {
+        affine_to_unit(c, y, -p.M, 0.0);
+        y = poly_eval(c, y, p.exp_c, ly0, sqrt(delta * qd(c, ly0)));
+    }
+}
+
+// Alg. 4, auxiliary thread of round j (1-based), from the relinearised sum of squares S (G groups,
+// before the rotate-and-sum) of the m main-thread ciphertexts per group: returns lr, the
+// replicated (mask, rotate-and-sum) product of Lambda = lambda_1 ... lambda_j, and updates lam_c
+// (Lambda; have_lam false before round 1).  y0_scale: the scale of y0; ly0: its level.
+static DCt alg4_aux(he_ctx *c, const Plan &p, int j, DCt S, int m, int ly0, double y0_scale, DCt &lam_c,
+                    bool &have_lam) {
+    PhaseScope ph_aux(c, "aux");
+    const int jj = j - 1;   // plan index
+    int n0 = c->n0, stride = (int)((long)m * n0 / p.n), nrot = ilog2c(p.n / m), top = c->user_top;
+    double delta = std::ldexp(1.0, c->log_scale);
+    S = rotsum(c, S, stride, nrot);
+    double a = p.a[jj], b = p.b[jj];
+    DCt v = bts_boosted(c, p, S, p.gs[jj], (2.0 / (b - a)) * qd(c, top));
+    affine_to_unit(c, v, a, b);
+    std::vector<double> cf = p.inv_c[jj];
+    double g = pow(p.gs[jj], p.expo[jj]);
+    for (auto &x : cf) x = x * g;
+    int dj = ilog2c((int)cf.size());
+    int lp = top - dj;
+    DCt lam = lp < c->bts_min ? split_eval(c, p, v, cf, dj, delta, p.b_max[jj]) : poly_eval(c, v, cf, lp, delta);
+    double lmax = p.lam_max[jj];
+    int lam_lv = have_lam ? lam_c.level : top;
+    DCt lb = bts_boosted(c, p, lam, 1.0 / lmax, qd(c, lam_lv) * lmax);
+    lb.scale = lb.scale / lmax;           // lambda_j at scale q_(lam_lv)
+    lam_c = have_lam ? hmult(c, lam_c, lb) : lb;
+    have_lam = true;
+    // where z lands and the scale it needs there: j squarings, then (j < k) one more for S
+    int lz = ly0 - 1;
+    double sz = delta;
+    for (int i = (j == p.k ? j : j + 1); i >= 1; i--) sz = sqrt(sz * qd(c, lz - i + 1));
+    double s_lr = (sz * qd(c, ly0)) / y0_scale;
+    double sm = (s_lr * qd(c, lam_c.level)) / lam_c.scale;
+    DCt lr = ct_copy(c, lam_c);
+    ct_mul_plain(c, lr, mask_pt(c, stride, lam_c.level, 1.0, sm));
+    lr.scale = lr.scale * sm;
+    return rotsum(c, rescale(c, lr), stride, nrot);
+}
+
+// Alg. 4, main thread of round j: y^(j)_c = (lr y0_c)^(2^j) (j squarings)
+static void alg4_update(he_ctx *c, int j, const DCt &lr, const std::vector<DCt> &y0, std::vector<DCt> &ys, int m, int G) {
+    PhaseScope ph_main(c, "main");
+    for (size_t i = 0; i < ys.size(); i++) {
+        DCt z = G > 1 && m > 1 ? hmult_grouped(c, lr, y0[i], m) : hmult(c, lr, y0[i]);
+        for (int t = 0; t < j; t++) z = hmult(c, z, z);
+        ys[i] = z;
+    }
+}
+
 static std::vector<DCt> softmax_run_b(he_ctx *c, const Plan &p, std::vector<DCt> ys, int m, int G = 1) {
     REQUIRE(G == 1 || (ys.size() == 1 && ys[0].nct == G * m), HE_EINVAL, "softmax: groups need one batch");
     REQUIRE(c->bootstrap, HE_EINVAL, "Alg. 4 needs bootstrapping");
-    int n0 = c->n0, n = p.n;
-    int stride = (int)((long)m * n0 / n);
-    int nrot = ilog2c(n / m);
-    int top = c->user_top;
-    double delta = std::ldexp(1.0, c->log_scale);
-    int ly0 = ys[0].level - ilog2c(p.exp_deg + 1);
-    {
-        PhaseScope ph(c, "main");
-        for (auto &y : ys) {
-            affine_to_unit(c, y, -p.M, 0.0);
-            y = poly_eval(c, y, p.exp_c, ly0, sqrt(delta * qd(c, ly0)));
-        }
-    }
+    alg4_exp(c, p, ys);
     const std::vector<DCt> y0 = ys;
-    const double y0_scale = y0[0].scale;
+    const int ly0 = y0[0].level;
     DCt lam_c;
     bool have_lam = false;
     for (int j = 1; j <= p.k; j++) {
-        const int jj = j - 1;   // plan index
         DCt S = square_sum(c, ys, m, G);
-        PhaseScope ph_aux(c, "aux");
-        S = rotsum(c, S, stride, nrot);
-        double a = p.a[jj], b = p.b[jj];
-        DCt v = bts_boosted(c, p, S, p.gs[jj], (2.0 / (b - a)) * qd(c, top));
-        affine_to_unit(c, v, a, b);
-        std::vector<double> cf = p.inv_c[jj];
-        double g = pow(p.gs[jj], p.expo[jj]);
-        for (auto &x : cf) x = x * g;
-        int dj = ilog2c((int)cf.size());
-        int lp = top - dj;
-        DCt lam = lp < c->bts_min ? split_eval(c, p, v, cf, dj, delta, p.b_max[jj]) : poly_eval(c, v, cf, lp, delta);
-        double lmax = p.lam_max[jj];
-        int lam_lv = have_lam ? lam_c.level : top;
-        DCt lb = bts_boosted(c, p, lam, 1.0 / lmax, qd(c, lam_lv) * lmax);
-        lb.scale = lb.scale / lmax;           // lambda_j at scale q_(lam_lv)
-        lam_c = have_lam ? hmult(c, lam_c, lb) : lb;
-        have_lam = true;
-        // where z lands and the scale it needs there: j squarings, then (j < k) one more for S
-        int lz = ly0 - 1;
-        double sz = delta;
-        for (int i = (j == p.k ? j : j + 1); i >= 1; i--) sz = sqrt(sz * qd(c, lz - i + 1));
-        double s_lr = (sz * qd(c, ly0)) / y0_scale;
-        double sm = (s_lr * qd(c, lam_c.level)) / lam_c.scale;
-        DCt lr = ct_copy(c, lam_c);
-        ct_mul_plain(c, lr, mask_pt(c, stride, lam_c.level, 1.0, sm));
-        lr.scale = lr.scale * sm;
-        lr = rotsum(c, rescale(c, lr), stride, nrot);
-        PhaseScope ph_main(c, "main");
-        for (size_t i = 0; i < ys.size(); i++) {
-            DCt z = G > 1 && m > 1 ? hmult_grouped(c, lr, y0[i], m) : hmult(c, lr, y0[i]);
-            for (int t = 0; t < j; t++) z = hmult(c, z, z);
-            ys[i] = z;
-        }
+        DCt lr = alg4_aux(c, p, j, S, m, ly0, y0[0].scale, lam_c, have_lam);
+        alg4_update(c, j, lr, y0, ys, m, G);
     }
     return ys;
 }
@@ -2081,6 +2133,88 @@ static void build_tables(he_ctx *c) {
     REQUIRE(al >= 1 && al <= 8 && c->ndig_top <= 8, HE_EINVAL, "alpha and the digit count must be at most 8");
     // linear-transform inner sums: up to HE_LT_MAXPT staged plaintext tiles of HE_LT_KT words
     CK(cudaFuncSetAttribute(k_lt_bsgs, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_LT_MAXPT * HE_LT_KT * 8));
+}
+
+// ---- autotuner
+// one warm-up run of fn, then the best of reps runs, timed with CUDA events on the context stream
+template <class F>
+static float time_best(he_ctx *c, int reps, F fn) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    fn();
+    float best = 1e30f;
+    for (int r = 0; r < reps; r++) {
+        CK(cudaEventRecord(a, c->st));
+        fn();
+        CK(cudaEventRecord(b, c->st));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+// times variants 0 and 1 of op (forced) with fn and keeps the faster one for (op, L, nct)
+template <class F>
+static void tune_op(he_ctx *c, int op, int L, int nct, int reps, F fn) {
+    he_ctx::TuneRec r;
+    for (int v = 0; v < 2; v++) {
+        c->tune_force[op] = v;
+        r.ms[v] = time_best(c, reps, fn);
+    }
+    c->tune_force[op] = -1;
+    r.choice = r.ms[1] < r.ms[0] ? 1 : 0;
+    c->tune[std::make_tuple(op, L, nct)] = r;
+}
+
+static void autotune(he_ctx *c, const std::vector<int> &levels, const std::vector<int> &ncts, int reps) {
+    REQUIRE(c->have_keys, HE_ENOKEY, "autotune: keygen first");
+    long cnt0[5], l0 = c->launches;
+    for (int i = 0; i < 5; i++) cnt0[i] = c->cnt[i];
+    std::vector<std::string> cached;
+    for (auto &kv : c->lt_cache) cached.push_back(kv.first);
+    for (int lv : levels) {
+        for (int nct : ncts) {
+            int L = lv + 1;
+            DCt x = ct_new(c, lv, nct, 1.0);
+            {
+                ProfScope ps_(c, "keygen", 0);
+                k_sample_uniform<<<grid_for(c, (long)2 * nct * L << c->logN), 256, 0, c->st>>>(
+                    x.d, (long)L * c->N, 2 * nct * L, L, qmap(L), c->d_mods, 0x5eedULL + lv, 0x70e0ULL, c->logN);
+            }
+            LAUNCH_CHECK();
+            tune_op(c, HE_TUNE_MODUP, L, nct, reps, [&] { DPtr d = ks_modup(c, x.d + (long)L * c->N, x.cs(c), nct, L); });
+            if (!c->bootstrap) continue;
+            // the bootstrapping linear-transform level that runs at this level, if any:
+            // SlotToCoeff level g at stc_levels - g, CoeffToSlot level g at the top - g
+            for (int inverse = 0; inverse < 2; inverse++) {
+                int nlev = inverse ? c->cts_levels : c->stc_levels;
+                int g = inverse ? (c->nq - 1) - lv : c->stc_levels - lv;
+                if (g < 0 || g >= nlev) continue;
+                LtDesc d = lt_levels(c, nlev, inverse)[g];
+                const LtLevel &Lv = lt_prepare(c, d, 1.0, qd(c, lv), lv);
+                std::vector<int> gal;
+                for (int b : Lv.baby)
+                    if (b != 0) gal.push_back(galois_for_rot(c, (long)b * Lv.hmin));
+                if (gal.size() >= 2 && gal.size() <= 16)
+                    tune_op(c, HE_TUNE_ROT, L, nct, reps, [&] { std::vector<DCt> r = rotate_hoisted(c, x, gal); });
+                tune_op(c, HE_TUNE_LT_ROWS, L, nct, reps, [&] { DCt r = lt_eval_level(c, x, d, 1.0, qd(c, lv)); });
+                tune_op(c, HE_TUNE_LT_SMALL, L, nct, reps, [&] { DCt r = lt_eval_level(c, x, d, 1.0, qd(c, lv)); });
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(c->st));
+    // the tuner's own work is not counted, and its diagonal encodings are dropped
+    for (auto it = c->lt_cache.begin(); it != c->lt_cache.end();) {
+        if (std::find(cached.begin(), cached.end(), it->first) == cached.end()) it = c->lt_cache.erase(it);
+        else ++it;
+    }
+    for (int i = 0; i < 5; i++) c->cnt[i] = cnt0[i];
+    c->launches = l0;
 }
 
 // ------------------------------------------------------------------------- C ABI
@@ -2527,6 +2661,91 @@ int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts) {
     API_END
 }
 
+// ---- Alg. 4 split over shares of the main-thread ciphertexts (one share per device)
+static int share_plan_check(he_ctx *ctx, const he_softmax_plan *plan, int m_total) {
+    if (!ctx || !plan || plan->k < 1 || plan->k > 16 || plan->method != HE_SOFTMAX_ALG4 || !plan->exp_coeffs ||
+        !plan->inv_deg || !plan->inv_coeffs || !plan->inv_a || !plan->inv_b || !plan->gain_s || !plan->exponent ||
+        !plan->lam_max || !plan->b_max)
+        return HE_EINVAL;
+    int n = plan->n;
+    if (m_total < 1 || n < 1 || (n & (n - 1)) || n % m_total || ctx->n0 % n || !ctx->bootstrap) {
+        ctx->err = "split Softmax: Alg. 4 plan, a bootstrapping context, n a power of two dividing N/2 and m | n";
+        return HE_EINVAL;
+    }
+    return HE_OK;
+}
+
+static void put_compact(he_ctx *ctx, const DCt &y, he_ct *out) {
+    CK(cudaMemcpyAsync(out->data, y.d, (size_t)y.nct * y.cs(ctx) * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    out->level = y.level;
+    out->scale = y.scale;
+    out->n_ct = y.nct;
+}
+
+int he_softmax_share_exp(he_ctx *ctx, const he_softmax_plan *plan, he_ct *share) {
+    int rc = share_plan_check(ctx, plan, 1);
+    if (rc) return rc;
+    if (!share || !share->data) return HE_EINVAL;
+    API_BEGIN
+    Plan p = plan_of(ctx, plan);
+    std::vector<DCt> ys{ct_copy(ctx, ct_view(ctx, share))};
+    alg4_exp(ctx, p, ys);
+    put_compact(ctx, ys[0], share);
+    API_END
+}
+
+int he_softmax_share_square_sum(he_ctx *ctx, const he_ct *ys, uint64_t *d) {
+    if (!ctx || !ys || !d) return HE_EINVAL;
+    API_BEGIN
+    DCt y = ct_view(ctx, ys);
+    DPtr t = tensor_sum(ctx, std::vector<DCt>{y}, y.nct, 1);
+    CK(cudaMemcpyAsync(d, t.get(), (size_t)3 * (y.level + 1) * ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    API_END
+}
+
+int he_softmax_aux_round(he_ctx *ctx, const he_softmax_plan *plan, int j, int m_total, const uint64_t *d_sum,
+                         int level, double y_scale, int y0_level, double y0_scale, he_ct *lam, he_ct *lr) {
+    int rc = share_plan_check(ctx, plan, m_total);
+    if (rc) return rc;
+    if (!d_sum || !lam || !lam->data || !lr || !lr->data || j < 1 || j > plan->k || level < 1 || level >= ctx->nq ||
+        y0_level < 1 || y0_level >= ctx->nq)
+        return HE_EINVAL;
+    API_BEGIN
+    Plan p = plan_of(ctx, plan);
+    int L = level + 1;
+    DPtr dr = dalloc(ctx, (size_t)3 * L * ctx->N);
+    {
+        ProfScope ps_(ctx, "elementwise", 0);
+        k_reduce_limbs<<<grid_for(ctx, (long)3 * L << ctx->logN), 256, 0, ctx->st>>>(dr.get(), d_sum, 3 * L, L, qmap(L),
+                                                                                   ctx->d_mods, ctx->logN);
+    }
+    he_ctx *c = ctx;
+    LAUNCH_CHECK();
+    DCt S = relin_sum(ctx, dr.get(), level, 1, y_scale);
+    DCt lam_c;
+    bool have_lam = j > 1;
+    if (have_lam) lam_c = ct_view(ctx, lam);
+    DCt out = alg4_aux(ctx, p, j, S, m_total, y0_level, y0_scale, lam_c, have_lam);
+    put_compact(ctx, lam_c, lam);
+    put_compact(ctx, out, lr);
+    API_END
+}
+
+int he_softmax_share_update(he_ctx *ctx, const he_softmax_plan *plan, int j, const he_ct *lr, const he_ct *y0,
+                            he_ct *ys) {
+    int rc = share_plan_check(ctx, plan, 1);
+    if (rc) return rc;
+    if (!lr || !y0 || !ys || !ys->data || j < 1 || j > plan->k) return HE_EINVAL;
+    API_BEGIN
+    DCt l = ct_view(ctx, lr), y = ct_view(ctx, y0);
+    REQUIRE(l.nct == 1, HE_EINVAL, "lr must be one ciphertext");
+    REQUIRE(ys->data != y0->data, HE_EINVAL, "ys must not be y0's buffer");
+    std::vector<DCt> out{y}, in{y};
+    alg4_update(ctx, j, l, in, out, y.nct, 1);
+    put_compact(ctx, out[0], ys);
+    API_END
+}
+
 int he_ntt(he_ctx *ctx, uint64_t *data, int n_poly, int n_limb, int inverse) {
     if (!ctx || !data || n_poly < 1 || n_limb < 1 || n_limb > ctx->nq) return HE_EINVAL;
     API_BEGIN
@@ -2691,6 +2910,37 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out) {
     API_BEGIN
     put_out(ctx, mod_raise(ctx, ct_view(ctx, a), top), out);
     API_END
+}
+
+int he_autotune(he_ctx *ctx, const int *levels, int n_levels, const int *ncts, int n_ncts, int reps) {
+    if (!ctx || !levels || !ncts || n_levels < 1 || n_ncts < 1 || reps < 1) return HE_EINVAL;
+    for (int i = 0; i < n_levels; i++)
+        if (levels[i] < 1 || levels[i] >= ctx->nq) return HE_EINVAL;
+    for (int i = 0; i < n_ncts; i++)
+        if (ncts[i] < 1 || ncts[i] > 4096) return HE_EINVAL;
+    API_BEGIN
+    autotune(ctx, std::vector<int>(levels, levels + n_levels), std::vector<int>(ncts, ncts + n_ncts), reps);
+    API_END
+}
+
+int he_tune_table(const he_ctx *ctx, char *buf, size_t len) {
+    if (!ctx || !buf || len == 0) return HE_EINVAL;
+    std::string out;
+    for (const auto &kv : ctx->tune) {
+        char line[128];
+        snprintf(line, sizeof line, "%d %d %d %d %.4f %.4f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), kv.second.choice, kv.second.ms[0], kv.second.ms[1]);
+        out += line;
+    }
+    if (out.size() >= len) return HE_EINVAL;
+    memcpy(buf, out.c_str(), out.size() + 1);
+    return HE_OK;
+}
+
+int he_tune_force(he_ctx *ctx, int op, int choice) {
+    if (!ctx || op < 0 || op > 3 || choice < -1 || choice > 1) return HE_EINVAL;
+    ctx->tune_force[op] = choice;
+    return HE_OK;
 }
 
 int he_counters(const he_ctx *ctx, long *out5) {

@@ -695,6 +695,17 @@ __global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e,
     }
 }
 
+// x_i mod q_i for `count` limbs of N words (limb l uses modulus map.prime[l % nper]), any uint64
+__global__ void k_reduce_limbs(uint64_t *out, const uint64_t *x, int count, int nper, LimbMap map, const ModC *mods,
+                               int logN) {
+    const long N = 1L << logN, total = (long)count << logN;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(i >> logN);
+        out[i] = reduce_u64(x[i], mods[map.prime[l % nper]]);
+    }
+    (void)N;
+}
+
 // bounded spin used only by the device-wait self test: waits for *flag != 0 at most max_iter
 // polls, then records a timeout in *status (1 = flag seen, 2 = gave up) and returns
 __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter) {

@@ -127,6 +127,8 @@ __global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qm
 __global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
                               Scal pm, int nl, int dlo, int dhi, LimbMap map, const ModC *mods, int logN);
 __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter);
+__global__ void k_reduce_limbs(uint64_t *out, const uint64_t *x, int count, int nper, LimbMap map, const ModC *mods,
+                               int logN);
 
 // key-switching inner product sum_j d~_j swk_j (k_ks_inner_t<ndig>, ndig in 1 .. 8: the key
 // words of a (limb, coefficient) kept in registers); M.n > 0: grid.y key switches of the same digits

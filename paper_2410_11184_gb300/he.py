@@ -87,12 +87,24 @@ def lib():
             "he_bootstrap": [vp, C.POINTER(he_ct), C.c_double, C.c_double, C.POINTER(he_ct)],
             "he_mod_raise": [vp, C.POINTER(he_ct), C.c_int, C.POINTER(he_ct)],
             "he_counters": [vp, C.POINTER(C.c_long)],
+            "he_softmax_share_exp": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct)],
+            "he_softmax_share_square_sum": [vp, C.POINTER(he_ct), vp],
+            "he_softmax_aux_round": [vp, C.POINTER(he_softmax_plan), C.c_int, C.c_int, vp, C.c_int, C.c_double,
+                                     C.c_int, C.c_double, C.POINTER(he_ct), C.POINTER(he_ct)],
+            "he_softmax_share_update": [vp, C.POINTER(he_softmax_plan), C.c_int, C.POINTER(he_ct), C.POINTER(he_ct),
+                                        C.POINTER(he_ct)],
             "he_selftest_bounded_wait": [vp, C.c_long],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = None if name == "he_context_destroy" else C.c_int
+        L.he_autotune.restype = C.c_int
+        L.he_autotune.argtypes = [vp, intp, C.c_int, intp, C.c_int, C.c_int]
+        L.he_tune_table.restype = C.c_int
+        L.he_tune_table.argtypes = [vp, C.c_char_p, C.c_size_t]
+        L.he_tune_force.restype = C.c_int
+        L.he_tune_force.argtypes = [vp, C.c_int, C.c_int]
         L.he_launch_count.restype = C.c_long
         L.he_launch_count.argtypes = [vp]
         L.he_profile_kernel.restype = C.c_int
@@ -254,6 +266,40 @@ class Context:
         cts.update(h)
         return cts
 
+    # ---- Alg. 4 split over shares of the main-thread ciphertexts (one share per device)
+    def softmax_share_exp(self, share, plan):
+        """he_softmax_share_exp: y0 = P_exp(2x/M + 1) in place on the share."""
+        pl = Plan(plan)
+        h = share.c()
+        self.check(lib().he_softmax_share_exp(self.h, C.byref(pl.s), C.byref(h)))
+        share.update(h)
+        return share
+
+    def softmax_share_square_sum(self, ys):
+        """he_softmax_share_square_sum: the share's sum of y (x) y, a device tensor [3][level+1][N]."""
+        d = self.torch.empty(3 * (ys.level + 1) * self.n, dtype=self.torch.int64, device=self.device)
+        h = ys.c()
+        self.check(lib().he_softmax_share_square_sum(self.h, C.byref(h), C.c_void_p(d.data_ptr())))
+        return d
+
+    def softmax_aux_round(self, plan, j, m_total, d_sum, level, y_scale, y0, lam, lr):
+        """he_softmax_aux_round: d_sum is the elementwise integer sum of the shares' d tensors;
+        lam (Lambda, updated) and lr (written) are one-ciphertext buffers at the top user level."""
+        pl = Plan(plan)
+        hl, hr = lam.c(), lr.c()
+        self.check(lib().he_softmax_aux_round(self.h, C.byref(pl.s), j, m_total, C.c_void_p(d_sum.data_ptr()),
+                                              level, y_scale, y0.level, y0.scale, C.byref(hl), C.byref(hr)))
+        lam.update(hl)
+        lr.update(hr)
+
+    def softmax_share_update(self, plan, j, lr, y0, ys):
+        """he_softmax_share_update: ys = (lr y0)^(2^j) for the share."""
+        pl = Plan(plan)
+        hl, hy, ho = lr.c(), y0.c(), ys.c()
+        self.check(lib().he_softmax_share_update(self.h, C.byref(pl.s), j, C.byref(hl), C.byref(hy), C.byref(ho)))
+        ys.update(ho)
+        return ys
+
     def softmax_grouped(self, cts, plan, groups):
         """he_softmax_grouped in place: `groups` independent Softmax batches of
         cts.n_ct / groups ciphertexts each."""
@@ -366,6 +412,29 @@ class Context:
             name, n, ms, b = line.split()
             out[name] = (int(n), float(ms), float(b))
         return out
+
+    # ---- autotuner (launch strategies; every variant gives the same words)
+    TUNE_OPS = ("modup", "rot", "lt_small", "lt_rows")
+
+    def autotune(self, levels, ncts, reps=2):
+        lv = np.ascontiguousarray(levels, dtype=np.int32)
+        nc = np.ascontiguousarray(ncts, dtype=np.int32)
+        self.check(lib().he_autotune(self.h, lv.ctypes.data_as(intp), len(lv), nc.ctypes.data_as(intp), len(nc), reps))
+
+    def tune_table(self):
+        """[{op, limbs, n_ct, choice, ms: [variant 0, variant 1]}] of the autotuner's table"""
+        buf = C.create_string_buffer(1 << 18)
+        self.check(lib().he_tune_table(self.h, buf, len(buf)))
+        out = []
+        for line in buf.value.decode().splitlines():
+            op, L, n, ch, m0, m1 = line.split()
+            out.append({"op": self.TUNE_OPS[int(op)], "limbs": int(L), "n_ct": int(n), "choice": int(ch),
+                        "ms": [float(m0), float(m1)]})
+        return out
+
+    def tune_force(self, op, choice):
+        """forces variant `choice` (0 or 1) of op ("modup", "rot", "lt_small", "lt_rows"); -1 restores"""
+        self.check(lib().he_tune_force(self.h, self.TUNE_OPS.index(op), choice))
 
     def selftest_bounded_wait(self, max_iter):
         return lib().he_selftest_bounded_wait(self.h, max_iter)

@@ -1,8 +1,10 @@
 """Small fixed workloads for Nsight Compute captures (profiles/ summaries name the command).
 
-  python -m paper_2410_11184_gb300.profile_case softmax   # one N=2^16 Softmax of dim 256 (1 ciphertext)
-  python -m paper_2410_11184_gb300.profile_case keyswitch # 4 HMults at level 12, 64 ciphertexts
-                                                         # (inside the NVTX range "hmult")
+  python -m paper_2410_11184_gb300.profile_case softmax       # one N=2^16 Softmax of dim 256 (1 ciphertext),
+                                                              # Alg. 4, inside the NVTX range "softmax"
+  python -m paper_2410_11184_gb300.profile_case softmax_alg2  # the same by Alg. 2
+  python -m paper_2410_11184_gb300.profile_case keyswitch     # 4 HMults at level 12, 64 ciphertexts
+                                                              # (inside the NVTX range "hmult")
 """
 import sys
 
@@ -14,17 +16,22 @@ from paper_2410_11184_gb300 import he, workloads
 
 def main(which):
     chains, plans, evalmod = he.load_params()
-    ch, pl, em = chains["fgb16"], plans["n256_M128"], evalmod["fgb16"]
-    if which != "softmax":
+    ch, em = chains["fgb16"], evalmod["fgb16"]
+    pl = plans["n256_M128"] if which == "softmax_alg2" else he.load_plans_b()["n256_M128_B"]
+    if not which.startswith("softmax"):
         ch = dict(ch, bootstrap=0)  # relinearisation key only: a few GB on the device
         em = None
     g = he.Context(ch, em)
     g.keygen(5)
-    if which == "softmax":
+    if which.startswith("softmax"):
         g.keygen_softmax(256, 1)
         x = workloads.attention_logits(128, 256, 1)
         cts = g.encrypt(x, 256, 1, pl["M"], 3)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("softmax")  # ncu --nvtx --nvtx-include "softmax/" selects these launches
         g.softmax(cts, pl)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     else:
         m = 64
         top = ch["user_top_level"]

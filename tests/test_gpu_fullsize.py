@@ -201,3 +201,48 @@ def test_fullsize_softmax_golden(full, params, name):
     assert _limb_hashes(g.to_coeff(cts)) == gold["out_hash"]
     err = np.abs(g.decrypt(cts, n) - O.softmax_fp64(x)).max()
     assert err < 2 ** -15, -math.log2(err)
+
+
+@pytest.mark.parametrize("plan", ["n128_M64", "n128_M64_B"])
+def test_fullsize_llama_layer_shape_precision(full, params, plan):
+    """The LLaMa-7B per-layer shape (Sec. 5.2.7): one layer = 32 heads x 128 query rows = 4096
+    Softmax of dimension 128 in m = 16 ciphertexts (n/m = 8), logits q.k/sqrt(128) with one
+    sigma ~ U[0.5, 1.5] per head, minus a public bound 16, clipped to [-64, 0]; four layers in
+    one grouped pass, each >= 15 bits against FP64 Softmax, by Alg. 2 and by Alg. 4."""
+    g, ch, em = full
+    pl = he.load_plans_b()[plan] if plan.endswith("_B") else params[1][plan]
+    n, M, m, groups = pl["n"], pl["M"], 16, 4
+    g.keygen_softmax(n, m)
+    L = m * g.n0 // n
+    xs = [workloads.attention_logits(L, n, 900 + i, M=M, d=128, bound=16.0, sigma="per_head", rows_per_head=128)
+          for i in range(groups)]
+    parts = [g.encrypt(x, n, m, M, 950 + i) for i, x in enumerate(xs)]
+    batch = he.Ciphertexts(g, torch.cat([p.tensor for p in parts]), parts[0].level, parts[0].scale, m * groups)
+    del parts
+    g.softmax_grouped(batch, pl, groups)
+    w = m * 2 * (batch.level + 1) * g.n
+    for i, x in enumerate(xs):
+        one = he.Ciphertexts(g, batch.tensor[i * w:(i + 1) * w], batch.level, batch.scale, m)
+        err = np.abs(g.decrypt(one, n) - O.softmax_fp64(x)).max()
+        assert err < 2 ** -15, (plan, i, -math.log2(err))
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_fullsize_large_dimension_alg4_precision(full, n):
+    """Dimensions of the serving mix that Alg. 2 cannot serve on this chain (n = 4096) or
+    serves with little margin (n = 1024): Alg. 4 with one bootstrapping of every lambda_j, on
+    one ciphertext of N0/n Softmax of uniform inputs on [-64, 0], two requests grouped."""
+    g, ch, em = full
+    pl = he.load_plans_b()["n%d_M64_B" % n]
+    M = pl["M"]
+    g.keygen_softmax(n, 1)
+    L = g.n0 // n
+    xs = [workloads.uniform_inputs(L, n, 70 + i, M) for i in range(2)]
+    parts = [g.encrypt(x, n, 1, M, 80 + i) for i, x in enumerate(xs)]
+    batch = he.Ciphertexts(g, torch.cat([p.tensor for p in parts]), parts[0].level, parts[0].scale, 2)
+    g.softmax_grouped(batch, pl, 2)
+    w = 2 * (batch.level + 1) * g.n
+    for i, x in enumerate(xs):
+        one = he.Ciphertexts(g, batch.tensor[i * w:(i + 1) * w], batch.level, batch.scale, 1)
+        err = np.abs(g.decrypt(one, n) - O.softmax_fp64(x)).max()
+        assert err < 2 ** -15, (n, i, -math.log2(err))

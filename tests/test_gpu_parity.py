@@ -326,3 +326,82 @@ def test_softmax_alg4_bit_exact(toybts, params, mode):
     for i in range(m):
         assert np.array_equal(got[i], outs[i].data), i
     assert np.abs(g.decrypt(gc, n) - O.softmax_fp64(x)).max() < 2 ** -15
+
+
+@pytest.mark.parametrize("split", [(2, 2), (1, 3)])
+def test_softmax_alg4_split_shares_equal_unsplit(toybts, split):
+    """Alg. 4 split over shares of the main-thread ciphertexts (the multi-device form: one share
+    per device, the shares' sums of squares added as integers, the auxiliary thread on every
+    device): two shares in one process, sums added on the host side of the boundary; every
+    share's output equals the unsplit batched he_softmax's, bit for bit."""
+    g, o, em = toybts
+    pl = he.load_plans_b()["toybts_n16_M32_B"]
+    n, m = pl["n"], sum(split)
+    g.keygen_softmax(n, m)
+    L = m * o.n0 // n
+    x = np.random.default_rng(29).uniform(-pl["M"], 0, (L, n))
+    whole = g.encrypt(x, n, m, pl["M"], 35)
+    ref = g.like(whole)
+    ref.tensor.copy_(whole.tensor)
+    g.softmax(ref, pl, batched=True)
+    cw = 2 * (whole.level + 1) * g.n
+    shares, lo = [], 0
+    for cnt in split:
+        t = whole.tensor[lo * cw:(lo + cnt) * cw].clone()
+        shares.append(he.Ciphertexts(g, t, whole.level, whole.scale, cnt))
+        lo += cnt
+    y0 = [g.softmax_share_exp(s_, pl) for s_ in shares]
+    ys = [g.like(s_) for s_ in shares]
+    lam, lr = g.alloc(o.chain["user_top_level"], 1), g.alloc(o.chain["user_top_level"], 1)
+    for j in range(1, pl["k"] + 1):
+        src = y0 if j == 1 else ys
+        d = [g.softmax_share_square_sum(s_) for s_ in src]
+        dsum = d[0] + d[1]   # integer sum of residues (< 2^61): exact
+        g.softmax_aux_round(pl, j, m, dsum, src[0].level, src[0].scale, y0[0], lam, lr)
+        ys = [g.softmax_share_update(pl, j, lr, y0[i], g.like(y0[i])) for i in range(2)]
+    assert all(y.level == ref.level and y.scale == ref.scale for y in ys)
+    got = torch.cat([y.tensor[:y.n_ct * 2 * (y.level + 1) * g.n] for y in ys])
+    assert torch.equal(got, ref.tensor[:m * 2 * (ref.level + 1) * g.n])
+
+
+def test_autotune_variants_bit_identical(toybts):
+    """Every launch strategy the autotuner chooses between gives the same words: each variant of
+    each operation forced in turn on multiplications, hoisted rotations and SlotToCoeff /
+    CoeffToSlot levels at batch sizes 1, 2 and 6; then he_autotune fills its table (one entry
+    per timed operation, level and batch size) and results stay the same."""
+    g, o, em = toybts
+    rng = np.random.default_rng(31)
+    top = len(o.q) - 1
+
+    def run():
+        out = []
+        for nct in (1, 2, 6):
+            a = g.from_coeff(_rand_ct(o, 3, rng_fixed(nct), nct), 3, 2.0 ** 42)
+            b = g.from_coeff(_rand_ct(o, top, rng_fixed(nct + 10), nct), top, float(o.q[0]))
+            out.append(g.to_coeff(g.hmult(a, a)))
+            out.append(g.to_coeff(g.lintrans(a, 3, False, 0, 16.0, float(o.q[3]))))
+            out.append(g.to_coeff(g.lintrans(b, 3, True, 1, 1.0, float(o.q[top]))))
+        return out
+
+    def rng_fixed(k):
+        return np.random.default_rng(1000 + k)
+
+    ref = run()
+    for op in ("modup", "rot", "lt_small", "lt_rows"):
+        for choice in (0, 1):
+            g.tune_force(op, choice)
+            got = run()
+            g.tune_force(op, -1)
+            for i, (x, y) in enumerate(zip(ref, got)):
+                assert np.array_equal(x, y), (op, choice, i)
+    g.autotune([3, top - 1, top], [1, 6], reps=1)
+    table = g.tune_table()
+    ops = {e["op"] for e in table}
+    assert ops == {"modup", "rot", "lt_small", "lt_rows"}, ops
+    assert all(e["choice"] in (0, 1) and min(e["ms"]) > 0 for e in table)
+    assert {(e["limbs"], e["n_ct"]) for e in table if e["op"] == "modup"} == {(4, 1), (4, 6), (top, 1), (top, 6),
+                                                                                 (top + 1, 1), (top + 1, 6)}
+    got = run()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    del rng

@@ -44,10 +44,13 @@ def _cat(g, parts):
     return he.Ciphertexts(g, t, parts[0].level, parts[0].scale, sum(p.n_ct for p in parts))
 
 
+@pytest.mark.parametrize("plan", ["toybts_n16_M32", "toybts_n16_M32_B"])
 @pytest.mark.parametrize("m,groups", [(1, 3), (2, 2)])
-def test_grouped_equals_alone_and_oracle(ctx, params, m, groups):
+def test_grouped_equals_alone_and_oracle(ctx, params, m, groups, plan):
+    """Alg. 2 and Alg. 4 (plan suffix _B): every group of a grouped pass equals the group alone."""
     g, o, em = ctx
-    pl = params[1]["toybts_n16_M32"]
+    alg4 = plan.endswith("_B")
+    pl = he.load_plans_b()[plan] if alg4 else params[1][plan]
     n = pl["n"]
     xs = [_inputs(g, pl, m, 100 + i) for i in range(groups)]
     parts = [g.encrypt(x, n, m, pl["M"], 200 + i) for i, x in enumerate(xs)]
@@ -64,7 +67,8 @@ def test_grouped_equals_alone_and_oracle(ctx, params, m, groups):
     # group 0 against the oracle, limb for limb
     top = o.chain["user_top_level"]
     slots = O.pack(xs[0], m, o.n0)
-    outs = o.softmax([o.encrypt(slots[j], top, (2 / pl["M"]) * o.q[top], 200, j) for j in range(m)], pl, em)
+    ins = [o.encrypt(slots[j], top, (2 / pl["M"]) * o.q[top], 200, j) for j in range(m)]
+    outs = o.softmax_b(ins, pl, em) if alg4 else o.softmax(ins, pl, em)
     got = g.to_coeff(batch)
     for j in range(m):
         assert np.array_equal(got[j], outs[j].data), j
