@@ -117,6 +117,18 @@ class ClockSampler:
 NTT_DRAM_PER_ALG_BYTE = 1.733e6 / (16 * 65536)
 
 
+# Warp instructions per limb of the N = 2^16 transforms (ncu sass__inst_executed_per_opcode /
+# smsp__inst_executed.sum of one capture, divided by the limbs of the launch): forward = column
+# pass + row pass of a 320-limb ModUp transform (76 513 280 + 86 999 040 over 320 limbs; python -m
+# paper_2410_11184_gb300.profile_case keyswitch); inverse = the two inverse passes of a 768-limb
+# ModUp transform of the same case (196 018 176 + 242 712 576 over 768 limbs)
+# (profiles/ntt_instruction_mix_n65536.txt).  The NTT is bound by integer instruction
+# issue (64-bit modular butterflies on 32-bit pipes), so its roofline is the SM issue limit:
+# 152 SMs x 4 sub-partitions x 1 warp instruction per cycle x 2070 MHz (the SM count and maximum
+# SM clock of GB300; four schedulers per SM on this architecture).
+NTT_WARP_INSTR_PER_LIMB = {"fwd": (76513280 + 86999040) / 320, "inv": (196018176 + 242712576) / 768}
+ISSUE_PEAK_G = 152 * 4 * 2.070   # G warp instructions / s
+
 # integer pipes of the NTT passes (both forward passes of a 320-limb ModUp transform at N = 2^16,
 # weighted by their durations 105 / 131 us; ncu SpeedOfLight / ComputeWorkloadAnalysis /
 # SchedulerStats sections, python -m paper_2410_11184_gb300.profile_case keyswitch):
@@ -573,8 +585,12 @@ def main():
             for fam, (nl, ms, b) in g.profile_breakdown().items():
                 if fam.startswith("phase:"):
                     phases[fam[6:]] = {"launches": nl, "ms": round(ms, 3)}
+                    if fam.startswith("phase:bootstrap."):   # the sum of the bootstrapping's steps
+                        tot = phases.setdefault("bootstrap", {"launches": 0, "ms": 0.0})
+                        tot["launches"] += nl
+                        tot["ms"] = round(tot["ms"] + ms, 3)
                     continue
-                breakdown[fam] = {"launches": nl, "ms": round(ms, 3)}
+                breakdown[fam] = {"launches": nl, "ms": round(ms, 3), "bytes": b}
                 if b > 0 and ms > 0:
                     breakdown[fam]["gbs"] = round(b / (ms * 1e-3) / 1e9, 1)
             g.profile_kernel("")
@@ -702,17 +718,30 @@ def main():
     hbm, peak_kind = peaks()
     roof = None
     if k_launch:
-        achieved = (k_bytes / k_launch) / ((k_ms / k_launch) * 1e-3) / 1e9
+        gbs = (k_bytes / k_launch) / ((k_ms / k_launch) * 1e-3) / 1e9
         traffic = (k_bytes / k_launch) * NTT_DRAM_PER_ALG_BYTE if args.profile_kernel == "ntt" else None
-        roof = {"bound": "hbm", "kernel": args.profile_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
-                # graph replays: the events inside the graph hold the last timed step
-                "launches_per_step": k_launch, "kernel_ms_per_step": k_ms,
-                "share_of_step": k_ms / prof_ms_step, "profiled_ms_per_step": prof_ms_step,
-                "timed": "CUDA events inside a second captured graph of the same step, its last replay of %d"
-                         % args.steps}
-        if args.profile_kernel == "ntt":
-            roof["int_pipes"] = NTT_INT_PIPES
+        hbm_view = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "peak_kind": peak_kind, "algorithmic_bytes": "16 N per limb (read + write)"}
+        roof = dict(hbm_view, kernel=args.profile_kernel, traffic=traffic)
+        if args.profile_kernel == "ntt" and breakdown:
+            # limbs per direction from the eager breakdown (16 N algorithmic bytes per limb)
+            lb = 16.0 * g.n
+            fwd = sum(v["bytes"] for k, v in breakdown.items() if k.startswith("ntt") and not k.endswith("_inv")) / lb
+            inv = sum(v["bytes"] for k, v in breakdown.items() if k.startswith("ntt") and k.endswith("_inv")) / lb
+            per_limb = (fwd * NTT_WARP_INSTR_PER_LIMB["fwd"] + inv * NTT_WARP_INSTR_PER_LIMB["inv"]) / (fwd + inv)
+            limbs = k_bytes / lb   # the timed replay's limbs
+            ach = limbs * per_limb / (k_ms * 1e-3) / 1e9
+            roof = {"bound": "alu", "kernel": "ntt", "achieved": ach, "peak": ISSUE_PEAK_G,
+                    "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G, "traffic": traffic,
+                    "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction/cycle x 2070 MHz",
+                    "work": "warp instructions per limb from ncu (forward %.0f, inverse %.0f), %.0f%% forward limbs"
+                            % (NTT_WARP_INSTR_PER_LIMB["fwd"], NTT_WARP_INSTR_PER_LIMB["inv"],
+                               100 * fwd / (fwd + inv)),
+                    "hbm_view": hbm_view, "int_pipes": NTT_INT_PIPES}
+        roof.update({"launches_per_step": k_launch, "kernel_ms_per_step": k_ms,
+                     "share_of_step": k_ms / prof_ms_step, "profiled_ms_per_step": prof_ms_step,
+                     "timed": "CUDA events inside a second captured graph of the same step, its last replay of %d"
+                              % args.steps})
     all_err = [e for v in prec_err.values() for e in v]
     precision = {"gate_bits": 15, "vs": "FP64 Softmax, max |error| per run",
                  "seeds": list(range(100, 100 + args.precision_seeds)), "total": stats_bits(all_err),

@@ -300,12 +300,14 @@ int he_profile_kernel(he_ctx *ctx, const char *name);
 int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes);
 /* with he_profile_kernel(ctx, "all"): every launch and device copy is timed; this call
  * synchronises and writes one text line "family launches total_ms bytes" (bytes: the
- * algorithmic bytes of those launches, 0 where not stated) per kernel family (ntt,
- * modup, ks_inner, moddown, tensor, rescale, lintrans, elementwise, automorph, modraise, encode, decode,
- * keygen, copy) into buf (len bytes, NUL-terminated), then one line "phase:P launches total_ms 0"
- * per phase of the Softmax circuit the launches belonged to (main: the m main-thread ciphertexts;
- * aux: the auxiliary thread of Alg. 3 outside bootstrapping; bootstrap: every bootstrapping;
- * other: launches outside a Softmax), then resets.  HE_EINVAL if buf is too small.  The phases are
+ * algorithmic bytes of those launches, 0 where not stated) per kernel family (the transforms by
+ * call site and direction: ntt, ntt_modup, ntt_moddown, ntt_rescale, ntt_modraise, each with an
+ * _inv twin for the inverse, 16 N bytes per limb; modup, ks_inner, moddown, tensor, rescale,
+ * lintrans, elementwise, automorph, modraise, encode, decode, keygen, copy) into buf (len bytes,
+ * NUL-terminated), then one line "phase:P launches total_ms 0" per phase of the Softmax circuit the launches belonged to (main: the m main-thread ciphertexts;
+ * aux: the auxiliary thread of Alg. 3 outside bootstrapping; bootstrap.stc, bootstrap.modraise,
+ * bootstrap.cts, bootstrap.evalmod: the four steps of every bootstrapping; other: launches
+ * outside a Softmax), then resets.  HE_EINVAL if buf is too small.  The phases are
  * also NVTX ranges of the same names. */
 int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len);
 /* bounded device wait self test: a kernel polls a flag nobody sets for at most max_iter polls

@@ -59,16 +59,36 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
 // estimate is at most 2 below the exact quotient and a w - h q < 2q + 2q.  The low word
 // a w + h nq = a w - h q is exact mod 2^64 because the true value is below 4q < 2^63.
 // Written as 32-bit multiply-adds only: with h = H + t2, H = a1 w'1 + hi(a0 w'1) (exact in
-// 64 bits) and t2 = hi(a1 w'0), h nq = H nq + t2 nq, so no 64-bit addition is needed.
+// 64 bits) and t2 = hi(a1 w'0), h nq = H nq + t2 nq, so no 64-bit addition is needed.  The
+// 64-bit sums are explicit carry chains (mad.lo.cc / madc.hi), which the compiler otherwise
+// lowers with separate adds.
 __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t nq) {
-    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), p0 = (uint32_t)wp, p1 = (uint32_t)(wp >> 32);
-    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32), n0 = (uint32_t)nq, n1 = (uint32_t)(nq >> 32);
-    const uint32_t t2 = __umulhi(a1, p0);
-    const uint64_t H = (uint64_t)a1 * p1 + __umulhi(a0, p1);
-    const uint32_t h0 = (uint32_t)H, h1 = (uint32_t)(H >> 32);
-    const uint64_t acc = (uint64_t)a0 * w0 + (uint64_t)h0 * n0 + (uint64_t)t2 * n0;
-    const uint32_t hi = (uint32_t)(acc >> 32) + a0 * w1 + a1 * w0 + h0 * n1 + h1 * n0 + t2 * n1;
-    return ((uint64_t)hi << 32) | (uint32_t)acc;
+    uint32_t a0, a1, p0, p1, w0, w1, n0, n1, r0, r1;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(a0), "=r"(a1) : "l"(a));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(p0), "=r"(p1) : "l"(wp));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(w0), "=r"(w1) : "l"(w));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(n0), "=r"(n1) : "l"(nq));
+    asm("{\n\t.reg .u32 t, t2, h0, h1;\n\t"
+        "mul.hi.u32 t, %2, %5;\n\t"            // hi(a0 w'1)
+        "mul.hi.u32 t2, %3, %4;\n\t"           // t2 = hi(a1 w'0)
+        "mad.lo.cc.u32 h0, %3, %5, t;\n\t"     // H = a1 w'1 + hi(a0 w'1)
+        "madc.hi.u32 h1, %3, %5, 0;\n\t"
+        "mul.lo.u32 %0, %2, %6;\n\t"           // acc = a0 w0 + h0 n0 + t2 n0 (mod 2^64)
+        "mul.hi.u32 %1, %2, %6;\n\t"
+        "mad.lo.cc.u32 %0, h0, %8, %0;\n\t"
+        "madc.hi.u32 %1, h0, %8, %1;\n\t"
+        "mad.lo.cc.u32 %0, t2, %8, %0;\n\t"
+        "madc.hi.u32 %1, t2, %8, %1;\n\t"
+        "mad.lo.u32 %1, %2, %7, %1;\n\t"       // high word: + a0 w1 + a1 w0 + h0 n1 + h1 n0 + t2 n1
+        "mad.lo.u32 %1, %3, %6, %1;\n\t"
+        "mad.lo.u32 %1, h0, %9, %1;\n\t"
+        "mad.lo.u32 %1, h1, %8, %1;\n\t"
+        "mad.lo.u32 %1, t2, %9, %1;\n\t}"
+        : "=&r"(r0), "=&r"(r1)
+        : "r"(a0), "r"(a1), "r"(p0), "r"(p1), "r"(w0), "r"(w1), "r"(n0), "r"(n1));
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(r0), "r"(r1));
+    return r;
 }
 
 // valid for a < 2^62 and b < q (the quotient estimate stays within 2 of the true one)

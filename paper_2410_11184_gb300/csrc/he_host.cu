@@ -312,6 +312,15 @@ static LimbMap single(int p) {
 }
 
 // ------------------------------------------------------------------------- NTT launches
+static const char *ntt_inv_family(const char *site) {
+    static const char *const fwd[] = {"ntt", "ntt_modup", "ntt_moddown", "ntt_rescale", "ntt_modraise"};
+    static const char *const inv[] = {"ntt_inv", "ntt_modup_inv", "ntt_moddown_inv", "ntt_rescale_inv",
+                                      "ntt_modraise_inv"};
+    for (int i = 0; i < 5; i++)
+        if (!strcmp(site, fwd[i])) return inv[i];
+    return "ntt_inv";
+}
+
 // NTT of `count` limbs in place, or out of place from src (limb l of polynomial i at
 // src + i src_stride + l N) when src is given; register-blocked passes of 8 (N = 2^12) or 16
 // (N = 2^16) coefficients per thread, the only ring sizes a context accepts.
@@ -321,11 +330,9 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
                 const NttFuse *fuse = nullptr) {
     if (count <= 0) return;
     REQUIRE(!fuse || !inverse, HE_EINVAL, "fused transform: forward only");
-    // algorithmic bytes: the transform's read + write, plus what a fused ModDown epilogue reads
-    double extra = !fuse ? 0.0
-                   : fuse->kind == 1 ? 8.0 * count * c->N * (fuse->add ? 2 : 1)
-                   : fuse->kind == 3 ? 16.0 * count * c->N : 0.0;
-    ProfScope ps(c, site, 16.0 * count * c->N + extra);
+    // timing family: the call site with the direction ("ntt_modup" forward, "ntt_modup_inv"
+    // inverse); algorithmic bytes: the transform's read + write of every limb, 16 N per limb
+    ProfScope ps(c, inverse ? ntt_inv_family(site) : site, 16.0 * count * c->N);
     c->launches++;
     launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
                   c->d_ninv, c->logN, c->st, src, src_stride, fuse);
@@ -1490,18 +1497,22 @@ static std::vector<int> lt_rotation_steps(he_ctx *c, const LtDesc &lv) {
 
 // ------------------------------------------------------------------------- bootstrapping
 static DCt bootstrap(he_ctx *c, const DCt &x, double gain, double out_scale) {
-    PhaseScope ph(c, "bootstrap");
     REQUIRE(c->bootstrap, HE_EINVAL, "bootstrapping not enabled");
     REQUIRE(x.level >= c->stc_levels, HE_ELEVEL, "bootstrap: level too low");
+    std::unique_ptr<PhaseScope> ph(new PhaseScope(c, "bootstrap.stc"));
     DCt y = ct_drop(c, x, c->stc_levels);
     std::vector<LtDesc> lv = lt_levels(c, c->stc_levels, 0);
     for (int g = 0; g < c->stc_levels; g++) y = lt_eval_level(c, y, lv[g], g == 0 ? gain : 1.0, (double)c->mods[y.level]);
     double d_in = y.scale;
     int top = c->nq - 1;
+    ph.reset();   // the previous step's scope ends first (NVTX ranges nest)
+    ph.reset(new PhaseScope(c, "bootstrap.modraise"));
     DCt z = mod_raise(c, y, top);
     z.scale = (double)c->mods[0];
     int em_in = top - c->cts_levels;
     double s_em = (double)c->mods[em_in];
+    ph.reset();   // the previous step's scope ends first (NVTX ranges nest)
+    ph.reset(new PhaseScope(c, "bootstrap.cts"));
     lv = lt_levels(c, c->cts_levels, 1);
     for (int g = 0; g < c->cts_levels; g++) {
         double gn = g == c->cts_levels - 1 ? 1.0 / (2.0 * c->em_K) : 1.0;
@@ -1509,6 +1520,8 @@ static DCt bootstrap(he_ctx *c, const DCt &x, double gain, double out_scale) {
         double pts = g == c->cts_levels - 1 ? (qs * s_em) / z.scale : qs;
         z = lt_eval_level(c, z, lv[g], gn, pts);
     }
+    ph.reset();   // the previous step's scope ends first (NVTX ranges nest)
+    ph.reset(new PhaseScope(c, "bootstrap.evalmod"));
     DCt cj = rotate(c, z, 2 * c->N - 1);
     ct_add_inplace(c, z, cj);
     int lp = c->user_top + c->em_r;

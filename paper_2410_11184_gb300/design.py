@@ -392,6 +392,52 @@ def build_b(write=True, names=None):
     return plans
 
 
+def newton_inv_root(y, v, p, steps):
+    """Newton's iteration for v^(-1/p) (App. A for p = 2): y <- y ((p + 1) - v y^p) / p, `steps`
+    times.  A relative error e of y becomes 1 - ((1 + e)(p + 1 - (1 + e)^p)) / p ~ ((p + 1)/2) e^2."""
+    for _ in range(steps):
+        y = y * ((p + 1.0) - v * y ** p) / p
+    return y
+
+
+def newton_levels(p):
+    """levels of one Newton step for v^(-1/p), p = 2^j, arranged as ((p+1)/p) y - (v y) y^p / p:
+    y^p takes j squarings while v y takes one product beside them, and their product one more
+    level (two levels for p = 2, as in App. A; the constants are free in the scale)."""
+    return int(round(math.log2(p))) + 1
+
+
+def newton_study(plans, names=None):
+    """Newton-refined inverse roots against the plans' single polynomials: for every round, the
+    plan's degree-d minimax fit P_j of v^(-1/p) (p = 2 for Alg. 2, 2^j for Alg. 4) with its depth
+    ceil(log2(d + 1)) and relative error eps = max |v^(1/p) P_j(v) - 1|, beside a lower-degree
+    fit of the same function on the same interval followed by one Newton step at a depth no
+    larger.  Returns rows (plan, round, p, depth, eps, newton degree, newton depth, newton eps)."""
+    rows = []
+    for name, pl in plans.items():
+        if names and name not in names:
+            continue
+        alg4 = pl.get("version") == "B"
+        for j, it in enumerate(pl["iters"][: pl["k"]], start=1):
+            p = 2 ** j if alg4 else 2
+            a, b, d = it["a"], it["b"], it["deg"]
+            depth = int(math.ceil(math.log2(d + 1)))
+            uu = np.cos(np.linspace(0.0, np.pi, 20001))
+            vv = 0.5 * (b - a) * uu + 0.5 * (a + b)
+            c = np.array([float.fromhex(h) for h in it["coeffs"]])
+            eps = float(np.max(np.abs(vv ** (1.0 / p) * (cheb_vander(uu, d) @ c) - 1.0)))
+            nd_depth = depth - newton_levels(p)
+            if nd_depth < 1:
+                rows.append((name, j, p, depth, eps, None, None, None))
+                continue
+            dn = 2 ** nd_depth - 1
+            cn, _ = weighted_minimax(lambda v, p=p: v ** (-1.0 / p), lambda v, p=p: v ** (1.0 / p), a, b, dn)
+            y = newton_inv_root(cheb_vander(uu, dn) @ cn, vv, p, 1)
+            eps_n = float(np.max(np.abs(vv ** (1.0 / p) * y - 1.0)))
+            rows.append((name, j, p, depth, eps, dn, nd_depth + newton_levels(p), eps_n))
+    return rows
+
+
 def design_evalmod(K, r, deg):
     """cos(2 pi (K u - 1/4) / 2^r) on u in [-1, 1]; r double angles give sin(2 pi K u)."""
     g = lambda u: np.cos(2.0 * np.pi * (K * u - 0.25) / 2.0 ** r)
@@ -449,6 +495,14 @@ def load_params():
 if __name__ == "__main__":
     import sys
 
+    if "--newton-study" in sys.argv:
+        _, plans, _ = load_params()
+        with open(os.path.join(PARAMS_DIR, "plans_b.json")) as fh:
+            plans.update(json.load(fh))
+        names = [a for a in sys.argv[1:] if not a.startswith("--")] or ["n256_M128", "n256_M128_B", "n4096_M64_B"]
+        for r in newton_study(plans, names):
+            print(r)
+        sys.exit(0)
     if "--version-b" in sys.argv:
         # Alg. 4 plans only (params/plans_b.json); the other parameter files stay as they are.
         # Further arguments name the plans to (re)design; the others are kept from the file.

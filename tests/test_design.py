@@ -122,3 +122,33 @@ def test_softmax_k_matches_theorem_3_3():
     assert D.softmax_k(8, 16) == 2
     assert D.softmax_k(128, 256) == 5
     assert D.softmax_k(64, 128) == 4
+
+
+def test_newton_inverse_root_step():
+    """Newton's step for v^(-1/p) (App. A for p = 2): the exact root is a fixed point, and a
+    relative error e becomes about ((p + 1)/2) e^2 (quadratic convergence from small errors);
+    from a large error (e = -0.9 for p = 2) the step does not converge."""
+    from paper_2410_11184_gb300 import design as D
+
+    v = np.linspace(0.01, 2.0, 101)
+    for p in (2, 4, 8):
+        exact = v ** (-1.0 / p)
+        assert np.allclose(D.newton_inv_root(exact, v, p, 1), exact, rtol=1e-14)
+        for e in (1e-3, -1e-3, 1e-2):
+            got = D.newton_inv_root(exact * (1 + e), v, p, 1) / exact - 1.0
+            assert np.allclose(got, -(p + 1) / 2 * e * e, rtol=0.05, atol=1e-12)
+    bad = D.newton_inv_root(v ** -0.5 * 0.1, v, 2, 1) / v ** -0.5 - 1.0
+    assert np.all(np.abs(bad) > 0.8)
+    assert D.newton_levels(2) == 2 and D.newton_levels(16) == 5
+
+
+@pytest.mark.slow
+def test_newton_refinement_loses_at_equal_depth(params):
+    """Round 5 of the n = 256, M = 128 plan: its degree-127 fit of v^(-1/2) (depth 7) reaches
+    1.5e-7; a degree-31 fit with one Newton step (two levels) at the same depth does far worse."""
+    from paper_2410_11184_gb300 import design as D
+
+    rows = D.newton_study({"n256_M128": params[1]["n256_M128"]})
+    last = rows[-1]
+    assert last[3] == last[6] == 7
+    assert last[4] < 1e-6 and last[7] > 100 * last[4]
