@@ -142,6 +142,10 @@ struct he_ctx {
     std::map<std::tuple<int, int, int>, TuneRec> tune;
     int tune_force[4] = {-1, -1, -1, -1};
     cudaStream_t st = nullptr;
+    // side streams for independent branches of a circuit (Branch), created on first use
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork_ev[2] = {nullptr, nullptr}, join_ev[2] = {nullptr, nullptr};
+    int branch_depth = 0;   // > 0 while a Branch is open
     std::string err;
     long cnt[5] = {0, 0, 0, 0, 0};
     long launches = 0;
@@ -248,13 +252,64 @@ PhaseScope::~PhaseScope() {
         if (!(cond)) throw HeErr{code, msg};                              \
     } while (0)
 
+// Stream-ordered device buffers.  A buffer is freed on the stream that is current when its last
+// reference goes (c->st then), not on the one it was allocated on: inside a Branch that is the
+// branch's stream, which follows every use of the buffer before the fork and in the branch;
+// after the join it is the main stream, which follows the branch.  A buffer is never in use on
+// two branches at once unless an outer scope holds it.
 static DPtr dalloc(he_ctx *c, size_t words) {
     void *p = nullptr;
     if (words == 0) words = 1;
     cudaError_t e = cudaMallocAsync(&p, words * 8, c->st);
     if (e != cudaSuccess) throw HeErr{HE_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
-    cudaStream_t st = c->st;
-    return DPtr((uint64_t *)p, [st](uint64_t *q) { cudaFreeAsync(q, st); });
+    return DPtr((uint64_t *)p, [c](uint64_t *q) { cudaFreeAsync(q, c->st); });
+}
+
+// An independent branch of a circuit on side stream i.  Construction forks it from the work
+// issued so far on the current (main) stream; between enter() and leave() the library issues on
+// the side stream; join() (or the destructor) makes the main stream wait for the branch.  Several
+// branches forked at the same point run concurrently with each other and with what the main
+// stream does before the joins; inside a graph capture they become parallel branches of the graph.
+struct Branch {
+    he_ctx *c;
+    cudaStream_t main;
+    int i;
+    bool joined = false, inside = false;
+    Branch(he_ctx *c_, int i_) : c(c_), main(c_->st), i(i_) {
+        if (!c->side[i]) {
+            CK(cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c->fork_ev[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(c->fork_ev[i], main));
+        CK(cudaStreamWaitEvent(c->side[i], c->fork_ev[i], 0));
+    }
+    void enter() {
+        c->st = c->side[i];
+        c->branch_depth++;
+        inside = true;
+    }
+    void leave() {
+        if (!inside) return;
+        inside = false;
+        c->branch_depth--;
+        c->st = main;
+    }
+    void join() {
+        leave();
+        if (joined) return;
+        joined = true;
+        cudaEventRecord(c->join_ev[i], c->side[i]);
+        cudaStreamWaitEvent(main, c->join_ev[i], 0);
+    }
+    ~Branch() { join(); }
+};
+
+// a cache entry (encoded diagonals or masks) made inside a Branch may be read by another branch
+// or the main stream: outside a graph capture, finish it before it is shared (first use only;
+// captures run after an eager pass has filled the caches)
+static void cache_entry_made(he_ctx *c) {
+    if (c->branch_depth > 0 && !c->capturing) CK(cudaStreamSynchronize(c->st));
 }
 
 static dim3 grid_for(he_ctx *c, long total) {
@@ -1353,6 +1408,7 @@ static const LtLevel &lt_prepare(he_ctx *c, const LtDesc &lv, double gain, doubl
             L.pts.push_back(p);
         }
     }
+    cache_entry_made(c);
     return c->lt_cache.emplace(keyb, std::move(L)).first->second;
 }
 
@@ -1754,7 +1810,10 @@ static std::vector<DCt> softmax_run(he_ctx *c, const Plan &p, std::vector<DCt> y
         char mkey[128];
         snprintf(mkey, sizeof mkey, "mask:%d:%d:%a:%a", stride, lm, mval, smk);
         auto mit = c->pt_cache.find(mkey);
-        if (mit == c->pt_cache.end()) mit = c->pt_cache.emplace(mkey, encode(c, mk, smk, lm)).first;
+        if (mit == c->pt_cache.end()) {
+            mit = c->pt_cache.emplace(mkey, encode(c, mk, smk, lm)).first;
+            cache_entry_made(c);
+        }
         ct_mul_plain(c, lam, mit->second.get());
         lam.scale = lam.scale * smk;
         lam = rescale(c, lam);
@@ -1807,14 +1866,29 @@ static DCt split_eval(he_ctx *c, const Plan &p, const DCt &v, const std::vector<
     std::vector<double> e(h / 2 + 1, 0.0);
     e[h / 2] = 1.0;
     double s_t = sqrt(2.0 * qd(c, top) * delta);
-    DCt t = bts_boosted(c, p, poly_eval(c, v, e, lo, delta), 1.0, s_t);
-    DCt th = hmult(c, t, t);                  // t^2 at 2 Delta = 2 t^2 - 1 + 1 at Delta
-    th.scale = th.scale / 2.0;
-    ct_add_const(c, th, h_round(-1.0 * th.scale));
-    DCt bb = bts_boosted(c, p, poly_eval(c, v, b_c, lo, delta), 1.0 / bmax, qd(c, top - 1) * bmax);
+    // the T and B halves are independent one-ciphertext chains (each with a bootstrapping) and
+    // run on two side streams, concurrently with each other and with A on the main stream
+    DCt th, bb;
+    Branch br_t(c, 0), br_b(c, 1);   // both fork here
+    br_t.enter();
+    {
+        DCt t = bts_boosted(c, p, poly_eval(c, v, e, lo, delta), 1.0, s_t);
+        th = hmult(c, t, t);                  // t^2 at 2 Delta = 2 t^2 - 1 + 1 at Delta
+        th.scale = th.scale / 2.0;
+        ct_add_const(c, th, h_round(-1.0 * th.scale));
+    }
+    br_t.leave();
+    br_b.enter();
+    bb = bts_boosted(c, p, poly_eval(c, v, b_c, lo, delta), 1.0 / bmax, qd(c, top - 1) * bmax);
     bb.scale = bb.scale / bmax;               // B at scale q_(top-1)
+    br_b.leave();
+    // A needs only the scale of T_h B, which the host knows from the scale bookkeeping alone
+    double prod_scale = (th.scale * bb.scale) / qd(c, std::min(th.level, bb.level));
+    DCt a = poly_eval(c, v, a_c, lo, prod_scale);
+    br_t.join();
+    br_b.join();
     DCt prod = hmult(c, th, bb);
-    DCt a = poly_eval(c, v, a_c, lo, prod.scale);
+    REQUIRE(prod.scale == prod_scale, HE_EINVAL, "split polynomial: scale bookkeeping");
     DCt out = ct_drop(c, prod, lo);
     ct_add_inplace(c, out, a);
     return out;
@@ -1830,6 +1904,7 @@ static const uint64_t *mask_pt(he_ctx *c, int stride, int level, double mval, do
         std::vector<double2> mk(c->n0, make_double2(0.0, 0.0));
         for (int i = 0; i < stride; i++) mk[i].x = mval;
         mit = c->pt_cache.emplace(mkey, encode(c, mk, scale, level)).first;
+        cache_entry_made(c);
     }
     return mit->second.get();
 }
@@ -2320,6 +2395,13 @@ void he_context_destroy(he_ctx *c) {
     }
     c->pt_cache.clear();
     c->lt_cache.clear();
+    for (int i = 0; i < 2; i++)
+        if (c->side[i]) {
+            cudaStreamSynchronize(c->side[i]);
+            cudaStreamDestroy(c->side[i]);
+            cudaEventDestroy(c->fork_ev[i]);
+            cudaEventDestroy(c->join_ev[i]);
+        }
     for (auto &kv : c->keys) cudaFree(kv.second);
     for (auto &e : c->prof_ev) {
         cudaEventDestroy(e.first);

@@ -405,3 +405,47 @@ def test_autotune_variants_bit_identical(toybts):
     for x, y in zip(ref, got):
         assert np.array_equal(x, y)
     del rng
+
+
+@pytest.mark.parametrize("mode", ["batched", "graph"])
+def test_softmax_alg4_split_first_polynomial_bit_exact(toybts, mode):
+    """A first polynomial one level deeper than the room above the bootstrapping input (degree
+    1023, Chebyshev interpolant of v^(-1/2) on the plan's interval) is evaluated as A + T_512 B:
+    T_256 and B bootstrapped on two side streams beside A.  Every output limb equals the oracle's
+    (which evaluates the three parts one after the other), eagerly and by graph replay."""
+    import copy
+
+    from paper_2410_11184_gb300 import design as D
+
+    g, o, em = toybts
+    pl = copy.deepcopy(he.load_plans_b()["toybts_n16_M32_B"])
+    it = pl["iters"][0]
+    a, b = it["a"], it["b"]
+    c, _ = D.cheb_interp(lambda u: (0.5 * (b - a) * u + 0.5 * (a + b)) ** -0.5, 1023)
+    it["coeffs"] = D.hexlist(c)
+    it["deg"] = 1023
+    D.bts_gains_b(pl, o.chain)
+    assert it["b_max"] > 0
+    n, m = pl["n"], 2
+    g.keygen_softmax(n, m)
+    L = m * o.n0 // n
+    x = np.random.default_rng(37).uniform(-pl["M"], 0, (L, n))
+    gc = g.encrypt(x, n, m, pl["M"], 38)
+    top = o.chain["user_top_level"]
+    slots = O.pack(x, m, o.n0)
+    outs = o.softmax_b([o.encrypt(slots[i], top, (2 / pl["M"]) * o.q[top], 38, i) for i in range(m)], pl, em)
+    c0 = g.counters()
+    if mode == "graph":
+        work = g.like(gc)
+        for _ in range(2):
+            work.tensor.copy_(gc.tensor)
+            work.level, work.scale, work.n_ct = gc.level, gc.scale, gc.n_ct
+            g.softmax(work, pl, graph=True)
+        gc = work
+    else:
+        g.softmax(gc, pl, batched=True)
+        assert g.counters()["bts"] - c0["bts"] == 2 * pl["k"] + 2
+    assert gc.level == outs[0].level and gc.scale == outs[0].scale
+    got = g.to_coeff(gc)
+    for i in range(m):
+        assert np.array_equal(got[i], outs[i].data), i
