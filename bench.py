@@ -491,7 +491,13 @@ def main():
         table = g.tune_table()
         tune = {"seconds": round(time.perf_counter() - t0, 2), "entries": len(table),
                 "keys": "(op, limbs, n_ct) for levels 1..%d and n_ct in %s" % (len(ch["q"]) - 1, sorted({1, m})),
-                "non_default": [e for e in table if e["choice"] != (1 if e["n_ct"] <= 4 else 0)]}
+                "non_default": [e for e in table if e["op"] != "ntt_small"
+                                and e["choice"] != (1 if e["n_ct"] <= 4 else 0)],
+                "ntt_small_cta_at_limbs": {d: [e["limbs"] for e in table if e["op"] == "ntt_small"
+                                               and e["n_ct"] == i and e["choice"] == 1]
+                                           for i, d in enumerate(("forward", "inverse"))},
+                "ntt_small_cta_ms": {"%s_%d" % ("fwd" if e["n_ct"] == 0 else "inv", e["limbs"]): e["ms"]
+                                     for e in table if e["op"] == "ntt_small"}}
     x = attention_logits(L, n, seed=seeds["inputs"])
     src = g.encrypt(x, n, m, M, seeds["encrypt"])
     work = g.like(src)
@@ -550,6 +556,9 @@ def main():
             work2.level, work2.scale, work2.n_ct = src.level, src.scale, src.n_ct
             g.softmax(work2, pl, graph=True)
 
+        # with branches on side streams, events around a launch would also time the kernels that
+        # overlap it: the roofline graph runs every launch on one stream
+        g.tune_force("branches", 0)
         g.profile_kernel(args.profile_kernel)
         step_prof()   # eager run + capture with the events inside
         step_prof()
@@ -564,6 +573,7 @@ def main():
         prof_ms_step = evp[0].elapsed_time(evp[1]) / args.steps
         k_ms, k_launch, k_bytes = g.profile_read()   # the last replay's events
         g.profile_kernel("")
+        g.tune_force("branches", -1)
         del work2
         # plain mode: the same operation list one ciphertext at a time
         plain_ms = None
@@ -579,8 +589,10 @@ def main():
         # per-family and per-phase breakdown of one more (untimed) step: CUDA events around every launch
         breakdown, phases = None, None
         if not args.no_breakdown:
+            g.tune_force("branches", 0)   # one stream: the per-launch times add up to the step
             g.profile_kernel("all")
             step(True, graph=False)
+            g.tune_force("branches", -1)
             breakdown, phases = {}, {}
             for fam, (nl, ms, b) in g.profile_breakdown().items():
                 if fam.startswith("phase:"):

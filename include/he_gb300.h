@@ -265,7 +265,14 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
  * more; 0: per digit), HE_TUNE_ROT (1: the key switches of several hoisted rotations in one
  * inner-product launch and one ModDown; 0: one per rotation), HE_TUNE_LT_SMALL (1: one ModUp of all
  * giant-step sums of a bootstrapping linear-transform level; 0: one per giant step),
- * HE_TUNE_LT_ROWS (1: linear-transform inner sums without shared-memory staging; 0: staged).
+ * HE_TUNE_LT_ROWS (1: linear-transform inner sums without shared-memory staging; 0: staged),
+ * HE_TUNE_BRANCHES (1: independent branches of a circuit -- the halves of a split polynomial, the
+ * basis elements of one layer and the two halves of every Chebyshev division of a polynomial
+ * evaluation -- on side streams, concurrently, and as parallel branches of a captured graph; 0:
+ * one stream; he_tune_force only, on by default), HE_TUNE_NTT_SMALL (1: transforms in CTAs of 64
+ * threads instead of 256; he_autotune times both on a ladder of limb counts (1 .. 2048) per
+ * direction, and a transform takes the choice of the largest ladder count at or below its limb
+ * count; 256 until tuned; table entries (HE_TUNE_NTT_SMALL, limbs, 0 forward / 1 inverse)).
  * Without a table entry the choice is 1 for batches of at most 4 ciphertexts (8 rows for
  * HE_TUNE_LT_ROWS).
  * he_autotune times both variants of every operation on the device (CUDA events on the context
@@ -278,6 +285,8 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
 #define HE_TUNE_ROT 1
 #define HE_TUNE_LT_SMALL 2
 #define HE_TUNE_LT_ROWS 3
+#define HE_TUNE_BRANCHES 4
+#define HE_TUNE_NTT_SMALL 5
 int he_autotune(he_ctx *ctx, const int *levels, int n_levels, const int *ncts, int n_ncts, int reps);
 /* the table as text, one line "op limbs n_ct choice ms_variant0 ms_variant1" per entry, into buf
  * (len bytes, NUL-terminated; HE_EINVAL if too small) */

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -140,12 +141,17 @@ struct he_ctx {
         float ms[2];
     };
     std::map<std::tuple<int, int, int>, TuneRec> tune;
-    int tune_force[4] = {-1, -1, -1, -1};
+    int tune_force[6] = {-1, -1, -1, -1, -1, -1};
+    // CTA size of the transforms per direction (forward, inverse): the autotuner's choice at each
+    // limb count of its ladder; a launch takes the choice of the largest ladder count <= its own
+    std::vector<std::pair<int, int>> ntt_small[2];
     cudaStream_t st = nullptr;
     // side streams for independent branches of a circuit (Branch), created on first use
-    cudaStream_t side[2] = {nullptr, nullptr};
-    cudaEvent_t fork_ev[2] = {nullptr, nullptr}, join_ev[2] = {nullptr, nullptr};
-    int branch_depth = 0;   // > 0 while a Branch is open
+    static const int NSIDE = 4;
+    cudaStream_t side[NSIDE] = {};
+    cudaEvent_t fork_ev[NSIDE] = {}, join_ev[NSIDE] = {};
+    int branch_depth = 0;   // > 0 while a Branch is entered
+    int next_side = 0;      // round-robin choice of the side stream for the next branch
     std::string err;
     long cnt[5] = {0, 0, 0, 0, 0};
     long launches = 0;
@@ -275,7 +281,11 @@ struct Branch {
     cudaStream_t main;
     int i;
     bool joined = false, inside = false;
-    Branch(he_ctx *c_, int i_) : c(c_), main(c_->st), i(i_) {
+    // side stream i, or the next one round-robin with i < 0
+    bool on;
+    Branch(he_ctx *c_, int i_ = -1)
+        : c(c_), main(c_->st), i(i_ >= 0 ? i_ : c_->next_side++ % he_ctx::NSIDE), on(c_->tune_force[HE_TUNE_BRANCHES] != 0) {
+        if (!on) return;   // serial: everything stays on the context stream
         if (!c->side[i]) {
             CK(cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
             CK(cudaEventCreateWithFlags(&c->fork_ev[i], cudaEventDisableTiming));
@@ -285,19 +295,20 @@ struct Branch {
         CK(cudaStreamWaitEvent(c->side[i], c->fork_ev[i], 0));
     }
     void enter() {
+        if (!on) return;
         c->st = c->side[i];
         c->branch_depth++;
         inside = true;
     }
     void leave() {
-        if (!inside) return;
+        if (!on || !inside) return;
         inside = false;
         c->branch_depth--;
         c->st = main;
     }
     void join() {
         leave();
-        if (joined) return;
+        if (!on || joined) return;
         joined = true;
         cudaEventRecord(c->join_ev[i], c->side[i]);
         cudaStreamWaitEvent(main, c->join_ev[i], 0);
@@ -326,7 +337,12 @@ static dim3 grid_for(he_ctx *c, long total) {
 //   HE_TUNE_LT_SMALL  1: one ModUp of every giant-step sum of a linear-transform level and one
 //                     launch summing their inner products; 0: a ModUp per giant step
 //   HE_TUNE_LT_ROWS   1: inner sums without shared-memory staging; 0: staged diagonal tiles
-// Defaults (no table entry): 1 for batches of at most 4 ciphertexts (8 rows for LT_ROWS).
+//   HE_TUNE_BRANCHES  1: independent branches of a circuit on side streams (Branch); 0: every
+//                     launch on the context stream, in the same order as the host issues it
+//   HE_TUNE_NTT_SMALL 1: the transform in CTAs of 64 threads (4 sub-transforms each); 0: 256
+//                     threads.  Chosen per direction from a ladder of limb counts (ntt_small).
+// Defaults (no table entry): 1 for batches of at most 4 ciphertexts (8 rows for LT_ROWS);
+// branches on.
 static int tune_pick(he_ctx *c, int op, int L, int nct, int dflt) {
     if (c->tune_force[op] >= 0) return c->tune_force[op];
     auto it = c->tune.find(std::make_tuple(op, L, nct));
@@ -389,8 +405,15 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     // inverse); algorithmic bytes: the transform's read + write of every limb, 16 N per limb
     ProfScope ps(c, inverse ? ntt_inv_family(site) : site, 16.0 * count * c->N);
     c->launches++;
+    bool small = false;
+    if (c->tune_force[HE_TUNE_NTT_SMALL] >= 0) {
+        small = c->tune_force[HE_TUNE_NTT_SMALL] == 1;
+    } else {
+        for (const auto &e : c->ntt_small[inverse ? 1 : 0])   // ascending limb counts
+            if (e.first <= count) small = e.second == 1;
+    }
     launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
-                  c->d_ninv, c->logN, c->st, src, src_stride, fuse);
+                  c->d_ninv, c->logN, c->st, src, src_stride, fuse, small);
     LAUNCH_CHECK();
 }
 
@@ -745,12 +768,14 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     return y;
 }
 
-static void tensor_into(he_ctx *c, uint64_t *d, const DCt &a, const DCt &b, int level, bool accumulate) {
+// d[i] = a[i] (x) b[i / bdiv] for the a.nct ciphertexts of a (bdiv = a.nct: b's one ciphertext
+// with every one of a), limbs 0..level of each
+static void tensor_into(he_ctx *c, uint64_t *d, const DCt &a, const DCt &b, int level, bool accumulate, int bdiv = 1) {
     int L = level + 1;
     long tot = (long)a.nct * L << c->logN;
-    ProfScope ps(c, "tensor", 8.0 * c->N * (double)a.nct * L * (2 + 2 + 3));
-    k_tensor<<<grid_for(c, tot), 256, 0, c->st>>>(d, 3L * L * c->N, a.d, a.cs(c), b.d, b.cs(c), a.nct, L, qmap(L),
-                                                   c->d_mods, c->logN, accumulate ? 1 : 0);
+    ProfScope ps(c, "tensor", 8.0 * c->N * L * ((double)a.nct * (2 + 3) + 2.0 * (a.nct / bdiv)));
+    k_tensor<<<grid_for(c, tot), 256, 0, c->st>>>(d, 3L * L * c->N, a.d, a.cs(c), b.d, b.cs(c), b.ps(c), bdiv, a.nct, L,
+                                                   qmap(L), c->d_mods, c->logN, accumulate ? 1 : 0);
     LAUNCH_CHECK();
 }
 
@@ -764,10 +789,9 @@ static DCt hmult(he_ctx *c, const DCt &a, const DCt &b) {
     if (a.nct == b.nct) {
         tensor_into(c, d.get(), a, b, level, false);
     } else {
-        // one operand shared by every ciphertext of the other batch
+        // one operand shared by every ciphertext of the other batch: one launch
         const DCt &many = a.nct > 1 ? a : b, &one = a.nct > 1 ? b : a;
-        for (int i = 0; i < nct; i++)
-            tensor_into(c, d.get() + (long)i * 3 * (level + 1) * c->N, ct_sub(c, many, i), one, level, false);
+        tensor_into(c, d.get(), many, one, level, false, many.nct);
     }
     DCt r = relin_rescale(c, d.get(), level, nct, a.scale * b.scale);
     c->cnt[2]++;
@@ -780,8 +804,7 @@ static DCt hmult_grouped(he_ctx *c, const DCt &lam, const DCt &y, int m) {
     REQUIRE(level >= 1, HE_ELEVEL, "hmult at level 0");
     REQUIRE(y.nct == lam.nct * m, HE_EINVAL, "hmult_grouped: batch sizes");
     DPtr d = dalloc(c, (size_t)y.nct * 3 * (level + 1) * c->N);
-    for (int i = 0; i < y.nct; i++)
-        tensor_into(c, d.get() + (long)i * 3 * (level + 1) * c->N, ct_sub(c, y, i), ct_sub(c, lam, i / m), level, false);
+    tensor_into(c, d.get(), y, lam, level, false, m);   // ciphertext i of y with lam[i / m], one launch
     DCt r = relin_rescale(c, d.get(), level, y.nct, lam.scale * y.scale);
     c->cnt[2]++;
     return r;
@@ -1147,6 +1170,9 @@ struct PolyEval {
         auto it = T.find(k);
         if (it != T.end()) return it->second;
         REQUIRE(k >= 1, HE_EINVAL, "getT");
+        // inside a branch every basis element must exist already (precompute): one made here could
+        // be read by another branch before this one is joined
+        REQUIRE(c->branch_depth == 0, HE_EINVAL, "polynomial evaluation: basis element not precomputed");
         if ((k & (k - 1)) == 0) {
             const DCt &h = getT(k / 2);
             DCt x = hmult(c, h, h);
@@ -1172,6 +1198,109 @@ struct PolyEval {
     static int trim(const std::vector<double> &cf, int d) {
         while (d > 0 && cf[d] == 0.0) d--;
         return d;
+    }
+
+    // the basis elements T_k that eval(cf_in, d, lt, .) reads, walking its recursion on the host
+    void collect(const std::vector<double> &cf_in, int d, int lt, std::set<int> &need) const {
+        d = trim(cf_in, d);
+        if (d < 1) return;
+        int avail = lin - lt, j = ilog2c(d + 1);
+        if (d < 8 && avail >= ilog2c(d) + 1) {
+            for (int k = 1; k <= d; k++)
+                if (cf_in[k] != 0.0) need.insert(k);
+            return;
+        }
+        int a = 1 << (j - 1);
+        std::vector<double> q(d - a + 1, 0.0), r(a, 0.0);
+        split(cf_in, d, a, q, r);
+        need.insert(a);
+        int dq = trim(q, d - a);
+        if (dq != 0) collect(q, dq, lt + 1, need);
+        int dr = trim(r, a - 1);
+        if (dr >= 1) collect(r, dr, lt, need);
+    }
+
+    // Chebyshev division p = r + T_a q (T_i = 2 T_a T_(i-a) - T_(2a-i)): q, r from the coefficients
+    static void split(const std::vector<double> &cf_in, int d, int a, std::vector<double> &q, std::vector<double> &r) {
+        q[0] = cf_in[a];
+        for (int i = 1; i <= d - a; i++) q[i] = 2.0 * cf_in[a + i];
+        for (int i = 0; i < a; i++) r[i] = cf_in[i];
+        for (int i = a + 1; i <= d; i++) r[2 * a - i] = r[2 * a - i] - cf_in[i];
+    }
+
+    static void deps(int k, int *dk, int &nd) {
+        nd = 0;
+        if ((k & (k - 1)) == 0) {
+            dk[nd++] = k / 2;
+            return;
+        }
+        int a = 1;
+        while (a * 2 < k) a *= 2;
+        dk[nd++] = a;
+        dk[nd++] = k - a;
+        dk[nd++] = a - (k - a);
+    }
+
+    // makes every T_k of need and their dependencies, layer by layer (a layer's elements depend
+    // only on earlier layers); the elements of one layer are computed concurrently, one on the
+    // main stream and the others on side streams
+    void precompute(std::set<int> need) {
+        std::vector<int> todo(need.begin(), need.end());
+        while (!todo.empty()) {   // closure under deps
+            int k = todo.back();
+            todo.pop_back();
+            int dk[3], nd;
+            if (k <= 1) continue;
+            deps(k, dk, nd);
+            for (int i = 0; i < nd; i++)
+                if (dk[i] >= 1 && !need.count(dk[i])) {
+                    need.insert(dk[i]);
+                    todo.push_back(dk[i]);
+                }
+        }
+        std::map<int, int> layer;
+        layer[1] = 0;
+        int maxl = 0;
+        for (int k : need) {   // ascending: dependencies are smaller
+            if (k <= 1) continue;
+            int dk[3], nd, l = 0;
+            deps(k, dk, nd);
+            for (int i = 0; i < nd; i++) l = std::max(l, layer.count(dk[i]) ? layer[dk[i]] : 0);
+            layer[k] = l + 1;
+            maxl = std::max(maxl, l + 1);
+        }
+        for (int l = 1; l <= maxl; l++) {
+            std::vector<int> ks;
+            for (int k : need)
+                if (k > 1 && layer[k] == l && !T.count(k)) ks.push_back(k);
+            std::vector<std::unique_ptr<Branch>> br;
+            for (size_t i = 1; i < ks.size(); i++) br.emplace_back(new Branch(c));   // all fork here
+            for (size_t i = 0; i < ks.size(); i++) {
+                if (i > 0) br[i - 1]->enter();
+                T[ks[i]] = makeT(ks[i]);
+                if (i > 0) br[i - 1]->leave();
+            }
+            for (auto &b : br) b->join();
+        }
+    }
+
+    // T_k from its dependencies (all present)
+    DCt makeT(int k) {
+        if ((k & (k - 1)) == 0) {
+            const DCt &h = T.at(k / 2);
+            DCt x = hmult(c, h, h);
+            ct_mul_int(c, x, 2);
+            ct_add_const(c, x, h_round(-x.scale));
+            return x;
+        }
+        int a = 1;
+        while (a * 2 < k) a *= 2;
+        int b = k - a;
+        DCt p = hmult(c, T.at(a), T.at(b));
+        ct_mul_int(c, p, 2);
+        DCt s = adjust(T.at(a - b), p.level, p.scale);
+        ct_add_inplace(c, p, s, true);
+        return p;
     }
 
     // sum_k round(cf_k st q / scale_k) T_k + round(cf_0 st q) at level lt + 1, then rescale:
@@ -1218,13 +1347,13 @@ struct PolyEval {
         if (d < 8 && avail >= ilog2c(d) + 1) return lincomb(cf_in, d, lt, st);
         int a = 1 << (j - 1);
         std::vector<double> q(d - a + 1, 0.0), r(a, 0.0);
-        q[0] = cf_in[a];
-        for (int i = 1; i <= d - a; i++) q[i] = 2.0 * cf_in[a + i];
-        for (int i = 0; i < a; i++) r[i] = cf_in[i];
-        for (int i = a + 1; i <= d; i++) r[2 * a - i] = r[2 * a - i] - cf_in[i];
+        split(cf_in, d, a, q, r);
         getT(a);
-        int dq = trim(q, d - a);
+        int dq = trim(q, d - a), dr = trim(r, a - 1);
         DCt out;
+        // T_a q and r are independent: with both present, T_a q runs on a side stream beside r
+        std::unique_ptr<Branch> bq(dq != 0 && dr >= 1 ? new Branch(c) : nullptr);
+        if (bq) bq->enter();
         if (dq == 0) {
             std::vector<double> tmp(a + 1, 0.0);
             tmp[a] = q[0];
@@ -1234,9 +1363,10 @@ struct PolyEval {
             DCt Q = eval(q, dq, lt + 1, sq);
             out = hmult(c, T[a], Q);   // T_a's limbs above Q's level are not read
         }
-        int dr = trim(r, a - 1);
+        if (bq) bq->leave();
         if (dr >= 1) {
             DCt R = eval(r, dr, lt, st);
+            if (bq) bq->join();
             ct_add_inplace(c, out, R);
         } else {
             ct_add_const(c, out, h_round(r[0] * out.scale));
@@ -1250,6 +1380,9 @@ static DCt poly_eval(he_ctx *c, const DCt &u, const std::vector<double> &cf, int
     pe.c = c;
     pe.T[1] = u;
     pe.lin = u.level;
+    std::set<int> need;
+    pe.collect(cf, (int)cf.size() - 1, level_out, need);
+    pe.precompute(need);
     return pe.eval(cf, (int)cf.size() - 1, level_out, scale_out);
 }
 
@@ -2295,6 +2428,28 @@ static void autotune(he_ctx *c, const std::vector<int> &levels, const std::vecto
             }
         }
     }
+    // transforms: 64- against 256-thread CTAs, per direction, over a ladder of limb counts; a
+    // launch then takes the choice of the largest ladder count at or below its own
+    {
+        const int counts[] = {1, 2, 4, 6, 8, 10, 12, 16, 20, 25, 32, 40, 50, 64, 100, 128, 256, 512, 1024, 2048};
+        const int maxc = 2048;
+        DPtr buf = dalloc(c, (size_t)maxc * c->N);
+        {
+            ProfScope ps_(c, "keygen", 0);
+            k_sample_uniform<<<grid_for(c, (long)maxc << c->logN), 256, 0, c->st>>>(
+                buf.get(), 0, maxc, 1, qmap(1), c->d_mods, 0x5eedULL, 0x70e1ULL, c->logN);
+        }
+        LAUNCH_CHECK();
+        for (int inv = 0; inv < 2; inv++) {
+            std::vector<std::pair<int, int>> ladder;
+            for (int n : counts) {
+                tune_op(c, HE_TUNE_NTT_SMALL, n, inv, reps,
+                        [&] { ntt(c, buf.get(), n, qmap(1), c->N, inv != 0); });
+                ladder.push_back({n, c->tune[std::make_tuple(HE_TUNE_NTT_SMALL, n, inv)].choice});
+            }
+            c->ntt_small[inv] = ladder;
+        }
+    }
     CK(cudaStreamSynchronize(c->st));
     // the tuner's own work is not counted, and its diagonal encodings are dropped
     for (auto it = c->lt_cache.begin(); it != c->lt_cache.end();) {
@@ -2395,7 +2550,7 @@ void he_context_destroy(he_ctx *c) {
     }
     c->pt_cache.clear();
     c->lt_cache.clear();
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < he_ctx::NSIDE; i++)
         if (c->side[i]) {
             cudaStreamSynchronize(c->side[i]);
             cudaStreamDestroy(c->side[i]);
@@ -3033,7 +3188,7 @@ int he_tune_table(const he_ctx *ctx, char *buf, size_t len) {
 }
 
 int he_tune_force(he_ctx *ctx, int op, int choice) {
-    if (!ctx || op < 0 || op > 3 || choice < -1 || choice > 1) return HE_EINVAL;
+    if (!ctx || op < 0 || op > HE_TUNE_NTT_SMALL || choice < -1 || choice > 1) return HE_EINVAL;
     ctx->tune_force[op] = choice;
     return HE_OK;
 }

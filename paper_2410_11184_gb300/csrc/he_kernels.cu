@@ -63,10 +63,12 @@ __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int npe
     }
 }
 
-// tensor of ciphertext batches a, b (each [ct][2][nper][N] with their own strides) into
-// d [ct][3][nper][N]; accumulate adds into d
-__global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
-                         int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate) {
+// tensor of ciphertext batches a, b into d [ct][3][nper][N]: ciphertext c of a (stride sa, two
+// polynomials of sa/2 words) with ciphertext c / bdiv of b (stride sb, polynomial stride psb):
+// bdiv = 1 pairs them one to one, bdiv = m pairs every m of a with one of b (nct: one b for all);
+// accumulate adds into d
+__global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb, long psb,
+                         int bdiv, int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate) {
     const int N = 1 << logN;
     long total = (long)nct * nper << logN;
     for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
@@ -75,8 +77,8 @@ __global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const
         const ModC m = mods[map.prime[li]];
         long off = (long)li * N + k;
         // each ciphertext holds 2 (inputs) or 3 (output) polynomials: poly stride = ct stride / #polys
-        const uint64_t *pa = a + c * sa, *pb = b + c * sb;
-        long psa = sa / 2, psb = sb / 2, ps = sd / 3;
+        const uint64_t *pa = a + c * sa, *pb = b + (c / bdiv) * sb;
+        long psa = sa / 2, ps = sd / 3;
         uint64_t a0 = pa[off], a1 = pa[psa + off], b0 = pb[off], b1 = pb[psb + off];
         uint64_t d0 = mul_mod(a0, b0, m);
         uint64_t d1 = add_mod(mul_mod(a0, b1, m), mul_mod(a1, b0, m), m.q);
@@ -785,12 +787,12 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
 }
 
 // Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
-template <int LOGE, int KIND>
-__global__ void __launch_bounds__(256, 3) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+template <int LOGE, int KIND, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride, NttFuse F) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
-    constexpr int SUB = 256 / TPS;                         // columns per CTA
+    constexpr int SUB = NT / TPS;                         // columns per CTA
     __shared__ uint64_t sm[S * SUB];
     const int N = 1 << logN, N2 = N / S;
     const int l = blockIdx.y, p = map.prime[l % nper];
@@ -828,12 +830,12 @@ __global__ void __launch_bounds__(256, 3) k_ntt_cols_fwd_rb(uint64_t *base, int 
 }
 
 // Forward row pass: stages m = N1 .. N/2 on rows of S = N2 contiguous coefficients.
-template <int LOGE, int KIND>
-__global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+template <int LOGE, int KIND, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          NttFuse F) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
-    constexpr int SUB = 256 / TPS;                         // rows per CTA
+    constexpr int SUB = NT / TPS;                         // rows per CTA
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
     constexpr int SP = S + S / E;
     __shared__ uint64_t sm[SP * SUB];
@@ -912,12 +914,12 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_fwd_rb(uint64_t *base, int 
 }
 
 // Inverse row pass: stages h = N/2 .. N1 (t = 1 .. N2/2).
-template <int LOGE>
-__global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+template <int LOGE, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
-    constexpr int SUB = 256 / TPS;
+    constexpr int SUB = NT / TPS;
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
     constexpr int SP = S + S / E;
     __shared__ uint64_t sm[SP * SUB];
@@ -950,12 +952,12 @@ __global__ void __launch_bounds__(256, 3) k_ntt_rows_inv_rb(uint64_t *base, int 
 }
 
 // Inverse column pass: stages h = N1/2 .. 1, then the N^{-1} factor.
-template <int LOGE>
-__global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
+template <int LOGE, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv,
                                                          int logN) {
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
-    constexpr int SUB = 256 / TPS;
+    constexpr int SUB = NT / TPS;
     __shared__ uint64_t sm[S * SUB];
     const int N = 1 << logN, N2 = N / S;
     const int l = blockIdx.y, p = map.prime[l % nper];
@@ -978,35 +980,42 @@ __global__ void __launch_bounds__(256) k_ntt_cols_inv_rb(uint64_t *base, int npe
     for (int j = 0; j < E; j++) a[(long)(k + E * j) * N2 + col] = mul_shoup(v[j], ni, nip, q);
 }
 
-template <int LOGE>
+// NT threads per CTA: 256 (16 sub-transforms per CTA at N = 2^16), or 64 for transforms of few
+// limbs, whose 256-thread grids leave SMs idle (four times as many, smaller CTAs)
+template <int LOGE, int NT>
 static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
                       const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
                       const uint64_t *src, long src_stride, const NttFuse &F) {
-    constexpr int E = 1 << LOGE, S = E * E, SUB = 256 / E;
+    constexpr int E = 1 << LOGE, S = E * E, SUB = NT / E;
     dim3 g(((1 << logN) / S) / SUB, count);
     if (!inverse && F.kind == 1) {
-        k_ntt_cols_fwd_rb<LOGE, 1><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 1><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        k_ntt_cols_fwd_rb<LOGE, 1, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 1, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse && F.kind == 3) {
-        k_ntt_cols_fwd_rb<LOGE, 3><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 3><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        k_ntt_cols_fwd_rb<LOGE, 3, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 3, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse && F.kind == 2) {
-        k_ntt_cols_fwd_rb<LOGE, 2><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 2><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        k_ntt_cols_fwd_rb<LOGE, 2, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 2, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse) {
-        k_ntt_cols_fwd_rb<LOGE, 0><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 0><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        k_ntt_cols_fwd_rb<LOGE, 0, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        k_ntt_rows_fwd_rb<LOGE, 0, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else {
-        k_ntt_rows_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
-        k_ntt_cols_inv_rb<LOGE><<<g, 256, 0, st>>>(base, nper, poly_stride, map, mods, tw2, ninv, logN);
+        k_ntt_rows_inv_rb<LOGE, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
+        k_ntt_cols_inv_rb<LOGE, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, ninv, logN);
     }
 }
 
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
                    const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
-                   const uint64_t *src, long src_stride, const NttFuse *fuse) {
+                   const uint64_t *src, long src_stride, const NttFuse *fuse, bool small_cta) {
     NttFuse F{};
     if (fuse) F = *fuse;
-    if (logE == 4) launch_rb<4>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
-    else launch_rb<3>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
+    if (logE == 4) {
+        if (small_cta) launch_rb<4, 64>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
+        else launch_rb<4, 256>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
+    } else {
+        if (small_cta) launch_rb<3, 64>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
+        else launch_rb<3, 256>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
+    }
 }

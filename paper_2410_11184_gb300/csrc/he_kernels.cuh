@@ -82,8 +82,8 @@ __global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa,
                              int count, int nper, LimbMap map, const ModC *mods, int logN);
 __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int nper, LimbMap map,
                              const ModC *mods, int logN);
-__global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb,
-                         int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
+__global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb, long psb,
+                         int bdiv, int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate);
 __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN);
 __global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal, int count, int nper,
                               LimbMap map, const ModC *mods, int logN);
@@ -143,4 +143,5 @@ void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *
 // tw2: per modulus p, N (psi^brv(k), Shoup companion) pairs at tw2 + 2 N p, then N inverse pairs
 void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
                    const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
-                   const uint64_t *src = nullptr, long src_stride = 0, const NttFuse *fuse = nullptr);
+                   const uint64_t *src = nullptr, long src_stride = 0, const NttFuse *fuse = nullptr,
+                   bool small_cta = false);

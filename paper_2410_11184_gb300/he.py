@@ -414,7 +414,7 @@ class Context:
         return out
 
     # ---- autotuner (launch strategies; every variant gives the same words)
-    TUNE_OPS = ("modup", "rot", "lt_small", "lt_rows")
+    TUNE_OPS = ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small")
 
     def autotune(self, levels, ncts, reps=2):
         lv = np.ascontiguousarray(levels, dtype=np.int32)
@@ -433,7 +433,8 @@ class Context:
         return out
 
     def tune_force(self, op, choice):
-        """forces variant `choice` (0 or 1) of op ("modup", "rot", "lt_small", "lt_rows"); -1 restores"""
+        """forces variant `choice` (0 or 1) of op ("modup", "rot", "lt_small", "lt_rows", "branches",
+        "ntt_small"); -1 restores"""
         self.check(lib().he_tune_force(self.h, self.TUNE_OPS.index(op), choice))
 
     def selftest_bounded_wait(self, max_iter):

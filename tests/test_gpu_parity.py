@@ -366,9 +366,10 @@ def test_softmax_alg4_split_shares_equal_unsplit(toybts, split):
 
 def test_autotune_variants_bit_identical(toybts):
     """Every launch strategy the autotuner chooses between gives the same words: each variant of
-    each operation forced in turn on multiplications, hoisted rotations and SlotToCoeff /
-    CoeffToSlot levels at batch sizes 1, 2 and 6; then he_autotune fills its table (one entry
-    per timed operation, level and batch size) and results stay the same."""
+    each operation forced in turn (branches on side streams or one stream, transform CTA size) on
+    multiplications, hoisted rotations, SlotToCoeff / CoeffToSlot levels and a degree-31
+    polynomial at batch sizes 1, 2 and 6; then he_autotune fills its table (one entry per timed
+    operation, level and batch size) and results stay the same."""
     g, o, em = toybts
     rng = np.random.default_rng(31)
     top = len(o.q) - 1
@@ -381,13 +382,15 @@ def test_autotune_variants_bit_identical(toybts):
             out.append(g.to_coeff(g.hmult(a, a)))
             out.append(g.to_coeff(g.lintrans(a, 3, False, 0, 16.0, float(o.q[3]))))
             out.append(g.to_coeff(g.lintrans(b, 3, True, 1, 1.0, float(o.q[top]))))
+            u = g.from_coeff(_rand_ct(o, 20, rng_fixed(nct + 20), nct), 20, float(o.q[20]))
+            out.append(g.to_coeff(g.poly_eval(u, np.linspace(0.3, -0.2, 32), 15, 2.0 ** 42)))
         return out
 
     def rng_fixed(k):
         return np.random.default_rng(1000 + k)
 
     ref = run()
-    for op in ("modup", "rot", "lt_small", "lt_rows"):
+    for op in ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small"):
         for choice in (0, 1):
             g.tune_force(op, choice)
             got = run()
@@ -397,10 +400,12 @@ def test_autotune_variants_bit_identical(toybts):
     g.autotune([3, top - 1, top], [1, 6], reps=1)
     table = g.tune_table()
     ops = {e["op"] for e in table}
-    assert ops == {"modup", "rot", "lt_small", "lt_rows"}, ops
+    assert ops == {"modup", "rot", "lt_small", "lt_rows", "ntt_small"}, ops
     assert all(e["choice"] in (0, 1) and min(e["ms"]) > 0 for e in table)
     assert {(e["limbs"], e["n_ct"]) for e in table if e["op"] == "modup"} == {(4, 1), (4, 6), (top, 1), (top, 6),
                                                                                  (top + 1, 1), (top + 1, 6)}
+    # transform CTA size: both directions (n_ct holds the direction) over the limb-count ladder
+    assert {e["n_ct"] for e in table if e["op"] == "ntt_small"} == {0, 1}
     got = run()
     for x, y in zip(ref, got):
         assert np.array_equal(x, y)
