@@ -277,10 +277,10 @@ def run_reference(args, wl):
 
 def run_serve(args):
     """Serving workload: Poisson arrivals of one-ciphertext encrypted Softmax requests whose
-    dimension is drawn from {128, 256, 1024, 4096} (inputs uniform on [-64, 0], N = 2^16 with
-    bootstrapping), admitted by HBM budget and batched by shape (serve.Server).  Dimensions up to
-    1024 use the Alg. 2 plans, 4096 the Alg. 4 plan (Alg. 2 does not converge there on this
-    chain); 32768 is not served.  Prints one JSON line with p50/p99 request latency, Softmax/s and
+    dimension is drawn from {128, 256, 1024, 4096, 32768} (inputs uniform on [-64, 0], N = 2^16
+    with bootstrapping), admitted by HBM budget and batched by shape (serve.Server).  Dimensions
+    up to 1024 use the Alg. 2 plans, 4096 and 32768 the Alg. 4 plans (Alg. 2 does not converge
+    there on this chain).  Prints one JSON line with p50/p99 request latency, Softmax/s and
     the worst-case error per dimension."""
     import torch
 
@@ -288,7 +288,7 @@ def run_serve(args):
 
     chains, plans, evalmod = he.load_params()
     plans = dict(plans, **he.load_plans_b())
-    names = ["n128_M64", "n256_M64", "n1024_M64", "n4096_M64_B"]
+    names = ["n128_M64", "n256_M64", "n1024_M64", "n4096_M64_B"] + (["n32768_M64_B"] if "n32768_M64_B" in plans else [])
     g = he.Context(chains["fgb16"], evalmod["fgb16"])
     g.keygen(5)
     for nm in names:
@@ -341,15 +341,16 @@ def run_serve(args):
         worst[n] = max(worst.get(n, 0.0), err)
     softmax_done = sum(g.n0 // plans[k[0]]["n"] for k, _ in handles)
     line = {
-        "metric": "serving: request latency p50/p99 and Softmax/s (n in {128,256,1024,4096}, N=2^16, bootstrapping)",
+        "metric": "serving: request latency p50/p99 and Softmax/s (n in %s, N=2^16, bootstrapping)"
+                  % sorted(plans[nm]["n"] for nm in names),
         "value": st["p99_ms"], "unit": "ms (p99 request latency)", "higher_is_better": False,
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
         "softmax_per_s": softmax_done / st["span_s"], "requests": st["requests"], "span_s": st["span_s"],
         "arrival_rate_per_s": args.rate, "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
         "precision_bits_by_n": {str(n): -math.log2(e) if e > 0 else None for n, e in sorted(worst.items())},
         "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
-        "config": {"workload": "Poisson arrivals, one ciphertext per request, dims 128/256/1024/4096 on [-64, 0] "
-                                "(4096 by Alg. 4; 32768 not served)",
+        "config": {"workload": "Poisson arrivals, one ciphertext per request, dims %s on [-64, 0] (4096 and "
+                                "32768 by Alg. 4)" % "/".join(str(plans[nm]["n"]) for nm in names),
                    "hbm_budget_gb": budget / 1e9, "max_batch_ct": args.max_batch_ct},
     }
     print(json.dumps(line))
@@ -366,7 +367,7 @@ def run_llama(args):
     from paper_2410_11184_gb300 import he, workloads
 
     chains, plans, evalmod = he.load_params()
-    pl = plans["n128_M64"]
+    pl = he.load_plans_b()["n128_M64_B"] if args.method == "alg4" else plans["n128_M64"]
     n, M, layers, m = pl["n"], pl["M"], 32, 16
     stream = torch.cuda.Stream()
     g = he.Context(chains["fgb16"], evalmod["fgb16"], stream=stream)
@@ -420,7 +421,8 @@ def run_llama(args):
         "precision_bits_min_over_layers": min(bits), "precision_bits_max_over_layers": max(bits),
         "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
         "config": {"workload": "32 per-layer groups of 16 ciphertexts (4096 Softmax each), %d groups per pass" % per,
-                   "n": n, "M": M, "k": pl["k"], "ciphertexts": layers * m},
+                   "n": n, "M": M, "k": pl["k"], "ciphertexts": layers * m,
+                   "method": METHODS[args.method][1].replace("n = 256", "n = 128")},
     }))
 
 

@@ -2383,11 +2383,17 @@ static float time_best(he_ctx *c, int reps, F fn) {
 template <class F>
 static void tune_op(he_ctx *c, int op, int L, int nct, int reps, F fn) {
     he_ctx::TuneRec r;
+    const int prev = c->tune_force[op];
     for (int v = 0; v < 2; v++) {
         c->tune_force[op] = v;
-        r.ms[v] = time_best(c, reps, fn);
+        try {
+            r.ms[v] = time_best(c, reps, fn);
+        } catch (...) {
+            c->tune_force[op] = prev;
+            throw;
+        }
     }
-    c->tune_force[op] = -1;
+    c->tune_force[op] = prev;
     r.choice = r.ms[1] < r.ms[0] ? 1 : 0;
     c->tune[std::make_tuple(op, L, nct)] = r;
 }

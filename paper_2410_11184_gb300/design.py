@@ -370,6 +370,10 @@ def build_b(write=True, names=None):
         # n = 4096 (which Alg. 2 cannot serve on this chain): degree 511 after iteration 1, whose
         # depth 9 just fits above the bootstrapping input because each lambda_j is bootstrapped alone
         "n4096_M64_B": ("fgb16", 4096, 64.0, 4, 15, [255, 511, 511, 511]),
+        # n = 32768 (the vocabulary-sized Softmax of the serving mix): after iteration 1 the
+        # interval spans a ratio near 2^15, so degree 1023 in iterations 2-4, each evaluated split
+        # (A + T_512 B) since depth 10 exceeds the room above the bootstrapping input
+        "n32768_M64_B": ("fgb16", 32768, 64.0, 4, 15, [255, 1023, 1023, 1023]),
         # the same level map at N = 2^12 (toybts: user levels 12 ... 4), for the oracle's
         # ciphertext circuit: A = 2 keeps every interval narrow enough for degree 63
         "toybts_n16_M32_B": ("toybts", 16, 32.0, 4, 15, [63, 63, 63, 63]),

@@ -227,13 +227,19 @@ def test_fullsize_llama_layer_shape_precision(full, params, plan):
         assert err < 2 ** -15, (plan, i, -math.log2(err))
 
 
-@pytest.mark.parametrize("n", [1024, 4096])
+@pytest.mark.parametrize("n", [1024, 4096, 32768])
 def test_fullsize_large_dimension_alg4_precision(full, n):
-    """Dimensions of the serving mix that Alg. 2 cannot serve on this chain (n = 4096) or
-    serves with little margin (n = 1024): Alg. 4 with one bootstrapping of every lambda_j, on
-    one ciphertext of N0/n Softmax of uniform inputs on [-64, 0], two requests grouped."""
+    """Dimensions of the serving mix that Alg. 2 cannot serve on this chain (n = 4096, 32768) or
+    serves with little margin (n = 1024): Alg. 4 with one bootstrapping of every lambda_j (and
+    the split evaluation of its degree-1023 rounds at n = 32768), on one ciphertext of N0/n
+    Softmax of uniform inputs on [-64, 0], two requests grouped.  At least 15 bits against FP64
+    Softmax up to n = 4096; n = 32768 is reported and held to 10 bits (the paper reaches 12.8
+    bits absolute there, Sec. 5.2.5)."""
     g, ch, em = full
-    pl = he.load_plans_b()["n%d_M64_B" % n]
+    plans_b = he.load_plans_b()
+    if "n%d_M64_B" % n not in plans_b:
+        pytest.skip("plan n%d_M64_B not designed" % n)
+    pl = plans_b["n%d_M64_B" % n]
     M = pl["M"]
     g.keygen_softmax(n, 1)
     L = g.n0 // n
@@ -245,4 +251,5 @@ def test_fullsize_large_dimension_alg4_precision(full, n):
     for i, x in enumerate(xs):
         one = he.Ciphertexts(g, batch.tensor[i * w:(i + 1) * w], batch.level, batch.scale, 1)
         err = np.abs(g.decrypt(one, n) - O.softmax_fp64(x)).max()
-        assert err < 2 ** -15, (n, i, -math.log2(err))
+        print("n = %d, request %d: %.2f bits against FP64 Softmax" % (n, i, -math.log2(err)))
+        assert err < 2 ** (-15 if n <= 4096 else -10), (n, i, -math.log2(err))
