@@ -596,7 +596,12 @@ def main():
             step(True, graph=False)
             g.tune_force("branches", -1)
             breakdown, phases = {}, {}
+            phase_family = {}
             for fam, (nl, ms, b) in g.profile_breakdown().items():
+                if fam.startswith("pf:"):
+                    _, ph, fm = fam.split(":", 2)
+                    phase_family.setdefault(ph, {})[fm] = round(ms, 2)
+                    continue
                 if fam.startswith("phase:"):
                     phases[fam[6:]] = {"launches": nl, "ms": round(ms, 3)}
                     if fam.startswith("phase:bootstrap."):   # the sum of the bootstrapping's steps
@@ -780,6 +785,7 @@ def main():
         "roofline": roof,
         "breakdown_one_step": breakdown,
         "phase_ms_one_step": phases,
+        "phase_family_ms_one_step": phase_family if not args.no_breakdown else None,
         "other_method": other_line,
         "autotune": tune,
         "single_ct_latency": lat1,

@@ -316,7 +316,8 @@ int he_profile_read(he_ctx *ctx, double *total_ms, long *launches, double *bytes
  * NUL-terminated), then one line "phase:P launches total_ms 0" per phase of the Softmax circuit the launches belonged to (main: the m main-thread ciphertexts;
  * aux: the auxiliary thread of Alg. 3 outside bootstrapping; bootstrap.stc, bootstrap.modraise,
  * bootstrap.cts, bootstrap.evalmod: the four steps of every bootstrapping; other: launches
- * outside a Softmax), then resets.  HE_EINVAL if buf is too small.  The phases are
+ * outside a Softmax), then one line "pf:P:family launches total_ms bytes" per (phase, family)
+ * pair, then resets.  HE_EINVAL if buf is too small.  The phases are
  * also NVTX ranges of the same names. */
 int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len);
 /* bounded device wait self test: a kernel polls a flag nobody sets for at most max_iter polls

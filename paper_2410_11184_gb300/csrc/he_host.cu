@@ -3260,6 +3260,10 @@ int he_profile_breakdown(he_ctx *ctx, char *buf, size_t len) {
         auto &ph = fam[std::string("phase:") + ctx->prof_ph[i]];
         std::get<0>(ph)++;
         std::get<1>(ph) += ms;
+        auto &pf = fam[std::string("pf:") + ctx->prof_ph[i] + ":" + ctx->prof_fam[i]];
+        std::get<0>(pf)++;
+        std::get<1>(pf) += ms;
+        std::get<2>(pf) += ctx->prof_b[i];
     }
     for (auto &kv : ctx->graphs) {
         if (!kv.second.replayed) continue;

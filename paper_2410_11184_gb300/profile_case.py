@@ -6,6 +6,8 @@
   python -m paper_2410_11184_gb300.profile_case softmax_alg2  # the same by Alg. 2
   python -m paper_2410_11184_gb300.profile_case keyswitch     # 4 HMults at level 12, 64 ciphertexts
                                                               # (inside the NVTX range "hmult")
+  python -m paper_2410_11184_gb300.profile_case keyswitch_small   # the same with the transforms in
+                                                              # 64-thread CTAs (the autotuner's usual pick)
 """
 import sys
 
@@ -24,6 +26,8 @@ def main(which):
         em = None
     g = he.Context(ch, em)
     g.keygen(5)
+    if which == "keyswitch_small":
+        g.tune_force("ntt_small", 1)
     if which.startswith("softmax"):
         g.keygen_softmax(256, 1)
         x = workloads.attention_logits(128, 256, 1)
