@@ -111,30 +111,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the two forward NTT passes per
-# algorithmic byte (16 N per limb), from one capture of a 320-limb ModUp transform at N = 2^16
-# (python -m paper_2410_11184_gb300.profile_case keyswitch): 1.733 MB per 1.049 MB limb
-NTT_DRAM_PER_ALG_BYTE = 1.733e6 / (16 * 65536)
+# DRAM bytes per limb (ncu dram__bytes_read.sum + dram__bytes_write.sum of both passes over the
+# limbs of the launch) of the N = 2^16 transforms in 64-thread CTAs, the autotuner's usual pick:
+# forward (167.9 + 112.8 + 173.1 + 107.6) MB over 320 limbs, inverse (409.2 + 341.9 + 402.9 + 347.3)
+# MB over 768 limbs (python -m paper_2410_11184_gb300.profile_case keyswitch_small)
+NTT_DRAM_PER_LIMB = {"fwd": (167.870464 + 112.770048 + 173.091072 + 107.571712) * 1e6 / 320,
+                     "inv": (409.172224 + 341.905664 + 402.891520 + 347.335424) * 1e6 / 768}
 
-
-# Warp instructions per limb of the N = 2^16 transforms (ncu sass__inst_executed_per_opcode /
-# smsp__inst_executed.sum of one capture, divided by the limbs of the launch): forward = column
-# pass + row pass of a 320-limb ModUp transform (76 513 280 + 86 999 040 over 320 limbs; python -m
-# paper_2410_11184_gb300.profile_case keyswitch); inverse = the two inverse passes of a 768-limb
-# ModUp transform of the same case (196 018 176 + 242 712 576 over 768 limbs)
-# (profiles/ntt_instruction_mix_n65536.txt).  The NTT is bound by integer instruction
-# issue (64-bit modular butterflies on 32-bit pipes), so its roofline is the SM issue limit:
-# 152 SMs x 4 sub-partitions x 1 warp instruction per cycle x 2070 MHz (the SM count and maximum
-# SM clock of GB300; four schedulers per SM on this architecture).
-NTT_WARP_INSTR_PER_LIMB = {"fwd": (76513280 + 86999040) / 320, "inv": (196018176 + 242712576) / 768}
+# Warp instructions per limb of the N = 2^16 transforms (ncu smsp__inst_executed.sum of both passes
+# of one capture, divided by the limbs of the launch), same captures: forward (63 283 200 +
+# 72 744 960) over 320 limbs, inverse (166 232 064 + 210 173 952) over 768 limbs
+# (profiles/ntt_instruction_mix_n65536.txt).  The NTT is bound by integer instruction issue (64-bit
+# modular butterflies on 32-bit pipes), so its roofline is the SM issue limit: 152 SMs x 4
+# sub-partitions x 1 warp instruction per cycle x 2070 MHz (the SM count and maximum SM clock of
+# GB300; four schedulers per SM on this architecture).
+NTT_WARP_INSTR_PER_LIMB = {"fwd": (63283200 + 72744960) / 320, "inv": (166232064 + 210173952) / 768}
 ISSUE_PEAK_G = 152 * 4 * 2.070   # G warp instructions / s
 
-# integer pipes of the NTT passes (both forward passes of a 320-limb ModUp transform at N = 2^16,
-# weighted by their durations 105 / 131 us; ncu SpeedOfLight / ComputeWorkloadAnalysis /
-# SchedulerStats sections, python -m paper_2410_11184_gb300.profile_case keyswitch):
-# sm__pipe_alu_cycles_active, sm__pipe_fma_cycles_active (IMAD), smsp__issue_active, in % of peak
-NTT_INT_PIPES = {"alu_pct": 51.3, "fma_imad_pct": 38.1, "issue_active_pct": 57.3,
-                 "source": "ncu, k_ntt_{cols,rows}_fwd_rb<4,0> on 320 limbs (profiles/ntt_rb_keyswitch_m64_level12.txt)"}
+# integer pipes of the NTT passes (ncu, same captures): issue active of the four passes weighted by
+# their durations; ALU / FMA (IMAD) pipe cycles of the forward passes in 256-thread CTAs
+NTT_INT_PIPES = {"issue_active_pct": 52.8, "alu_pct": 40.3, "fma_imad_pct": 38.3,
+                 "source": "ncu, k_ntt_{cols,rows}_{fwd,inv}_rb<4> (profiles/ntt_instruction_mix_n65536.txt)"}
 
 # circuits: the plan file entry each method evaluates at n = 256 on [-128, 0]
 METHODS = {"alg4": ("n256_M128_B", "Alg. 4 (version B) + Alg. 3 auxiliary thread, Sec. 4.3"),
@@ -738,7 +735,7 @@ def main():
     roof = None
     if k_launch:
         gbs = (k_bytes / k_launch) / ((k_ms / k_launch) * 1e-3) / 1e9
-        traffic = (k_bytes / k_launch) * NTT_DRAM_PER_ALG_BYTE if args.profile_kernel == "ntt" else None
+        traffic = None
         hbm_view = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                     "peak_kind": peak_kind, "algorithmic_bytes": "16 N per limb (read + write)"}
         roof = dict(hbm_view, kernel=args.profile_kernel, traffic=traffic)
@@ -748,7 +745,9 @@ def main():
             fwd = sum(v["bytes"] for k, v in breakdown.items() if k.startswith("ntt") and not k.endswith("_inv")) / lb
             inv = sum(v["bytes"] for k, v in breakdown.items() if k.startswith("ntt") and k.endswith("_inv")) / lb
             per_limb = (fwd * NTT_WARP_INSTR_PER_LIMB["fwd"] + inv * NTT_WARP_INSTR_PER_LIMB["inv"]) / (fwd + inv)
+            dram_limb = (fwd * NTT_DRAM_PER_LIMB["fwd"] + inv * NTT_DRAM_PER_LIMB["inv"]) / (fwd + inv)
             limbs = k_bytes / lb   # the timed replay's limbs
+            traffic = dram_limb * limbs / k_launch   # DRAM bytes per launch
             ach = limbs * per_limb / (k_ms * 1e-3) / 1e9
             roof = {"bound": "alu", "kernel": "ntt", "achieved": ach, "peak": ISSUE_PEAK_G,
                     "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G, "traffic": traffic,

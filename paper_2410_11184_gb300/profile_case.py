@@ -2,7 +2,8 @@
 
   python -m paper_2410_11184_gb300.profile_case softmax       # one N=2^16 Softmax of dim 256 (1 ciphertext),
                                                               # Alg. 4, inside the NVTX range "softmax"
-                                                              # (a first call outside fills the caches)
+                                                              # (a first call outside fills the caches;
+                                                              # transforms in 64-thread CTAs)
   python -m paper_2410_11184_gb300.profile_case softmax_alg2  # the same by Alg. 2
   python -m paper_2410_11184_gb300.profile_case keyswitch     # 4 HMults at level 12, 64 ciphertexts
                                                               # (inside the NVTX range "hmult")
@@ -26,8 +27,8 @@ def main(which):
         em = None
     g = he.Context(ch, em)
     g.keygen(5)
-    if which == "keyswitch_small":
-        g.tune_force("ntt_small", 1)
+    if which in ("keyswitch_small", "softmax", "softmax_alg2"):
+        g.tune_force("ntt_small", 1)   # the transforms' 64-thread CTAs, the autotuner's pick at almost every size
     if which.startswith("softmax"):
         g.keygen_softmax(256, 1)
         x = workloads.attention_logits(128, 256, 1)
