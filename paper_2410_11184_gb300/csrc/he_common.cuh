@@ -32,6 +32,18 @@ struct LimbMap {
     int prime[HE_MAX_LIMBS];        // modulus index of limb i of each polynomial
 };
 
+// Programmatic dependent launch.  Every kernel of the library starts with grid_dep_enter():
+// it waits until the grid it follows in its stream has completed and its writes are visible
+// (griddepcontrol.wait; a no-op when the launch carries no programmatic dependency), and only
+// then lets the next kernel of the stream be scheduled (griddepcontrol.launch_dependents).
+// No kernel touches memory before the wait, so every launch sees the same memory as in plain
+// stream order; the next grid's launch and the first CTAs it places on SMs that this grid's
+// last wave has left overlap the end of this grid.
+__device__ __forceinline__ void grid_dep_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t he_mulhi(uint64_t a, uint64_t b) {
     return (uint64_t)__umul64hi((unsigned long long)a, (unsigned long long)b);
 }

@@ -493,7 +493,7 @@ static void ct_add_inplace(he_ctx *c, DCt &a, const DCt &b, bool sub = false) {
     long total = (long)count << c->logN;
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_add<<<grid_for(c, total), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), b.d, b.ps(c), count, a.level + 1, m,
+        klaunch(k_add, grid_for(c, total), 256, 0, c->st)(a.d, a.ps(c), a.d, a.ps(c), b.d, b.ps(c), count, a.level + 1, m,
                                                       c->d_mods, c->logN, sub ? 1 : 0);
     }
     LAUNCH_CHECK();
@@ -510,7 +510,7 @@ static void ct_mul_int(he_ctx *c, DCt &a, i128 k) {
     Scal s = scal_of(c, k, L);
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), s, count, L,
+        klaunch(k_mul_scalar, grid_for(c, (long)count << c->logN), 256, 0, c->st)(a.d, a.ps(c), a.d, a.ps(c), s, count, L,
                                                                               qmap(L), c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
@@ -522,7 +522,7 @@ static void ct_add_const(he_ctx *c, DCt &a, i128 k) {
     Scal s = scal_of(c, k, L);
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_add_scalar<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.cs(c), s, count, L, qmap(L),
+        klaunch(k_add_scalar, grid_for(c, (long)count << c->logN), 256, 0, c->st)(a.d, a.cs(c), s, count, L, qmap(L),
                                                                               c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
@@ -532,7 +532,7 @@ static void ct_mul_plain(he_ctx *c, DCt &a, const uint64_t *pt) {
     int L = a.level + 1, count = 2 * a.nct * L;
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul<<<grid_for(c, (long)count << c->logN), 256, 0, c->st>>>(a.d, a.ps(c), a.d, a.ps(c), pt, 0, count, L, qmap(L),
+        klaunch(k_mul, grid_for(c, (long)count << c->logN), 256, 0, c->st)(a.d, a.ps(c), a.d, a.ps(c), pt, 0, count, L, qmap(L),
                                                                        c->d_mods, c->logN, 0);
     }
     LAUNCH_CHECK();
@@ -576,10 +576,10 @@ static void rescale_noalloc(he_ctx *c, const DCt &a, uint64_t *out) {
                          cudaMemcpyDeviceToDevice, c->st));
     ntt(c, last, npoly, single(l), c->N, true);
     long tot = (long)npoly * l << c->logN;
-    k_rescale_spread<<<grid_for(c, tot), 256, 0, c->st>>>(tmp, last, npoly, l, qmap(l), c->d_mods, c->mods[l], c->logN);
+    klaunch(k_rescale_spread, grid_for(c, tot), 256, 0, c->st)(tmp, last, npoly, l, qmap(l), c->d_mods, c->mods[l], c->logN);
     LAUNCH_CHECK();
     ntt(c, tmp, npoly * l, qmap(l), (long)l * c->N, false);
-    k_rescale_fin<<<grid_for(c, tot), 256, 0, c->st>>>(out, a.d, tmp, npoly, L, qmap(l), c->d_mods,
+    klaunch(k_rescale_fin, grid_for(c, tot), 256, 0, c->st)(out, a.d, tmp, npoly, L, qmap(l), c->d_mods,
                                                         c->d_qlinv + (size_t)l * 2 * c->nq, c->logN);
     LAUNCH_CHECK();
     c->cnt[3]++;
@@ -607,7 +607,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
         dim3 grid(grid_for(c, (long)nct << c->logN).x, nd);
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * L + (double)nct * nd * nl));
-            k_modup_all<<<grid, 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, tmp.get(), (long)L * c->N, nct, D, nl,
+            klaunch(k_modup_all, grid, 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, tmp.get(), (long)L * c->N, nct, D, nl,
                                                  em, c->d_mods, c->d_cv + c->cv_off[L - 1][0], c->logN);
         }
         LAUNCH_CHECK();
@@ -619,7 +619,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
         long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * 2 * ds + (double)nct * nl));
-            k_modup<<<grid_for(c, tot), 256, 0, c->st>>>(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
+            klaunch(k_modup, grid_for(c, tot), 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
                                                           tmp.get(), (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
                                                           c->d_cv + c->cv_off[L - 1][j], c->logN, x, sx);
         }
@@ -665,7 +665,7 @@ static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, 
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (al + L));
-        k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(conv.get(), acc, 2 * nct, L, al, qmap(L),
+        klaunch(k_moddown_conv, grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st)(conv.get(), acc, 2 * nct, L, al, qmap(L),
                                                                                   c->d_pidx, c->d_mods, c->d_mdcv,
                                                                                   c->nq, c->logN);
     }
@@ -732,7 +732,7 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     for (int p = 0; p < 2; p++) {
         {
             ProfScope ps_(c, "elementwise", 0);
-            k_axpy_scalar<<<grid_for(c, (long)nct << c->logN), 256, 0, c->st>>>(
+            klaunch(k_axpy_scalar, grid_for(c, (long)nct << c->logN), 256, 0, c->st)(
                 acc.get() + (long)p * nl * c->N + (long)l * c->N, 2L * nl * c->N, d + (long)p * L * c->N + (long)l * c->N,
                 3L * L * c->N, pm, nct, 1, single(l), c->d_mods, c->logN);
         }
@@ -747,7 +747,7 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     DPtr conv = dalloc(c, (size_t)2 * nct * l * c->N);
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (nd + l));
-        k_moddown_conv<<<grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st>>>(
+        klaunch(k_moddown_conv, grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st)(
             conv.get(), acc.get(), 2 * nct, l, nd, qmap(l), c->d_rridx + (size_t)l * nd, c->d_mods,
             c->d_rrcv + (size_t)l * c->rrcv_stride, c->nq, c->logN);
     }
@@ -774,7 +774,7 @@ static void tensor_into(he_ctx *c, uint64_t *d, const DCt &a, const DCt &b, int 
     int L = level + 1;
     long tot = (long)a.nct * L << c->logN;
     ProfScope ps(c, "tensor", 8.0 * c->N * L * ((double)a.nct * (2 + 3) + 2.0 * (a.nct / bdiv)));
-    k_tensor<<<grid_for(c, tot), 256, 0, c->st>>>(d, 3L * L * c->N, a.d, a.cs(c), b.d, b.cs(c), b.ps(c), bdiv, a.nct, L,
+    klaunch(k_tensor, grid_for(c, tot), 256, 0, c->st)(d, 3L * L * c->N, a.d, a.cs(c), b.d, b.cs(c), b.ps(c), bdiv, a.nct, L,
                                                    qmap(L), c->d_mods, c->logN, accumulate ? 1 : 0);
     LAUNCH_CHECK();
 }
@@ -818,7 +818,7 @@ static void automorph_acc(he_ctx *c, DCt &y, const DCt &x, int g) {
     long tot = (long)x.nct * L << c->logN;
     {
         ProfScope ps_(c, "automorph", 0);
-        k_automorph_acc<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, y.cs(c), x.d, x.cs(c), x.nct * L, L, qmap(L),
+        klaunch(k_automorph_acc, grid_for(c, tot), 256, 0, c->st)(y.d, y.cs(c), x.d, x.cs(c), x.nct * L, L, qmap(L),
                                                               c->d_mods, g, c->logN);
     }
     LAUNCH_CHECK();
@@ -911,7 +911,7 @@ static DCt mod_raise(he_ctx *c, const DCt &a, int top) {
     long tot = (long)npoly * L << c->logN;
     {
         ProfScope ps_(c, "modraise", 0);
-        k_modraise<<<grid_for(c, tot), 256, 0, c->st>>>(y.d, x0.get(), npoly, L, qmap(L), c->d_mods, c->mods[0], c->logN);
+        klaunch(k_modraise, grid_for(c, tot), 256, 0, c->st)(y.d, x0.get(), npoly, L, qmap(L), c->d_mods, c->mods[0], c->logN);
     }
     LAUNCH_CHECK();
     ntt(c, y.d, npoly * L, qmap(L), (long)L * c->N, false, "ntt_modraise");
@@ -929,15 +929,15 @@ static DPtr encode(he_ctx *c, const std::vector<double2> &z, double scale, int l
     {
         ProfScope ps_(c, "encode", 0);
         for (int len = n0; len >= 2; len >>= 1)
-            k_sfft_inv_stage<<<g, 256, 0, c->st>>>(wd, n0, len, c->d_zeta, c->d_rg, 2 * c->N);
-        k_bitrev_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, c->logN - 1);
-        k_scale_c<<<grid_for(c, n0), 256, 0, c->st>>>(wd, n0, (double)n0);
+            klaunch(k_sfft_inv_stage, g, 256, 0, c->st)(wd, n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+        klaunch(k_bitrev_c, grid_for(c, n0), 256, 0, c->st)(wd, n0, c->logN - 1);
+        klaunch(k_scale_c, grid_for(c, n0), 256, 0, c->st)(wd, n0, (double)n0);
     }
     LAUNCH_CHECK();
     DPtr pt = dalloc(c, (size_t)L * c->N);
     {
         ProfScope ps_(c, "encode", 0);
-        k_round_to_limbs<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(pt.get(), 0, wd, scale, L, L, qmap(L),
+        klaunch(k_round_to_limbs, grid_for(c, (long)L << c->logN), 256, 0, c->st)(pt.get(), 0, wd, scale, L, L, qmap(L),
                                                                              c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
@@ -949,7 +949,7 @@ static DPtr encode(he_ctx *c, const std::vector<double2> &z, double scale, int l
 static void small_to_ntt(he_ctx *c, uint64_t *out, const int64_t *v, const LimbMap &m) {
     {
         ProfScope ps_(c, "encode", 0);
-        k_small_to_limbs<<<grid_for(c, (long)m.nper << c->logN), 256, 0, c->st>>>(out, 0, v, m.nper, m.nper, m, c->d_mods,
+        klaunch(k_small_to_limbs, grid_for(c, (long)m.nper << c->logN), 256, 0, c->st)(out, 0, v, m.nper, m.nper, m, c->d_mods,
                                                                                    c->logN);
     }
     LAUNCH_CHECK();
@@ -964,7 +964,7 @@ static uint64_t dom_key(int key_id, int digit, int which) {
 static void sample_small(he_ctx *c, int64_t *out, uint64_t seed, uint64_t dom, uint64_t ctr0, int kind) {
     {
         ProfScope ps_(c, "keygen", 0);
-        k_sample_small<<<grid_for(c, c->N), 256, 0, c->st>>>(out, c->N, seed, dom, ctr0, c->d_cdt, c->cdt_len, kind);
+        klaunch(k_sample_small, grid_for(c, c->N), 256, 0, c->st)(out, c->N, seed, dom, ctr0, c->d_cdt, c->cdt_len, kind);
     }
     LAUNCH_CHECK();
 }
@@ -991,23 +991,23 @@ static void encrypt_into(he_ctx *c, const std::vector<double2> &z, int level, do
     const uint64_t *pkb = c->d_pk, *pka = c->d_pk + (long)c->nq * c->N;
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, vn, 0, pkb, 0, L, L, m, c->d_mods, c->logN, 0);
+        klaunch(k_mul, grid_for(c, tot), 256, 0, c->st)(c0, 0, vn, 0, pkb, 0, L, L, m, c->d_mods, c->logN, 0);
     }
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, vn, 0, pka, 0, L, L, m, c->d_mods, c->logN, 0);
+        klaunch(k_mul, grid_for(c, tot), 256, 0, c->st)(c1, 0, vn, 0, pka, 0, L, L, m, c->d_mods, c->logN, 0);
     }
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, e0n, 0, L, L, m, c->d_mods, c->logN, 0);
+        klaunch(k_add, grid_for(c, tot), 256, 0, c->st)(c0, 0, c0, 0, e0n, 0, L, L, m, c->d_mods, c->logN, 0);
     }
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c0, 0, c0, 0, pt.get(), 0, L, L, m, c->d_mods, c->logN, 0);
+        klaunch(k_add, grid_for(c, tot), 256, 0, c->st)(c0, 0, c0, 0, pt.get(), 0, L, L, m, c->d_mods, c->logN, 0);
     }
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(c1, 0, c1, 0, e1n, 0, L, L, m, c->d_mods, c->logN, 0);
+        klaunch(k_add, grid_for(c, tot), 256, 0, c->st)(c1, 0, c1, 0, e1n, 0, L, L, m, c->d_mods, c->logN, 0);
     }
     LAUNCH_CHECK();
 }
@@ -1020,11 +1020,11 @@ static std::vector<double2> decrypt_slots(he_ctx *c, const DCt &x, int i) {
     long tot = (long)L << c->logN;
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, c1, 0, c->d_s, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+        klaunch(k_mul, grid_for(c, tot), 256, 0, c->st)(m.get(), 0, c1, 0, c->d_s, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
     }
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_add<<<grid_for(c, tot), 256, 0, c->st>>>(m.get(), 0, m.get(), 0, c0, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
+        klaunch(k_add, grid_for(c, tot), 256, 0, c->st)(m.get(), 0, m.get(), 0, c0, 0, L, L, qmap(L), c->d_mods, c->logN, 0);
     }
     LAUNCH_CHECK();
     ntt(c, m.get(), L, qmap(L), (long)L * c->N, true);
@@ -1032,14 +1032,14 @@ static std::vector<double2> decrypt_slots(he_ctx *c, const DCt &x, int i) {
     double2 *wd = (double2 *)w.get();
     {
         ProfScope ps_(c, "decode", 0);
-        k_crt_to_double<<<grid_for(c, c->N), 128, 0, c->st>>>(wd, m.get(), L, qmap(L), c->d_mods, c->d_radix, c->d_radinv,
+        klaunch(k_crt_to_double, grid_for(c, c->N), 128, 0, c->st)(wd, m.get(), L, qmap(L), c->d_mods, c->d_radix, c->d_radinv,
                                                               c->d_qd, x.scale, c->logN);
     }
     {
         ProfScope ps_(c, "decode", 0);
-        k_bitrev_c<<<grid_for(c, c->n0), 256, 0, c->st>>>(wd, c->n0, c->logN - 1);
+        klaunch(k_bitrev_c, grid_for(c, c->n0), 256, 0, c->st)(wd, c->n0, c->logN - 1);
         for (int len = 2; len <= c->n0; len <<= 1)
-            k_sfft_fwd_stage<<<grid_for(c, c->n0 / 2), 256, 0, c->st>>>(wd, c->n0, len, c->d_zeta, c->d_rg, 2 * c->N);
+            klaunch(k_sfft_fwd_stage, grid_for(c, c->n0 / 2), 256, 0, c->st)(wd, c->n0, len, c->d_zeta, c->d_rg, 2 * c->N);
     }
     LAUNCH_CHECK();
     std::vector<double2> z(c->n0);
@@ -1055,7 +1055,7 @@ static void keygen(he_ctx *c, uint64_t seed) {
     DPtr sint = dalloc(c, N);
     {
         ProfScope ps_(c, "keygen", 0);
-        k_sample_hwt<<<(N + 255) / 256, 256, 256 * 8, c->st>>>((int64_t *)sint.get(), N, c->h, seed, DOM_SK, DOM_SK_SIGN);
+        klaunch(k_sample_hwt, (N + 255) / 256, 256, 256 * 8, c->st)((int64_t *)sint.get(), N, c->h, seed, DOM_SK, DOM_SK_SIGN);
     }
     LAUNCH_CHECK();
     if (!c->d_s) CK(cudaMalloc(&c->d_s, (size_t)nm * N * 8));
@@ -1069,7 +1069,7 @@ static void keygen(he_ctx *c, uint64_t seed) {
     small_to_ntt(c, el.get(), (int64_t *)e.get(), qm);
     {
         ProfScope ps_(c, "keygen", 0);
-        k_sample_uniform<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pka, 0, c->nq, c->nq, qm, c->d_mods, seed,
+        klaunch(k_sample_uniform, grid_for(c, (long)c->nq << c->logN), 256, 0, c->st)(pka, 0, c->nq, c->nq, qm, c->d_mods, seed,
                                                                                   DOM_PK_A, c->logN);
     }
     LAUNCH_CHECK();
@@ -1078,7 +1078,7 @@ static void keygen(he_ctx *c, uint64_t seed) {
     memset(&z0, 0, sizeof z0);
     {
         ProfScope ps_(c, "keygen", 0);
-        k_key_combine<<<grid_for(c, (long)c->nq << c->logN), 256, 0, c->st>>>(pkb, pka, el.get(), c->d_s, nullptr, z0, c->nq,
+        klaunch(k_key_combine, grid_for(c, (long)c->nq << c->logN), 256, 0, c->st)(pkb, pka, el.get(), c->d_s, nullptr, z0, c->nq,
                                                                                0, 0, qm, c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
@@ -1096,12 +1096,12 @@ static void make_key(he_ctx *c, int galois) {
     if (galois == 0)
         {
             ProfScope ps_(c, "elementwise", 0);
-            k_mul<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, c->d_s, 0, nm, nm, am, c->d_mods, c->logN, 0);
+            klaunch(k_mul, grid_for(c, tot), 256, 0, c->st)(sp.get(), 0, c->d_s, 0, c->d_s, 0, nm, nm, am, c->d_mods, c->logN, 0);
         }
     else
         {
             ProfScope ps_(c, "automorph", 0);
-            k_automorph<<<grid_for(c, tot), 256, 0, c->st>>>(sp.get(), 0, c->d_s, 0, nm, nm, galois, c->logN);
+            klaunch(k_automorph, grid_for(c, tot), 256, 0, c->st)(sp.get(), 0, c->d_s, 0, nm, nm, galois, c->logN);
         }
     LAUNCH_CHECK();
     Scal pm;
@@ -1116,7 +1116,7 @@ static void make_key(he_ctx *c, int galois) {
         small_to_ntt(c, el.get(), (int64_t *)e.get(), am);
         {
             ProfScope ps_(c, "keygen", 0);
-            k_sample_uniform<<<grid_for(c, tot), 256, 0, c->st>>>(a, 0, nm, nm, am, c->d_mods, c->seed, dom_key(galois, j, 0),
+            klaunch(k_sample_uniform, grid_for(c, tot), 256, 0, c->st)(a, 0, nm, nm, am, c->d_mods, c->seed, dom_key(galois, j, 0),
                                                                    c->logN);
         }
         LAUNCH_CHECK();
@@ -1124,7 +1124,7 @@ static void make_key(he_ctx *c, int galois) {
         int dlo = j * c->alpha, dhi = std::min((j + 1) * c->alpha, c->nq);
         {
             ProfScope ps_(c, "keygen", 0);
-            k_key_combine<<<grid_for(c, tot), 256, 0, c->st>>>(b, a, el.get(), c->d_s, sp.get(), pm, nm, dlo, dhi, am,
+            klaunch(k_key_combine, grid_for(c, tot), 256, 0, c->st)(b, a, el.get(), c->d_s, sp.get(), pm, nm, dlo, dhi, am,
                                                                 c->d_mods, c->logN);
         }
         LAUNCH_CHECK();
@@ -1135,7 +1135,7 @@ static void make_key(he_ctx *c, int galois) {
     for (int t = 0; t < nm; t++) rm.v[t] = h_mont(1, c->mods[t]);
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul_scalar<<<grid_for(c, (long)2 * nd * nm << c->logN), 256, 0, c->st>>>(key, (long)nm * N, key, (long)nm * N, rm, 2 * nd * nm, nm, am,
+        klaunch(k_mul_scalar, grid_for(c, (long)2 * nd * nm << c->logN), 256, 0, c->st)(key, (long)nm * N, key, (long)nm * N, rm, 2 * nd * nm, nm, am,
                                                                                   c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
@@ -1159,7 +1159,7 @@ struct PolyEval {
         Scal s = scal_of(c, h_round((st * q) / x.scale), L);
         {
             ProfScope ps_(c, "elementwise", 0);
-            k_mul_scalar<<<grid_for(c, (long)2 * x.nct * L << c->logN), 256, 0, c->st>>>(
+            klaunch(k_mul_scalar, grid_for(c, (long)2 * x.nct * L << c->logN), 256, 0, c->st)(
                 y.d, y.ps(c), x.d, x.ps(c), s, 2 * x.nct * L, L, qmap(L), c->d_mods, c->logN);
         }
         LAUNCH_CHECK();
@@ -1331,7 +1331,7 @@ struct PolyEval {
         DCt out = ct_new(c, lt + 1, nct, st * q);
         {
             ProfScope ps_(c, "elementwise", 0);
-            k_lincomb<<<grid_for(c, (long)nct * 2 * L << c->logN), 256, 0, c->st>>>(out.d, A, nct, L, qmap(L),
+            klaunch(k_lincomb, grid_for(c, (long)nct * 2 * L << c->logN), 256, 0, c->st)(out.d, A, nct, L, qmap(L),
                                                                                      c->d_mods, c->logN);
         }
         LAUNCH_CHECK();
@@ -1471,7 +1471,7 @@ static void to_mont(he_ctx *c, uint64_t *pt, int L) {
     for (int l = 0; l < L; l++) rm.v[l] = h_mont(1, c->mods[l]);
     {
         ProfScope ps_(c, "elementwise", 0);
-        k_mul_scalar<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(pt, 0, pt, 0, rm, L, L, qmap(L), c->d_mods,
+        klaunch(k_mul_scalar, grid_for(c, (long)L << c->logN), 256, 0, c->st)(pt, 0, pt, 0, rm, L, L, qmap(L), c->d_mods,
                                                                           c->logN);
     }
     LAUNCH_CHECK();
@@ -1601,10 +1601,10 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         size_t smem = (size_t)A.npt * HE_LT_KT * 8;
         ProfScope ps_(c, "lintrans", 8.0 * c->N * ((double)L * A.npt + (double)x.nct * 2 * L * (A.nb + A.na)));
         if (tune_pick(c, HE_TUNE_LT_ROWS, L, x.nct, 2 * x.nct <= 8))   // a few rows: no staging
-            k_lt_bsgs_direct<<<grid_for(c, (long)L << c->logN), 256, 0, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods,
+            klaunch(k_lt_bsgs_direct, grid_for(c, (long)L << c->logN), 256, 0, c->st)(A, 2 * x.nct, L, qmap(L), c->d_mods,
                                                                                  c->logN);
         else
-            k_lt_bsgs<<<grid, 256, smem, c->st>>>(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
+            klaunch(k_lt_bsgs, grid, 256, smem, c->st)(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
     }
     LAUNCH_CHECK();
     // acc = sum_a Rot(out_a, a g hmin): the c0(X^g) parts are added over Q_l, the key-switch
@@ -1647,7 +1647,7 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
             {
                 ProfScope ps(c, "ks_inner", 8.0 * c->N * M.n * ((double)x.nct * nd * nl + 2.0 * nd * nl) +
                                                 8.0 * c->N * 2.0 * x.nct * nl);
-                k_ks_inner_sum<<<grid_for(c, (long)nl << c->logN), 256, 0, c->st>>>(
+                klaunch(k_ks_inner_sum, grid_for(c, (long)nl << c->logN), 256, 0, c->st)(
                     ext.get(), dig.get(), x.nct, nd, L, al, extmap(c, L), c->d_mods, c->nm, c->nq, c->logN, M);
             }
             LAUNCH_CHECK();
@@ -1817,7 +1817,7 @@ static DPtr tensor_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
                 const uint64_t *acc = i == 1 ? dd.get() + (long)g * m * t3 : d.get() + g * t3;
                 {
                     ProfScope ps_(c, "elementwise", 0);
-                    k_add<<<grid_for(c, t3), 256, 0, c->st>>>(d.get() + g * t3, (long)L * c->N, acc, (long)L * c->N,
+                    klaunch(k_add, grid_for(c, t3), 256, 0, c->st)(d.get() + g * t3, (long)L * c->N, acc, (long)L * c->N,
                                                                dd.get() + ((long)g * m + i) * t3, (long)L * c->N,
                                                                3 * L, L, qmap(L), c->d_mods, c->logN, 0);
                 }
@@ -1845,7 +1845,7 @@ static DPtr tensor_sum(he_ctx *c, const std::vector<DCt> &ys, int m, int G) {
                     }
                 else {
                     ProfScope ps_(c, "elementwise", 0);
-                    k_add<<<grid_for(c, tot), 256, 0, c->st>>>(d.get(), (long)L * c->N, d.get(), (long)L * c->N,
+                    klaunch(k_add, grid_for(c, tot), 256, 0, c->st)(d.get(), (long)L * c->N, d.get(), (long)L * c->N,
                                                                 dd.get() + (long)i * 3 * L * c->N, (long)L * c->N,
                                                                 cnt, L, qmap(L), c->d_mods, c->logN, 0);
                 }
@@ -2410,7 +2410,7 @@ static void autotune(he_ctx *c, const std::vector<int> &levels, const std::vecto
             DCt x = ct_new(c, lv, nct, 1.0);
             {
                 ProfScope ps_(c, "keygen", 0);
-                k_sample_uniform<<<grid_for(c, (long)2 * nct * L << c->logN), 256, 0, c->st>>>(
+                klaunch(k_sample_uniform, grid_for(c, (long)2 * nct * L << c->logN), 256, 0, c->st)(
                     x.d, (long)L * c->N, 2 * nct * L, L, qmap(L), c->d_mods, 0x5eedULL + lv, 0x70e0ULL, c->logN);
             }
             LAUNCH_CHECK();
@@ -2442,7 +2442,7 @@ static void autotune(he_ctx *c, const std::vector<int> &levels, const std::vecto
         DPtr buf = dalloc(c, (size_t)maxc * c->N);
         {
             ProfScope ps_(c, "keygen", 0);
-            k_sample_uniform<<<grid_for(c, (long)maxc << c->logN), 256, 0, c->st>>>(
+            klaunch(k_sample_uniform, grid_for(c, (long)maxc << c->logN), 256, 0, c->st)(
                 buf.get(), 0, maxc, 1, qmap(1), c->d_mods, 0x5eedULL, 0x70e1ULL, c->logN);
         }
         LAUNCH_CHECK();
@@ -2869,6 +2869,12 @@ int he_softmax_graph(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts) {
         }
         cudaStream_t user = ctx->st;
         ctx->st = ctx->gstream;   // everything below is recorded into the graph
+        // plain kernel edges in the graph: its replay hides launch latency by itself
+        struct PdlOff {
+            int prev = he_pdl_launch;
+            PdlOff() { he_pdl_launch = 0; }
+            ~PdlOff() { he_pdl_launch = prev; }
+        } pdl_off;
         CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
         ctx->capturing = true;
         ctx->cap_prof.clear();
@@ -2972,7 +2978,7 @@ int he_softmax_aux_round(he_ctx *ctx, const he_softmax_plan *plan, int j, int m_
     DPtr dr = dalloc(ctx, (size_t)3 * L * ctx->N);
     {
         ProfScope ps_(ctx, "elementwise", 0);
-        k_reduce_limbs<<<grid_for(ctx, (long)3 * L << ctx->logN), 256, 0, ctx->st>>>(dr.get(), d_sum, 3 * L, L, qmap(L),
+        klaunch(k_reduce_limbs, grid_for(ctx, (long)3 * L << ctx->logN), 256, 0, ctx->st)(dr.get(), d_sum, 3 * L, L, qmap(L),
                                                                                    ctx->d_mods, ctx->logN);
     }
     he_ctx *c = ctx;
@@ -3298,7 +3304,7 @@ int he_selftest_bounded_wait(he_ctx *ctx, long max_iter) {
     DPtr b = dalloc(ctx, 1);
     int *flag = (int *)b.get(), *status = flag + 1;
     CK(cudaMemsetAsync(b.get(), 0, 8, ctx->st));
-    k_bounded_wait<<<1, 32, 0, ctx->st>>>(flag, status, max_iter);
+    klaunch(k_bounded_wait, 1, 32, 0, ctx->st)(flag, status, max_iter);
     LAUNCH_CHECK();
     int hs = 0;
     CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));

@@ -5,6 +5,8 @@
 // lives at base + (l / nper) * poly_stride + (l % nper) * N and uses modulus prime[l % nper].
 #include "he_kernels.cuh"
 
+thread_local int he_pdl_launch = 1;   // see klaunch
+
 // ------------------------------------------------------------------------------------------
 // Elementwise kernels over a batch (count limbs, addressing as above).
 #define EW_PROLOGUE                                                                           \
@@ -18,6 +20,7 @@
 
 __global__ void k_add(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
                       int count, int nper, LimbMap map, const ModC *mods, int logN, int sub) {
+    grid_dep_enter();
     EW_PROLOGUE
     long off = (long)li * N + k;
     uint64_t u = a[po * sa + off], v = b[po * sb + off];
@@ -27,6 +30,7 @@ __global__ void k_add(uint64_t *out, long so, const uint64_t *a, long sa, const 
 
 __global__ void k_mul(uint64_t *out, long so, const uint64_t *a, long sa, const uint64_t *b, long sb,
                       int count, int nper, LimbMap map, const ModC *mods, int logN, int accumulate) {
+    grid_dep_enter();
     EW_PROLOGUE
     long off = (long)li * N + k;
     uint64_t r = mul_mod(a[po * sa + off], b[po * sb + off], m);
@@ -38,6 +42,7 @@ __global__ void k_mul(uint64_t *out, long so, const uint64_t *a, long sa, const 
 // out = a * s_l with a per-limb scalar (residue of the scalar mod each modulus, by limb index)
 __global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal,
                              int count, int nper, LimbMap map, const ModC *mods, int logN) {
+    grid_dep_enter();
     EW_PROLOGUE
     long off = (long)li * N + k;
     out[po * so + off] = mul_mod(a[po * sa + off], scal.v[li], m);
@@ -47,6 +52,7 @@ __global__ void k_mul_scalar(uint64_t *out, long so, const uint64_t *a, long sa,
 // out += a * scal[li] on the selected limbs
 __global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa, Scal scal, int count, int nper,
                               LimbMap map, const ModC *mods, int logN) {
+    grid_dep_enter();
     EW_PROLOGUE
     long off = (long)li * N + k;
     out[po * so + off] = add_mod(out[po * so + off], mul_mod(a[po * sa + off], scal.v[li], m), m.q);
@@ -57,6 +63,7 @@ __global__ void k_axpy_scalar(uint64_t *out, long so, const uint64_t *a, long sa
 // has the same value at every root)
 __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int nper, LimbMap map,
                              const ModC *mods, int logN) {
+    grid_dep_enter();
     EW_PROLOGUE
     long off = (long)li * N + k;
     a[po * sa + off] = add_mod(a[po * sa + off], scal.v[li], m.q);
@@ -69,6 +76,7 @@ __global__ void k_add_scalar(uint64_t *a, long sa, Scal scal, int count, int npe
 // accumulate adds into d
 __global__ void k_tensor(uint64_t *d, long sd, const uint64_t *a, long sa, const uint64_t *b, long sb, long psb,
                          int bdiv, int nct, int nper, LimbMap map, const ModC *mods, int logN, int accumulate) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)nct * nper << logN;
     for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
@@ -104,6 +112,7 @@ __device__ __forceinline__ int auto_index(int k, int g, int logN) {
 }
 
 __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, int g, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)count << logN;
     for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
@@ -117,6 +126,7 @@ __global__ void k_automorph(uint64_t *out, long so, const uint64_t *a, long sa, 
 // out += a(X^g) on the selected limbs (the c0 part of a rotation, added to a key-switch result)
 __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long sa, int count, int nper, LimbMap map,
                                 const ModC *mods, int g, int logN) {
+    grid_dep_enter();
     EW_PROLOGUE
     long o = po * so + (long)li * N + k;
     out[o] = add_mod(out[o], a[po * sa + (long)li * N + auto_index(k, g, logN)], m.q);
@@ -130,6 +140,7 @@ __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long 
 // terms below 16 q^2 < q 2^64).  Dynamic shared memory: npt * HE_LT_KT words.
 __global__ void __launch_bounds__(256) k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods,
                                                  int logN) {
+    grid_dep_enter();
     extern __shared__ uint64_t spt[];
     constexpr int KT = HE_LT_KT, RG = 256 / KT;
     const int N = 1 << logN, ntile = N / KT;
@@ -161,6 +172,7 @@ __global__ void __launch_bounds__(256) k_lt_bsgs(LtArgs A, int npoly, int L, Lim
 // The same sums for batches of a few rows (npoly <= 8): one thread per (limb, coefficient), no
 // staging; the plaintext values of a giant step are loaded once and used for every row.
 __global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)L << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -191,6 +203,7 @@ __global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const
 // Montgomery form (sums of at most 8 products stay below q 2^64), row nt a plain residue.
 // Reads each input once (only its first L limbs).
 __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap, const ModC *mods, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)nct * 2 * L << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -217,6 +230,7 @@ __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap,
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN, const uint64_t *xntt, long sxn) {
+    grid_dep_enter();
     // one thread per (ciphertext, coefficient): the digit's limbs are read once, then every
     // target limb is produced as one 128-bit sum reduced once (cv holds the products of the
     // other digit primes in Montgomery form, so redc returns the plain sum mod m_t)
@@ -267,6 +281,7 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
 // [nct][ndig][ntarget][N] (coefficient form).
 __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long sx, int nct, ModUpDigits D,
                             int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     const int j = blockIdx.y, lo = D.lo[j], ds = D.ds[j];
     const uint64_t *cv = cvbase + D.cvoff[j];
@@ -307,6 +322,7 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
 // One thread per (polynomial, coefficient): the alpha P limbs are read once.
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)npoly << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -354,6 +370,7 @@ template <int NDIG>
 __global__ void k_ks_inner_t(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int L, int alpha,
                              LimbMap tmap, const ModC *mods, const uint64_t *__restrict__ key, int key_nlimb,
                              int nq_all, int g, int logN, int accumulate, KsMulti M) {
+    grid_dep_enter();
     const int N = 1 << logN;
     const int nl = L + alpha;
     if (M.n) {   // key switch blockIdx.y of several (same digits, own key and galois element)
@@ -401,7 +418,7 @@ void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *
                      int logN, int accumulate, const KsMulti &M) {
 #define HE_KS_CASE(D)                                                                                          \
     case D:                                                                                                    \
-        k_ks_inner_t<D><<<grid, 256, 0, st>>>(acc, dig, nct, L, alpha, tmap, mods, key, key_nlimb, nq_all, g, logN, \
+        klaunch(k_ks_inner_t<D>, grid, 256, 0, st)(acc, dig, nct, L, alpha, tmap, mods, key, key_nlimb, nq_all, g, logN, \
                                               accumulate, M);                                                  \
         break;
     switch (ndig) {
@@ -416,6 +433,7 @@ void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *
 __global__ void k_ks_inner_sum(uint64_t *__restrict__ acc, const uint64_t *__restrict__ dig, int nct, int ndig,
                                int L, int alpha, LimbMap tmap, const ModC *mods, int key_nlimb, int nq_all, int logN,
                                KsMulti M) {
+    grid_dep_enter();
     const int N = 1 << logN;
     const int nl = L + alpha;
     long total = (long)nl << logN;
@@ -451,6 +469,7 @@ __global__ void k_ks_inner_sum(uint64_t *__restrict__ acc, const uint64_t *__res
 // the remaining L-1 limbs into tmp [npoly][L-1][N].
 __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly, int Lm1, LimbMap qmap,
                                  const ModC *mods, uint64_t ql, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)npoly * Lm1 << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -466,6 +485,7 @@ __global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int npoly,
 // Rescale, step 2: out_i = (x_i - t_i) * qlinv_i (x: [nct][2][L][N], out: [nct][2][L-1][N])
 __global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *t, int npoly, int L, LimbMap qmap,
                               const ModC *mods, const uint64_t *qlinv, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     const int Lm1 = L - 1;
     long total = (long)npoly * Lm1 << logN;
@@ -481,6 +501,7 @@ __global__ void k_rescale_fin(uint64_t *out, const uint64_t *x, const uint64_t *
 // ModRaise: level-0 coefficients (centred mod q0) reduced into L limbs (coefficient form)
 __global__ void k_modraise(uint64_t *out, const uint64_t *x0, int npoly, int L, LimbMap qmap, const ModC *mods,
                            uint64_t q0, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)npoly * L << logN;
     for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
@@ -514,6 +535,7 @@ __device__ __forceinline__ uint64_t rng64(uint64_t seed, uint64_t dom, uint64_t 
 // p * N + k of domain dom; value (w0 2^64 + w1) mod q_p
 __global__ void k_sample_uniform(uint64_t *out, long so, int count, int nper, LimbMap map,
                                  const ModC *mods, uint64_t seed, uint64_t dom, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)count << logN;
     for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
@@ -529,6 +551,7 @@ __global__ void k_sample_uniform(uint64_t *out, long so, int count, int nper, Li
 // small signed samples: kind 0 = Gaussian from the cumulative table, 1 = ternary {0,0,+1,-1}
 __global__ void k_sample_small(int64_t *out, int n, uint64_t seed, uint64_t dom, uint64_t ctr0,
                                const uint64_t *cdt, int cdt_len, int kind) {
+    grid_dep_enter();
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         uint64_t r = rng64(seed, dom, ctr0 + k);
         int64_t v;
@@ -548,6 +571,7 @@ __global__ void k_sample_small(int64_t *out, int n, uint64_t seed, uint64_t dom,
 // secret with exactly h nonzeros: coefficient k is nonzero iff fewer than h pairs
 // (draw_j, j) are smaller than (draw_k, k); sign from a second domain
 __global__ void k_sample_hwt(int64_t *out, int n, int h, uint64_t seed, uint64_t dom, uint64_t dom_sign) {
+    grid_dep_enter();
     extern __shared__ uint64_t keys[];
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t mine = k < n ? rng64(seed, dom, k) : 0;
@@ -570,6 +594,7 @@ __global__ void k_sample_hwt(int64_t *out, int n, int h, uint64_t seed, uint64_t
 // signed small coefficients into residues for every limb
 __global__ void k_small_to_limbs(uint64_t *out, long so, const int64_t *v, int count, int nper, LimbMap map,
                                  const ModC *mods, int logN) {
+    grid_dep_enter();
     EW_PROLOGUE
     out[po * so + (long)li * N + k] = reduce_i64(v[k], m);
     }
@@ -582,6 +607,7 @@ __global__ void k_small_to_limbs(uint64_t *out, long so, const int64_t *v, int c
 // Built with --fmad=false: every double operation is a single IEEE operation, in the
 // order the definition writes it.
 __global__ void k_bitrev_c(double2 *v, int n0, int logn0) {
+    grid_dep_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
         int j = brev_bits(i, logn0);
         if (i < j) {
@@ -593,6 +619,7 @@ __global__ void k_bitrev_c(double2 *v, int n0, int logn0) {
 }
 
 __global__ void k_sfft_fwd_stage(double2 *v, int n0, int len, const double2 *zeta, const int *rg, int m2n) {
+    grid_dep_enter();
     int lenh = len >> 1, lenq = len << 2, gap = m2n / lenq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < (n0 >> 1); b += gridDim.x * blockDim.x) {
         int i = (b / lenh) * len, j = b % lenh;
@@ -606,6 +633,7 @@ __global__ void k_sfft_fwd_stage(double2 *v, int n0, int len, const double2 *zet
 }
 
 __global__ void k_sfft_inv_stage(double2 *v, int n0, int len, const double2 *zeta, const int *rg, int m2n) {
+    grid_dep_enter();
     int lenh = len >> 1, lenq = len << 2, gap = m2n / lenq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < (n0 >> 1); b += gridDim.x * blockDim.x) {
         int i = (b / lenh) * len, j = b % lenh;
@@ -623,6 +651,7 @@ __global__ void k_sfft_inv_stage(double2 *v, int n0, int len, const double2 *zet
 }
 
 __global__ void k_scale_c(double2 *v, int n0, double div) {
+    grid_dep_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
         v[i].x = v[i].x / div;
         v[i].y = v[i].y / div;
@@ -645,6 +674,7 @@ __device__ __forceinline__ uint64_t round_reduce(double x, const ModC &m) {
 // coefficient k of round(scale * t): t_k = Re w_k (k < N0), Im w_{k-N0} (k >= N0)
 __global__ void k_round_to_limbs(uint64_t *out, long so, const double2 *w, double scale, int count, int nper,
                                  LimbMap map, const ModC *mods, int logN) {
+    grid_dep_enter();
     EW_PROLOGUE
     int n0 = N >> 1;
     double t = k < n0 ? w[k].x : w[k - n0].y;
@@ -657,6 +687,7 @@ __global__ void k_round_to_limbs(uint64_t *out, long so, const double2 *w, doubl
 // and inverses; computed on the host.
 __global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qmap, const ModC *mods,
                                 const uint64_t *radix, const uint64_t *radinv, const double *qd, double scale, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN, n0 = N >> 1;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
         uint64_t a[HE_MAX_LIMBS], b[HE_MAX_LIMBS];
@@ -686,6 +717,7 @@ __global__ void k_crt_to_double(double2 *w, const uint64_t *x, int L, LimbMap qm
 // switching-key rows: b = e - a s + [limb in digit] pmod_t s'  (all NTT form, limbs of Q u P)
 __global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
                               Scal pm, int nl, int dlo, int dhi, LimbMap map, const ModC *mods, int logN) {
+    grid_dep_enter();
     const int N = 1 << logN;
     long total = (long)nl << logN;
     for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
@@ -700,6 +732,7 @@ __global__ void k_key_combine(uint64_t *b, const uint64_t *a, const uint64_t *e,
 // x_i mod q_i for `count` limbs of N words (limb l uses modulus map.prime[l % nper]), any uint64
 __global__ void k_reduce_limbs(uint64_t *out, const uint64_t *x, int count, int nper, LimbMap map, const ModC *mods,
                                int logN) {
+    grid_dep_enter();
     const long N = 1L << logN, total = (long)count << logN;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const int l = (int)(i >> logN);
@@ -711,6 +744,7 @@ __global__ void k_reduce_limbs(uint64_t *out, const uint64_t *x, int count, int 
 // bounded spin used only by the device-wait self test: waits for *flag != 0 at most max_iter
 // polls, then records a timeout in *status (1 = flag seen, 2 = gave up) and returns
 __global__ void k_bounded_wait(const volatile int *flag, int *status, long max_iter) {
+    grid_dep_enter();
     if (threadIdx.x || blockIdx.x) return;
     for (long i = 0; i < max_iter; i++) {
         if (*flag) { *status = 1; return; }
@@ -791,6 +825,7 @@ template <int LOGE, int KIND, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride, NttFuse F) {
+    grid_dep_enter();
     constexpr int E = 1 << LOGE, S = E * E, TPS = S / E;   // threads per sub-transform = E
     constexpr int SUB = NT / TPS;                         // columns per CTA
     __shared__ uint64_t sm[S * SUB];
@@ -834,6 +869,7 @@ template <int LOGE, int KIND, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          NttFuse F) {
+    grid_dep_enter();
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = NT / TPS;                         // rows per CTA
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
@@ -918,6 +954,7 @@ template <int LOGE, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, int logN,
                                                          const uint64_t *src, long src_stride) {
+    grid_dep_enter();
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = NT / TPS;
     // one pad word per E: the E k + j accesses (stride E words) spread over all banks
@@ -956,6 +993,7 @@ template <int LOGE, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_inv_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
                                                          const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv,
                                                          int logN) {
+    grid_dep_enter();
     constexpr int E = 1 << LOGE, S = E * E, TPS = E;
     constexpr int SUB = NT / TPS;
     __shared__ uint64_t sm[S * SUB];
@@ -989,20 +1027,20 @@ static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long po
     constexpr int E = 1 << LOGE, S = E * E, SUB = NT / E;
     dim3 g(((1 << logN) / S) / SUB, count);
     if (!inverse && F.kind == 1) {
-        k_ntt_cols_fwd_rb<LOGE, 1, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 1, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        klaunch(k_ntt_cols_fwd_rb<LOGE, 1, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        klaunch(k_ntt_rows_fwd_rb<LOGE, 1, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse && F.kind == 3) {
-        k_ntt_cols_fwd_rb<LOGE, 3, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 3, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        klaunch(k_ntt_cols_fwd_rb<LOGE, 3, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        klaunch(k_ntt_rows_fwd_rb<LOGE, 3, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse && F.kind == 2) {
-        k_ntt_cols_fwd_rb<LOGE, 2, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 2, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        klaunch(k_ntt_cols_fwd_rb<LOGE, 2, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        klaunch(k_ntt_rows_fwd_rb<LOGE, 2, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else if (!inverse) {
-        k_ntt_cols_fwd_rb<LOGE, 0, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
-        k_ntt_rows_fwd_rb<LOGE, 0, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, F);
+        klaunch(k_ntt_cols_fwd_rb<LOGE, 0, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
+        klaunch(k_ntt_rows_fwd_rb<LOGE, 0, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, F);
     } else {
-        k_ntt_rows_inv_rb<LOGE, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
-        k_ntt_cols_inv_rb<LOGE, NT><<<g, NT, 0, st>>>(base, nper, poly_stride, map, mods, tw2, ninv, logN);
+        klaunch(k_ntt_rows_inv_rb<LOGE, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride);
+        klaunch(k_ntt_cols_inv_rb<LOGE, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, ninv, logN);
     }
 }
 

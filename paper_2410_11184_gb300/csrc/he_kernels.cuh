@@ -2,6 +2,42 @@
 #pragma once
 #include "he_common.cuh"
 
+#include <utility>
+
+// Launch helper: klaunch(kernel, grid, block, smem, stream)(args...) launches like
+// kernel<<<grid, block, smem, stream>>>(args...).  While he_pdl_launch is set (the default), the
+// launch carries the programmatic-stream-serialisation attribute, so the kernel may be scheduled
+// while the previous kernel of the stream finishes; its grid_dep_enter() keeps the order of
+// memory effects.  Measured on the Softmax step: 3-5% faster in eager streams; in a replayed
+// CUDA graph, which already hides launch latency, 0.2-0.7% slower, so graph capture turns it off
+// for the capturing thread.  Launch errors are left for cudaGetLastError, as with <<<>>>.
+extern thread_local int he_pdl_launch;
+template <typename... P>
+struct KLaunch {
+    void (*k)(P...);
+    dim3 grid, block;
+    size_t smem;
+    cudaStream_t st;
+    template <typename... A>
+    void operator()(A &&...a) const {
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = he_pdl_launch;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(a)...);
+    }
+};
+template <typename... P>
+inline KLaunch<P...> klaunch(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    return KLaunch<P...>{k, grid, block, smem, st};
+}
+
 struct Scal {
     uint64_t v[HE_MAX_LIMBS];
 };
