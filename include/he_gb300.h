@@ -272,9 +272,12 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
  * one stream; he_tune_force only, on by default), HE_TUNE_NTT_SMALL (1: transforms in CTAs of 64
  * threads instead of 256; he_autotune times both on a ladder of limb counts (1 .. 2048) per
  * direction, and a transform takes the choice of the largest ladder count at or below its limb
- * count; 256 until tuned; table entries (HE_TUNE_NTT_SMALL, limbs, 0 forward / 1 inverse)).
+ * count; 256 until tuned; table entries (HE_TUNE_NTT_SMALL, limbs, 0 forward / 1 inverse)),
+ * HE_TUNE_FUSE_CONV (1: the fast basis conversions of ModUp and ModDown computed inside the
+ * column pass of the forward transform that follows them, so the converted limbs are never
+ * written to HBM; 0: a conversion kernel, then the transform; timed on one relinearisation).
  * Without a table entry the choice is 1 for batches of at most 4 ciphertexts (8 rows for
- * HE_TUNE_LT_ROWS).
+ * HE_TUNE_LT_ROWS), and 0 for HE_TUNE_FUSE_CONV.
  * he_autotune times both variants of every operation on the device (CUDA events on the context
  * stream, the best of reps runs after one warm-up) for ciphertexts at each of the n_levels levels and
  * each of the n_ncts batch sizes, on uniformly random residues, and keeps the faster one per
@@ -287,6 +290,7 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
 #define HE_TUNE_LT_ROWS 3
 #define HE_TUNE_BRANCHES 4
 #define HE_TUNE_NTT_SMALL 5
+#define HE_TUNE_FUSE_CONV 6
 int he_autotune(he_ctx *ctx, const int *levels, int n_levels, const int *ncts, int n_ncts, int reps);
 /* the table as text, one line "op limbs n_ct choice ms_variant0 ms_variant1" per entry, into buf
  * (len bytes, NUL-terminated; HE_EINVAL if too small) */

@@ -85,6 +85,11 @@ struct he_ctx {
     std::vector<ModC> modc;
     ModC *d_mods = nullptr;
     uint64_t *d_ninv = nullptr;
+    // inverse-transform scale factors with a basis conversion's first factor folded in, per prime
+    // index (N^{-1} [qhat_i^{-1}]_{q_i}, Shoup): ModUp per level [nq][nm][2] (qhat within the
+    // limb's digit), ModDown [nm][2] (qhat within P), relinearise + rescale per level [nq][nm][2]
+    // (qhat within {q_l} u P)
+    uint64_t *d_ninv_up = nullptr, *d_ninv_down = nullptr, *d_ninv_rr = nullptr;
     ulonglong2 *d_tw2 = nullptr;   // per modulus: N (w, w') forward twiddle pairs, then N inverse pairs
     std::vector<std::vector<size_t>> cv_off;
     uint64_t *d_cv = nullptr;
@@ -141,7 +146,7 @@ struct he_ctx {
         float ms[2];
     };
     std::map<std::tuple<int, int, int>, TuneRec> tune;
-    int tune_force[6] = {-1, -1, -1, -1, -1, -1};
+    int tune_force[7] = {-1, -1, -1, -1, -1, -1, -1};
     // CTA size of the transforms per direction (forward, inverse): the autotuner's choice at each
     // limb count of its ladder; a launch takes the choice of the largest ladder count <= its own
     std::vector<std::pair<int, int>> ntt_small[2];
@@ -328,6 +333,16 @@ static dim3 grid_for(he_ctx *c, long total) {
     return dim3((unsigned)std::max(1L, std::min(b, (long)c->max_grid)));
 }
 
+// Chunks of the target limbs for a basis-conversion launch whose grid g (256-thread CTAs, times
+// `other` in its other dimension) is smaller than a full grid: one chunk per missing multiple,
+// at most one target per chunk.  Small batches (the auxiliary thread and the bootstrapping's one
+// ciphertext) otherwise leave most of the GPU idle with long per-thread loops over the targets.
+static unsigned conv_chunks(he_ctx *c, dim3 g, int other, int ntarget) {
+    long have = (long)g.x * other;
+    long want = (c->max_grid + have - 1) / have;
+    return (unsigned)std::max(1L, std::min(want, (long)ntarget));
+}
+
 // ------------------------------------------------------------------------- launch strategies
 // Bit-identical alternatives the autotuner chooses between, per (operation, limbs, ciphertexts):
 //   HE_TUNE_MODUP     1: every digit of the ModUp converted in one launch and transformed in one
@@ -341,8 +356,12 @@ static dim3 grid_for(he_ctx *c, long total) {
 //                     launch on the context stream, in the same order as the host issues it
 //   HE_TUNE_NTT_SMALL 1: the transform in CTAs of 64 threads (4 sub-transforms each); 0: 256
 //                     threads.  Chosen per direction from a ladder of limb counts (ntt_small).
+//   HE_TUNE_FUSE_CONV 1: the basis conversions of ModUp and ModDown computed in the column pass
+//                     of the forward transform that follows them (NttFuse kinds 4-6); 0: a
+//                     conversion kernel writes the converted limbs, then the transform reads them
 // Defaults (no table entry): 1 for batches of at most 4 ciphertexts (8 rows for LT_ROWS);
-// branches on.
+// branches on; separate conversions (the fused ones measured slower: their column-strided
+// re-reads of the source limbs for every target limb leave the pass latency-bound).
 static int tune_pick(he_ctx *c, int op, int L, int nct, int dflt) {
     if (c->tune_force[op] >= 0) return c->tune_force[op];
     auto it = c->tune.find(std::make_tuple(op, L, nct));
@@ -396,9 +415,11 @@ static const char *ntt_inv_family(const char *site) {
 // src + i src_stride + l N) when src is given; register-blocked passes of 8 (N = 2^12) or 16
 // (N = 2^16) coefficients per thread, the only ring sizes a context accepts.
 // fuse: neighbours of a forward transform, see NttFuse
+// ninv: the inverse transform's per-prime scale factors (default N^{-1}; a d_ninv_* table folds a
+// basis conversion's first factor in)
 static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long poly_stride, bool inverse,
                 const char *site = "ntt", const uint64_t *src = nullptr, long src_stride = 0,
-                const NttFuse *fuse = nullptr) {
+                const NttFuse *fuse = nullptr, const uint64_t *ninv = nullptr) {
     if (count <= 0) return;
     REQUIRE(!fuse || !inverse, HE_EINVAL, "fused transform: forward only");
     // timing family: the call site with the direction ("ntt_modup" forward, "ntt_modup_inv"
@@ -413,7 +434,7 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
             if (e.first <= count) small = e.second == 1;
     }
     launch_ntt_rb(c->logN == 16 ? 4 : 3, inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
-                  c->d_ninv, c->logN, c->st, src, src_stride, fuse, small);
+                  ninv ? ninv : c->d_ninv, c->logN, c->st, src, src_stride, fuse, small);
     LAUNCH_CHECK();
 }
 
@@ -587,14 +608,48 @@ static void rescale_noalloc(he_ctx *c, const DCt &a, uint64_t *out) {
 
 // ------------------------------------------------------------------------- key switching
 // ModUp of nct polynomials x (NTT form, L limbs, stride sx between polynomials):
-// digits [nct][ndig][L + alpha][N] in NTT form.
+// digits [nct][ndig][L + alpha][N] in NTT form.  The inverse transform multiplies limb i by
+// N^{-1} [qhat_i^{-1}]_{q_i} (qhat within its digit), the conversion's first factor.
 static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
     int al = c->alpha, nd = (L + al - 1) / al, nl = L + al;
     DPtr tmp = dalloc(c, (size_t)nct * L * c->N);
-    ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true, "ntt_modup", x, sx);
+    ntt(c, tmp.get(), nct * L, qmap(L), (long)L * c->N, true, "ntt_modup", x, sx, nullptr,
+        c->d_ninv_up + (size_t)(L - 1) * 2 * c->nm);
     DPtr dig = dalloc(c, (size_t)nct * nd * nl * c->N);
     LimbMap em = extmap(c, L);
-    if (tune_pick(c, HE_TUNE_MODUP, L, nct, nct <= 4)) {
+    const bool all = tune_pick(c, HE_TUNE_MODUP, L, nct, nct <= 4);
+    if (tune_pick(c, HE_TUNE_FUSE_CONV, L, nct, 0)) {
+        // conversion in the column pass of the forward transform (NttFuse kind 4): every limb of
+        // the extended basis outside the digit is converted and transformed in one pass pair,
+        // the digit's own limbs are copied from x; all digits in one launch (all) or one per digit
+        NttFuse F{};
+        F.kind = 4;
+        F.src = tmp.get();
+        F.sstride = (long)L * c->N;
+        F.cvw = c->d_cv + c->cv_off[L - 1][0];
+        F.wstride = nl;
+        F.xntt = x;
+        F.sxn = sx;
+        for (int j = 0; j < nd; j++) {
+            F.dlo[j] = j * al;
+            F.dds[j] = std::min(al, L - j * al);
+            F.dcv[j] = (long)(c->cv_off[L - 1][j] - c->cv_off[L - 1][0]) + 2 * F.dds[j];
+        }
+        if (all) {
+            F.ndc = nd;
+            F.j0 = 0;
+            ntt(c, dig.get(), nct * nd * nl, em, (long)nl * c->N, false, "ntt_modup", nullptr, 0, &F);
+        } else {
+            F.ndc = 1;
+            for (int j = 0; j < nd; j++) {
+                F.j0 = j;
+                ntt(c, dig.get() + (long)j * nl * c->N, nct * nl, em, (long)nd * nl * c->N, false, "ntt_modup", nullptr,
+                    0, &F);
+            }
+        }
+        return dig;
+    }
+    if (all) {
         // small batches: every digit converted in one launch and transformed in one more (the
         // per-digit launches would each fill a fraction of the GPU); the digit's own limbs are
         // converted too, which reproduces them exactly
@@ -605,6 +660,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
             D.cvoff[j] = (long)c->cv_off[L - 1][j] - (long)c->cv_off[L - 1][0];
         }
         dim3 grid(grid_for(c, (long)nct << c->logN).x, nd);
+        grid.z = conv_chunks(c, grid, nd, nl);
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * L + (double)nct * nd * nl));
             klaunch(k_modup_all, grid, 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, tmp.get(), (long)L * c->N, nct, D, nl,
@@ -619,7 +675,9 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
         long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * 2 * ds + (double)nct * nl));
-            klaunch(k_modup, grid_for(c, tot), 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
+            dim3 grid = grid_for(c, tot);
+            grid.y = conv_chunks(c, grid, 1, nl - ds);
+            klaunch(k_modup, grid, 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
                                                           tmp.get(), (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
                                                           c->d_cv + c->cv_off[L - 1][j], c->logN, x, sx);
         }
@@ -661,11 +719,37 @@ static void ks_inner_into(he_ctx *c, uint64_t *acc, const uint64_t *dig, int nct
 static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, long so, const uint64_t *add,
                        long sadd) {
     int al = c->alpha, nl = L + al;
-    ntt(c, acc + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true, "ntt_moddown");
+    // P limbs to coefficient form, times N^{-1} [phat_k^{-1}]_{p_k} (the conversion's first factor)
+    ntt(c, acc + (long)L * c->N, 2 * nct * al, pmap(c), (long)nl * c->N, true, "ntt_moddown", nullptr, 0, nullptr,
+        c->d_ninv_down);
     DPtr conv = dalloc(c, (size_t)2 * nct * L * c->N);
+    if (tune_pick(c, HE_TUNE_FUSE_CONV, L, nct, 0)) {
+        // Conv_{P->Q} in the transform's column pass (kind 5), (x - conv) P^{-1} (+ add) in its
+        // row pass; conv only carries the column pass's output to the row pass
+        NttFuse F{};
+        F.kind = 5;
+        F.alpha = al;
+        F.x = acc;
+        F.out = out;
+        F.so = so;
+        F.add = add;
+        F.sadd = sadd;
+        F.cst = c->d_pinv;
+        F.src = acc;
+        F.sstride = (long)nl * c->N;
+        F.slo = L;
+        F.ns = al;
+        for (int k = 0; k < al; k++) F.sidx[k] = c->nq + k;
+        F.cvw = c->d_mdcv + 2 * al;
+        F.wstride = c->nq;
+        ntt(c, conv.get(), 2 * nct * L, qmap(L), (long)L * c->N, false, "ntt_moddown", nullptr, 0, &F);
+        return;
+    }
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (al + L));
-        klaunch(k_moddown_conv, grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st)(conv.get(), acc, 2 * nct, L, al, qmap(L),
+        dim3 grid = grid_for(c, (long)2 * nct << c->logN);
+        grid.y = conv_chunks(c, grid, 1, L);
+        klaunch(k_moddown_conv, grid, 256, 0, c->st)(conv.get(), acc, 2 * nct, L, al, qmap(L),
                                                                                   c->d_pidx, c->d_mods, c->d_mdcv,
                                                                                   c->nq, c->logN);
     }
@@ -743,15 +827,9 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     dm.nper = nd;
     dm.prime[0] = l;
     for (int k = 0; k < al; k++) dm.prime[1 + k] = c->nq + k;
-    ntt(c, acc.get() + (long)l * c->N, 2 * nct * nd, dm, (long)nl * c->N, true, "ntt_moddown");
+    ntt(c, acc.get() + (long)l * c->N, 2 * nct * nd, dm, (long)nl * c->N, true, "ntt_moddown", nullptr, 0, nullptr,
+        c->d_ninv_rr + (size_t)l * 2 * c->nm);
     DPtr conv = dalloc(c, (size_t)2 * nct * l * c->N);
-    {
-        ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (nd + l));
-        klaunch(k_moddown_conv, grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st)(
-            conv.get(), acc.get(), 2 * nct, l, nd, qmap(l), c->d_rridx + (size_t)l * nd, c->d_mods,
-            c->d_rrcv + (size_t)l * c->rrcv_stride, c->nq, c->logN);
-    }
-    LAUNCH_CHECK();
     DCt y = ct_new(c, l - 1, nct, scale / (double)c->mods[l]);
     const uint64_t *cst = c->d_rrpq + (size_t)l * c->nq * 4;
     NttFuse F{};
@@ -763,6 +841,29 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     F.out = y.d;
     F.so = y.cs(c);
     F.cst = cst;
+    if (tune_pick(c, HE_TUNE_FUSE_CONV, L, nct, 0)) {
+        // Conv_{D->Q} in the column pass (kind 6), the division in the row pass
+        F.kind = 6;
+        F.src = acc.get();
+        F.sstride = (long)nl * c->N;
+        F.slo = l;
+        F.ns = nd;
+        for (int j = 0; j < nd; j++) F.sidx[j] = j == 0 ? l : c->nq + (j - 1);
+        F.cvw = c->d_rrcv + (size_t)l * c->rrcv_stride + 2 * nd;
+        F.wstride = c->nq;
+        ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown", nullptr, 0, &F);
+        c->cnt[3]++;
+        return y;
+    }
+    {
+        ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (nd + l));
+        dim3 grid = grid_for(c, (long)2 * nct << c->logN);
+        grid.y = conv_chunks(c, grid, 1, l);
+        klaunch(k_moddown_conv, grid, 256, 0, c->st)(
+            conv.get(), acc.get(), 2 * nct, l, nd, qmap(l), c->d_rridx + (size_t)l * nd, c->d_mods,
+            c->d_rrcv + (size_t)l * c->rrcv_stride, c->nq, c->logN);
+    }
+    LAUNCH_CHECK();
     ntt(c, conv.get(), 2 * nct * l, qmap(l), (long)l * c->N, false, "ntt_moddown", nullptr, 0, &F);
     c->cnt[3]++;
     return y;
@@ -2239,6 +2340,28 @@ static void build_tables(he_ctx *c) {
     CK(cudaMemcpy(c->d_pinv, pinv.data(), pinv.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->d_pidx, pidx.size() * sizeof(int)));
     CK(cudaMemcpy(c->d_pidx, pidx.data(), pidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // inverse-transform scale factors N^{-1} f mod p (with Shoup companions) where f is the first
+    // factor [qhat^{-1}] of the basis conversion that reads the transform's output
+    auto fold = [&](std::vector<uint64_t> &tab, size_t row, int p, uint64_t f) {
+        uint64_t q = c->mods[p], v = h_mulmod(ninv[2 * p], f % q, q);
+        tab[row * 2 * nm + 2 * p] = v;
+        tab[row * 2 * nm + 2 * p + 1] = h_shoup(v, q);
+    };
+    {
+        std::vector<uint64_t> up((size_t)c->nq * 2 * nm, 0), down((size_t)2 * nm, 0);
+        for (int Lm1 = 0; Lm1 < c->nq; Lm1++) {
+            int L = Lm1 + 1;
+            for (int j = 0; j * al < L; j++) {
+                int lo = j * al, ds = std::min(al, L - lo);
+                for (int i = 0; i < ds; i++) fold(up, Lm1, lo + i, cv[c->cv_off[Lm1][j] + i]);   // qhinv
+            }
+        }
+        for (int k = 0; k < al; k++) fold(down, 0, c->nq + k, md[k]);   // phinv
+        CK(cudaMalloc(&c->d_ninv_up, up.size() * 8));
+        CK(cudaMemcpy(c->d_ninv_up, up.data(), up.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&c->d_ninv_down, down.size() * 8));
+        CK(cudaMemcpy(c->d_ninv_down, down.data(), down.size() * 8, cudaMemcpyHostToDevice));
+    }
     // rescale constants: q_l^{-1} mod q_i (i < l)
     std::vector<uint64_t> ql((size_t)c->nq * 2 * c->nq, 0);
     for (int l = 1; l < c->nq; l++)
@@ -2296,6 +2419,11 @@ static void build_tables(he_ctx *c) {
         CK(cudaMemcpy(c->d_rrpq, rrpq.data(), rrpq.size() * 8, cudaMemcpyHostToDevice));
         CK(cudaMalloc(&c->d_rridx, rridx.size() * sizeof(int)));
         CK(cudaMemcpy(c->d_rridx, rridx.data(), rridx.size() * sizeof(int), cudaMemcpyHostToDevice));
+        std::vector<uint64_t> rr((size_t)c->nq * 2 * nm, 0);
+        for (int l = 1; l < c->nq; l++)
+            for (int j = 0; j < nd; j++) fold(rr, l, rridx[(size_t)l * nd + j], rrcv[(size_t)l * c->rrcv_stride + j]);
+        CK(cudaMalloc(&c->d_ninv_rr, rr.size() * 8));
+        CK(cudaMemcpy(c->d_ninv_rr, rr.data(), rr.size() * 8, cudaMemcpyHostToDevice));
     }
     // canonical embedding tables: zeta^j = exp(2 pi i j / 2N), 5^j mod 2N
     int m = 2 * N;
@@ -2415,6 +2543,12 @@ static void autotune(he_ctx *c, const std::vector<int> &levels, const std::vecto
             }
             LAUNCH_CHECK();
             tune_op(c, HE_TUNE_MODUP, L, nct, reps, [&] { DPtr d = ks_modup(c, x.d + (long)L * c->N, x.cs(c), nct, L); });
+            // fused or separate basis conversions: one relinearisation (ModUp, inner product, ModDown)
+            tune_op(c, HE_TUNE_FUSE_CONV, L, nct, reps, [&] {
+                DCt y = ct_new(c, lv, nct, 1.0);
+                DPtr dig = ks_modup(c, x.d + (long)L * c->N, x.cs(c), nct, L);
+                ks_finish(c, dig.get(), nct, L, 0, get_key(c, 0), y.d, y.cs(c), nullptr, 0);
+            });
             if (!c->bootstrap) continue;
             // the bootstrapping linear-transform level that runs at this level, if any:
             // SlotToCoeff level g at stc_levels - g, CoeffToSlot level g at the top - g
@@ -2569,7 +2703,7 @@ void he_context_destroy(he_ctx *c) {
         cudaEventDestroy(e.second);
     }
     void *ptrs[] = {c->d_mods, c->d_tw2, c->d_ninv, c->d_cv, c->d_mdcv, c->d_pinv, c->d_qlinv, c->d_pidx,
-                    c->d_rrcv, c->d_rrpq, c->d_rridx, c->d_zeta,
+                    c->d_rrcv, c->d_rrpq, c->d_rridx, c->d_ninv_up, c->d_ninv_down, c->d_ninv_rr, c->d_zeta,
                     c->d_rg, c->d_cdt, c->d_radix, c->d_radinv, c->d_qd, c->d_s, c->d_pk};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -3200,7 +3334,7 @@ int he_tune_table(const he_ctx *ctx, char *buf, size_t len) {
 }
 
 int he_tune_force(he_ctx *ctx, int op, int choice) {
-    if (!ctx || op < 0 || op > HE_TUNE_NTT_SMALL || choice < -1 || choice > 1) return HE_EINVAL;
+    if (!ctx || op < 0 || op > HE_TUNE_FUSE_CONV || choice < -1 || choice > 1) return HE_EINVAL;
     ctx->tune_force[op] = choice;
     return HE_OK;
 }

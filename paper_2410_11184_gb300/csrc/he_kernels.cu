@@ -225,8 +225,9 @@ __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap,
 // Basis conversion (coefficient domain).  ModUp for one digit D of a batch of polynomials:
 // for every target modulus t of the extended basis,
 //   out_t = sum_{i in D} [x_i * qhinv_i]_{q_i} * (qh_{i,t}) mod m_t.
-// For t in D this reproduces x_t.  cv layout per (level, digit): qhinv[a], qhinv_shoup[a],
-// then qh[a][ntarget].
+// For t in D this reproduces x_t.  The input x already holds [x_i qhinv_i]_{q_i}: the inverse
+// transform that produced it multiplied by N^{-1} qhinv_i instead of N^{-1}.  cv layout per
+// (level, digit): qhinv[a], qhinv_shoup[a], then qh[a][ntarget] (Montgomery form).
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN, const uint64_t *xntt, long sxn) {
@@ -246,7 +247,7 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
         for (int i = 0; i < HE_CONV_MAXSRC; i++) {
             if (i >= dsize) break;
             uint64_t qi = mods[tmap.prime[digit_lo + i]].q;
-            uint64_t v = mul_shoup(x[c * sx + (long)(digit_lo + i) * N + k], cv[i], cv[dsize + i], qi);
+            uint64_t v = x[c * sx + (long)(digit_lo + i) * N + k];
             if (v > (qi - 1) / 2) {
                 v = qi - v;
                 negmask |= 1u << i;
@@ -255,12 +256,15 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
         }
         uint64_t *o = out + c * so_ct + so_digit + k;
         // the digit's own limbs: the NTT-form input limbs themselves (the conversion would
-        // reproduce their coefficients)
-        for (int i = 0; i < dsize; i++)
-            o[(long)(digit_lo + i) * N] = xntt[c * sxn + (long)(digit_lo + i) * N + k];
-        for (int t = 0; t < ntarget; t++) {
-            if (t == digit_lo) t += dsize;
-            if (t >= ntarget) break;
+        // reproduce their coefficients); written by the first target chunk
+        if (blockIdx.y == 0)
+            for (int i = 0; i < dsize; i++)
+                o[(long)(digit_lo + i) * N] = xntt[c * sxn + (long)(digit_lo + i) * N + k];
+        // target chunk blockIdx.y of gridDim.y (small batches: more threads, fewer targets each)
+        const int tc = (ntarget + gridDim.y - 1) / gridDim.y, t1 = min(ntarget, (int)(blockIdx.y + 1) * tc);
+        for (int t = blockIdx.y * tc; t < t1; t++) {
+            if (t >= digit_lo && t < digit_lo + dsize) t = digit_lo + dsize;   // the digit's own limbs
+            if (t >= t1) break;
             const ModC mt = mods[tmap.prime[t]];
             // sum of |y_i| (c or m_t - c): below dsize 2^60 m_t < m_t 2^64
             uint64_t lo = 0, hi = 0;
@@ -275,7 +279,8 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
     }
 }
 
-// ModUp of all digits of nct polynomials in one launch (grid.y = digit j): every target limb of
+// ModUp of all digits of nct polynomials in one launch (grid.y = digit j, grid.z = chunk of the
+// targets): every target limb of
 // the extended basis is converted, the digit's own limbs included (there the conversion is the
 // CRT identity and returns x exactly), so one transform of all digits follows.  Output
 // [nct][ndig][ntarget][N] (coefficient form).
@@ -294,7 +299,7 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
         for (int i = 0; i < HE_CONV_MAXSRC; i++) {
             if (i >= ds) break;
             uint64_t qi = mods[tmap.prime[lo + i]].q;
-            uint64_t v = mul_shoup(x[c * sx + (long)(lo + i) * N + k], cv[i], cv[ds + i], qi);
+            uint64_t v = x[c * sx + (long)(lo + i) * N + k];
             if (v > (qi - 1) / 2) {
                 v = qi - v;
                 negmask |= 1u << i;
@@ -302,7 +307,9 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
             y[i] = v;
         }
         uint64_t *o = out + c * so_ct + (long)j * ntarget * N + k;
-        for (int t = 0; t < ntarget; t++) {
+        // target chunk blockIdx.z of gridDim.z
+        const int tc = (ntarget + gridDim.z - 1) / gridDim.z, t1 = min(ntarget, (int)(blockIdx.z + 1) * tc);
+        for (int t = blockIdx.z * tc; t < t1; t++) {
             const ModC mt = mods[tmap.prime[t]];
             uint64_t l0 = 0, h0 = 0;
 #pragma unroll
@@ -318,8 +325,10 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
 
 // ModDown conversion: conv_i = sum_k [y_k * phinv_k]_{p_k} (phat_k mod q_i); writes conv into
 // out (coefficient domain) for the Q limbs.  x: [npoly][L + alpha][N] with the coefficient-domain
-// P limbs at offset L.  cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][nqall] (by Q index).
-// One thread per (polynomial, coefficient): the alpha P limbs are read once.
+// P limbs at offset L, already multiplied by phinv_k (folded into the inverse transform's N^{-1}).
+// cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][nqall] (by Q index).
+// One thread per (polynomial, coefficient, chunk of targets; grid.y = chunk): the alpha P limbs are
+// read once per chunk.
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN) {
     grid_dep_enter();
@@ -338,7 +347,7 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
         for (int j = 0; j < HE_CONV_MAXSRC; j++) {
             if (j >= alpha) break;
             uint64_t pj = mods[pidx[j]].q;
-            uint64_t v = mul_shoup(xp[(long)j * N], cv[j], cv[alpha + j], pj);
+            uint64_t v = xp[(long)j * N];
             if (v > (pj - 1) / 2) {
                 v = pj - v;
                 negmask |= 1u << j;
@@ -346,7 +355,9 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
             y[j] = v;
         }
         uint64_t *o = out + (long)pl * L * N + k;
-        for (int i = 0; i < L; i++) {
+        // target chunk blockIdx.y of gridDim.y
+        const int tc = (L + gridDim.y - 1) / gridDim.y, i1 = min(L, (int)(blockIdx.y + 1) * tc);
+        for (int i = blockIdx.y * tc; i < i1; i++) {
             const ModC mi = mods[qmap.prime[i]];
             // one 128-bit sum, reduced once (phat_j mod q_i stored in Montgomery form)
             uint64_t lo = 0, hi = 0;
@@ -820,6 +831,38 @@ __device__ __forceinline__ void gs_stages_strided(uint64_t *v, int m0, int gbase
     }
 }
 
+// Fast basis conversion of the E coefficients off + E N2 j (j < E) of one target limb (modulus mt),
+// from ns source limbs at s0 + s N (moduli qsrc(s)) whose values already carry the factor
+// qhat_s^{-1} mod q_s: v_j = sum_s [y_s]_centred w_s mod m_t with w_s = qhat_s 2^64 mod m_t read at
+// w[s wstride].  A centred value y > (q_s - 1) / 2 enters as -(q_s - y), i.e. (q_s - y)(m_t - w_s);
+// the sum stays below ns 2^59 m_t < m_t 2^64, so one REDC gives the residue (as in k_modup).
+template <int E, class QF>
+__device__ __forceinline__ void conv_column(uint64_t *v, const uint64_t *s0, long N, int ns, QF qsrc,
+                                            const uint64_t *w, long wstride, const ModC &mt, long off, long step) {
+    uint64_t qs[HE_CONV_MAXSRC], ws[HE_CONV_MAXSRC];
+#pragma unroll
+    for (int s = 0; s < HE_CONV_MAXSRC; s++) {
+        if (s >= ns) break;
+        qs[s] = qsrc(s);
+        ws[s] = __ldg(w + s * wstride);
+    }
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        uint64_t lo = 0, hi = 0;
+#pragma unroll
+        for (int s = 0; s < HE_CONV_MAXSRC; s++) {
+            if (s >= ns) break;
+            uint64_t y = s0[s * N + off + j * step], ww = ws[s];
+            if (2 * y >= qs[s]) {   // y > (q_s - 1) / 2
+                y = qs[s] - y;
+                ww = mt.q - ww;
+            }
+            mac_wide(lo, hi, y, ww);
+        }
+        v[j] = redc(lo, hi, mt);
+    }
+}
+
 // Forward column pass: LOGS = log2(N1) stages, m = 1 .. N1/2.  CTA: SUB columns, E*... threads.
 template <int LOGE, int KIND, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_fwd_rb(uint64_t *base, int nper, long poly_stride, LimbMap map,
@@ -847,6 +890,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_fwd_rb(uint
             const uint64_t r = lp[(long)(k + E * j) * N2 + col];
             v[j] = r <= (F.ql - 1) / 2 ? mul_mod(r, 1, mi) : neg_mod(mul_mod(F.ql - r, 1, mi), mi.q);
         }
+    } else if (KIND == 4) {
+        // ModUp: polynomial l / nper is digit j of ciphertext c; limb t of the extended basis
+        const int poly = l / nper, t = l % nper, dj = F.j0 + poly % F.ndc, ci = poly / F.ndc;
+        const int lo = F.dlo[dj], ds = F.dds[dj];
+        if (t >= lo && t < lo + ds) {
+            // the digit's own limb: the NTT-form input itself (the row pass leaves this limb)
+            const uint64_t *xi = F.xntt + (long)ci * F.sxn + (long)t * N;
+#pragma unroll
+            for (int j = 0; j < E; j++) a[(long)(k + E * j) * N2 + col] = xi[(long)(k + E * j) * N2 + col];
+            return;   // uniform over the CTA: no barrier is skipped by part of it
+        }
+        conv_column<E>(v, F.src + (long)ci * F.sstride + (long)lo * N, N, ds,
+                       [&](int s) { return mods[lo + s].q; }, F.cvw + F.dcv[dj] + t, F.wstride, mods[p],
+                       (long)k * N2 + col, (long)E * N2);
+    } else if (KIND == 5 || KIND == 6) {
+        // ModDown: conv of limb i of polynomial l / nper from the dropped limbs of that polynomial
+        conv_column<E>(v, F.src + (long)(l / nper) * F.sstride + (long)F.slo * N, N, F.ns,
+                       [&](int s) { return mods[F.sidx[s]].q; }, F.cvw + p, F.wstride, mods[p],
+                       (long)k * N2 + col, (long)E * N2);
     } else {
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
@@ -881,6 +943,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint
     const uint64_t q = mods[p].q;
     const ulonglong2 *psi = tw2 + (long)p * 2 * N;
     const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
+    if (KIND == 4) {   // ModUp: the digit's own limbs were copied in NTT form by the column pass
+        const int t = l % nper, dj = F.j0 + (l / nper) % F.ndc;
+        if (t >= F.dlo[dj] && t < F.dlo[dj] + F.dds[dj]) return;   // uniform over the CTA
+    }
     uint64_t *g = a + (long)row * S;
     uint64_t v[E];
 #pragma unroll
@@ -911,7 +977,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint
         sm[rr * SP + (E + 1) * k + j] = r;
     }
     __syncthreads();
-    if (KIND == 0) {
+    if (KIND == 0 || KIND == 4) {
 #pragma unroll
         for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * SP + k + (E + 1) * j];
         return;
@@ -919,7 +985,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint
     // fused epilogue (ModDown or rescale): out from x and the transformed values
     const int pl = l / nper, i = l % nper;
     const long at = (long)i * N + (long)row * S + k;
-    if (KIND == 1) {
+    if (KIND == 1 || KIND == 5) {
         const uint64_t w = F.cst[2 * p], wp = F.cst[2 * p + 1];
         const uint64_t *xp = F.x + (long)pl * (nper + F.alpha) * N + at;
         const long o = (long)(pl / 2) * F.so + (long)(pl % 2) * nper * N + at;
@@ -1026,6 +1092,16 @@ static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long po
                       const uint64_t *src, long src_stride, const NttFuse &F) {
     constexpr int E = 1 << LOGE, S = E * E, SUB = NT / E;
     dim3 g(((1 << logN) / S) / SUB, count);
+#define HE_FWD_KIND(KD)                                                                                        \
+    if (!inverse && F.kind == KD) {                                                                            \
+        klaunch(k_ntt_cols_fwd_rb<LOGE, KD, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F); \
+        klaunch(k_ntt_rows_fwd_rb<LOGE, KD, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, F); \
+        return;                                                                                                \
+    }
+    HE_FWD_KIND(4)
+    HE_FWD_KIND(5)
+    HE_FWD_KIND(6)
+#undef HE_FWD_KIND
     if (!inverse && F.kind == 1) {
         klaunch(k_ntt_cols_fwd_rb<LOGE, 1, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);
         klaunch(k_ntt_rows_fwd_rb<LOGE, 1, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, F);

@@ -69,6 +69,18 @@ struct LtArgs {
 //       out_i = (P d_i + K_i - NTT(conv)_i) (P q_l)^{-1}, K_i at x + p (nper + alpha) N + i N,
 //       d_i (tensor) at add + (p / 2) sadd + (p % 2) (nper + 1) N + i N, out as in kind 1,
 //       cst[4 i ..]: P mod q_i, Shoup, (P q_l)^{-1} mod q_i, Shoup.
+// Kinds 4-6 compute the transformed batch itself in the column pass, as a fast basis conversion
+//   conv_t = sum_s [y_s]_centred (qhat_s mod m_t) mod m_t
+// of source limbs y_s in coefficient form that the inverse transform before has already
+// multiplied by qhat_s^{-1} mod q_s (its N^{-1} factor folded with that constant); the weights are
+// in Montgomery form, so one 128-bit sum reduced by REDC gives the residue.
+//   kind 4 (ModUp): polynomial p of the batch is digit j = j0 + p % ndc of ciphertext c = p / ndc
+//       (nper = L + alpha extended limbs t).  Sources: limbs dlo[j] .. dlo[j] + dds[j] - 1 of
+//       src + c sstride; weights cvw[dcv[j] + s wstride + t].  The digit's own limbs are copied
+//       from the NTT-form input xntt + c sxn instead (the row pass leaves them).
+//   kind 5 (ModDown): as kind 1, with conv computed from the ns limbs slo .. slo + ns - 1 of
+//       src + p sstride (moduli sidx[s]); weights cvw[s wstride + prime].
+//   kind 6 (relinearise + rescale): as kind 3, with conv computed as in kind 5.
 struct NttFuse {
     int kind;
     int alpha;
@@ -80,6 +92,18 @@ struct NttFuse {
     const uint64_t *cst;
     const uint64_t *last;
     uint64_t ql;
+    // kinds 4-6
+    const uint64_t *src;
+    long sstride;
+    const uint64_t *cvw;
+    int wstride;
+    int ns, slo;
+    int sidx[HE_CONV_MAXSRC];
+    const uint64_t *xntt;
+    long sxn;
+    int ndc, j0;
+    int dlo[8], dds[8];
+    long dcv[8];
 };
 
 // Several key switches in one inner-product launch.  k_ks_inner: the same digits, grid.y = r,

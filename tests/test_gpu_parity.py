@@ -366,7 +366,8 @@ def test_softmax_alg4_split_shares_equal_unsplit(toybts, split):
 
 def test_autotune_variants_bit_identical(toybts):
     """Every launch strategy the autotuner chooses between gives the same words: each variant of
-    each operation forced in turn (branches on side streams or one stream, transform CTA size) on
+    each operation forced in turn (branches on side streams or one stream, transform CTA size,
+    basis conversions fused into the transforms or separate) on
     multiplications, hoisted rotations, SlotToCoeff / CoeffToSlot levels and a degree-31
     polynomial at batch sizes 1, 2 and 6; then he_autotune fills its table (one entry per timed
     operation, level and batch size) and results stay the same."""
@@ -390,7 +391,7 @@ def test_autotune_variants_bit_identical(toybts):
         return np.random.default_rng(1000 + k)
 
     ref = run()
-    for op in ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small"):
+    for op in ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small", "fuse_conv"):
         for choice in (0, 1):
             g.tune_force(op, choice)
             got = run()
@@ -400,10 +401,12 @@ def test_autotune_variants_bit_identical(toybts):
     g.autotune([3, top - 1, top], [1, 6], reps=1)
     table = g.tune_table()
     ops = {e["op"] for e in table}
-    assert ops == {"modup", "rot", "lt_small", "lt_rows", "ntt_small"}, ops
+    assert ops == {"modup", "rot", "lt_small", "lt_rows", "ntt_small", "fuse_conv"}, ops
     assert all(e["choice"] in (0, 1) and min(e["ms"]) > 0 for e in table)
     assert {(e["limbs"], e["n_ct"]) for e in table if e["op"] == "modup"} == {(4, 1), (4, 6), (top, 1), (top, 6),
                                                                                  (top + 1, 1), (top + 1, 6)}
+    assert ({(e["limbs"], e["n_ct"]) for e in table if e["op"] == "fuse_conv"}
+            == {(e["limbs"], e["n_ct"]) for e in table if e["op"] == "modup"})
     # transform CTA size: both directions (n_ct holds the direction) over the limb-count ladder
     assert {e["n_ct"] for e in table if e["op"] == "ntt_small"} == {0, 1}
     got = run()
