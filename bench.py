@@ -279,6 +279,11 @@ def run_serve(args):
     up to 1024 use the Alg. 2 plans, 4096 and 32768 the Alg. 4 plans (Alg. 2 does not converge
     there on this chain).  Prints one JSON line with p50/p99 request latency, Softmax/s and
     the worst-case error per dimension."""
+    print(json.dumps(serve_measure(args, args.requests, args.rate)))
+
+
+def serve_measure(args, requests, rate):
+    """The serving run of run_serve (its own context, keys and server); returns its line."""
     import torch
 
     from paper_2410_11184_gb300 import he, serve, workloads
@@ -311,8 +316,8 @@ def run_serve(args):
         srv.submit(nm, host, 1, lv, sc).wait(600)
     srv.finished.clear()
     srv.batches.clear()
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.requests))
-    picks = [(names[rng.integers(len(names))], int(rng.integers(3))) for _ in range(args.requests)]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, requests))
+    picks = [(names[rng.integers(len(names))], int(rng.integers(3))) for _ in range(requests)]
     t0 = time.perf_counter()
     handles = []
     for t, key in zip(arrivals, picks):
@@ -343,14 +348,18 @@ def run_serve(args):
         "value": st["p99_ms"], "unit": "ms (p99 request latency)", "higher_is_better": False,
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
         "softmax_per_s": softmax_done / st["span_s"], "requests": st["requests"], "span_s": st["span_s"],
-        "arrival_rate_per_s": args.rate, "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
+        "arrival_rate_per_s": rate, "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
         "precision_bits_by_n": {str(n): -math.log2(e) if e > 0 else None for n, e in sorted(worst.items())},
         "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
         "config": {"workload": "Poisson arrivals, one ciphertext per request, dims %s on [-64, 0] (4096 and "
                                 "32768 by Alg. 4)" % "/".join(str(plans[nm]["n"]) for nm in names),
                    "hbm_budget_gb": budget / 1e9, "max_batch_ct": args.max_batch_ct},
     }
-    print(json.dumps(line))
+    srv = None
+    del g
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_llama(args):
@@ -433,6 +442,8 @@ def main():
     ap.add_argument("--layers-per-pass", type=int, default=4, help="llama: layer groups per grouped pass")
     ap.add_argument("--rate", type=float, default=8.0, help="serve: request arrivals per second")
     ap.add_argument("--requests", type=int, default=64, help="serve: number of requests")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="default workload: requests of the serving leg (0: off)")
     ap.add_argument("--max-batch-ct", type=int, default=16, help="serve: ciphertexts per batched pass")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-kernel", default="ntt")
@@ -740,11 +751,23 @@ def main():
                 if lat1:
                     # one problem at a time: the single-ciphertext latency times m, per Softmax
                     split["sequential_ms_per_softmax"] = lat1["p50_ms"] * m / L
-            except RuntimeError as e:   # a side measurement: report it, keep the line
-                split = {"error": str(e)[:200]}
+            except Exception as e:   # a side measurement: report it, keep the line
+                split = {"error": ("%s: %s" % (type(e).__name__, e))[:200]}
             passes = None
             torch.cuda.synchronize(dev)
             torch.cuda.empty_cache()
+
+    # serving (config 5's request loop, a short run): its own context beside this one
+    serving = None
+    if world == 1 and args.serve_requests > 0:
+        try:
+            sl = serve_measure(args, args.serve_requests, args.rate)
+            serving = {k: sl[k] for k in ("p50_ms", "p99_ms", "max_ms", "softmax_per_s", "requests", "span_s",
+                                          "arrival_rate_per_s", "batches", "mean_batch_requests",
+                                          "precision_bits_by_n")}
+            serving["workload"] = sl["config"]["workload"]
+        except Exception as e:   # a side measurement: report it, keep the line
+            serving = {"error": ("%s: %s" % (type(e).__name__, e))[:200]}
 
     ms_step, e2e_ms, xy_ms = shard.max_over_ranks([total_ms / args.steps, e2e_ms, xy_ms], dist)
     if rank != 0:
@@ -808,6 +831,7 @@ def main():
         "autotune": tune,
         "single_ct_latency": lat1,
         "split_packing": split,
+        "serving": serving,
         "e2e": {"value": e2e_ms / L, "unit": "ms/Softmax", "h2d_bytes_per_step": src.tensor.numel() * 8,
                 "d2h_bytes_per_step": out_words * 8,
                 "path": "pinned host ciphertexts -> he_softmax_graph -> host ciphertexts, every timed step"},

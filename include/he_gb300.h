@@ -138,6 +138,16 @@ int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched
  * that group alone, bit for bit (all groups share level and scale).  This is how a server batches
  * requests that arrive separately. */
 int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int groups);
+/* The problem statement's form of the call (Sec. 3, inputs in [-M, 0]^n, Assumption 3.5):
+ * Softmax of dimension n over the m = cts->n_ct ciphertexts, encrypted by he_encrypt with this
+ * M, by the method's circuit, with the plan registered for exactly (n, M, method).  The plans'
+ * polynomials come from the design script (the paper prints none); he_softmax_register copies a
+ * plan into the context (it owns the copy; registering the same (n, M, method) again replaces
+ * it).  he_softmax_nm runs he_softmax (batched; graph = 0) or he_softmax_graph (graph = 1) with
+ * that plan: HE_EINVAL if none is registered, otherwise as those calls.  he_softmax_register:
+ * HE_EINVAL for a NULL array the method reads or a method other than the two. */
+int he_softmax_register(he_ctx *ctx, const he_softmax_plan *plan);
+int he_softmax_nm(he_ctx *ctx, he_ct *cts, int n, double M, int method, int graph);
 /* he_softmax (batched) as one CUDA graph: the first call for a given (cts->data, level, scale,
  * n_ct, plan) runs the circuit once on a scratch copy (filling the key, diagonal and mask caches),
  * captures it on the context stream and launches the captured graph; later calls with the same

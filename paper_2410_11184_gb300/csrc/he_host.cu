@@ -137,6 +137,14 @@ struct he_ctx {
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
     std::map<std::string, SmGraph> graphs;  // captured Softmax circuits (he_softmax_graph)
+    // plans registered with he_softmax_register, by (n, M, method): deep copies whose arrays the
+    // context owns (the he_softmax_plan points into the vectors of its own map node)
+    struct PlanCopy {
+        he_softmax_plan p;
+        std::vector<double> exp_c, inv_c, a, b, gs, gl, expo, lam_max, b_max;
+        std::vector<int> deg;
+    };
+    std::map<std::tuple<int, double, int>, PlanCopy> plans;
     bool capturing = false;
     uint64_t *noalloc_scratch = nullptr;   // device address of g_rescale_scratch on this device
     // launch-strategy choices of the autotuner (he_autotune): (operation, limbs, ciphertexts) ->
@@ -331,16 +339,6 @@ static void cache_entry_made(he_ctx *c) {
 static dim3 grid_for(he_ctx *c, long total) {
     long b = (total + 255) / 256;
     return dim3((unsigned)std::max(1L, std::min(b, (long)c->max_grid)));
-}
-
-// Chunks of the target limbs for a basis-conversion launch whose grid g (256-thread CTAs, times
-// `other` in its other dimension) is smaller than a full grid: one chunk per missing multiple,
-// at most one target per chunk.  Small batches (the auxiliary thread and the bootstrapping's one
-// ciphertext) otherwise leave most of the GPU idle with long per-thread loops over the targets.
-static unsigned conv_chunks(he_ctx *c, dim3 g, int other, int ntarget) {
-    long have = (long)g.x * other;
-    long want = (c->max_grid + have - 1) / have;
-    return (unsigned)std::max(1L, std::min(want, (long)ntarget));
 }
 
 // ------------------------------------------------------------------------- launch strategies
@@ -660,7 +658,6 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
             D.cvoff[j] = (long)c->cv_off[L - 1][j] - (long)c->cv_off[L - 1][0];
         }
         dim3 grid(grid_for(c, (long)nct << c->logN).x, nd);
-        grid.z = conv_chunks(c, grid, nd, nl);
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * L + (double)nct * nd * nl));
             klaunch(k_modup_all, grid, 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, tmp.get(), (long)L * c->N, nct, D, nl,
@@ -675,9 +672,7 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
         long tot = (long)nct << c->logN;  // one thread per (ciphertext, coefficient)
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * 2 * ds + (double)nct * nl));
-            dim3 grid = grid_for(c, tot);
-            grid.y = conv_chunks(c, grid, 1, nl - ds);
-            klaunch(k_modup, grid, 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
+            klaunch(k_modup, grid_for(c, tot), 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, (long)j * nl * c->N,
                                                           tmp.get(), (long)L * c->N, nct, lo, ds, nl, em, c->d_mods,
                                                           c->d_cv + c->cv_off[L - 1][j], c->logN, x, sx);
         }
@@ -747,9 +742,7 @@ static void ks_moddown(he_ctx *c, uint64_t *acc, int nct, int L, uint64_t *out, 
     }
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (al + L));
-        dim3 grid = grid_for(c, (long)2 * nct << c->logN);
-        grid.y = conv_chunks(c, grid, 1, L);
-        klaunch(k_moddown_conv, grid, 256, 0, c->st)(conv.get(), acc, 2 * nct, L, al, qmap(L),
+        klaunch(k_moddown_conv, grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st)(conv.get(), acc, 2 * nct, L, al, qmap(L),
                                                                                   c->d_pidx, c->d_mods, c->d_mdcv,
                                                                                   c->nq, c->logN);
     }
@@ -857,9 +850,7 @@ static DCt relin_rescale(he_ctx *c, const uint64_t *d, int level, int nct, doubl
     }
     {
         ProfScope ps_(c, "moddown", 8.0 * c->N * 2 * nct * (nd + l));
-        dim3 grid = grid_for(c, (long)2 * nct << c->logN);
-        grid.y = conv_chunks(c, grid, 1, l);
-        klaunch(k_moddown_conv, grid, 256, 0, c->st)(
+        klaunch(k_moddown_conv, grid_for(c, (long)2 * nct << c->logN), 256, 0, c->st)(
             conv.get(), acc.get(), 2 * nct, l, nd, qmap(l), c->d_rridx + (size_t)l * nd, c->d_mods,
             c->d_rrcv + (size_t)l * c->rrcv_stride, c->nq, c->logN);
     }
@@ -2930,6 +2921,57 @@ int he_softmax(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int batched
     API_BEGIN
     softmax_inplace(ctx, plan, cts, batched != 0);
     API_END
+}
+
+int he_softmax_register(he_ctx *ctx, const he_softmax_plan *plan) {
+    if (!ctx || !plan || plan->k < 1 || plan->k > 16 || plan->exp_deg < 0 || !plan->exp_coeffs || !plan->inv_deg ||
+        !plan->inv_coeffs || !plan->inv_a || !plan->inv_b || !plan->gain_s)
+        return HE_EINVAL;
+    const bool b4 = plan->method == HE_SOFTMAX_ALG4;
+    if (plan->method != HE_SOFTMAX_ALG2 && !b4) return HE_EINVAL;
+    if (b4 ? (!plan->exponent || !plan->lam_max || !plan->b_max) : !plan->gain_l) return HE_EINVAL;
+    const int k = plan->k;
+    size_t nc = 0;
+    for (int j = 0; j < k; j++) {
+        if (plan->inv_deg[j] < 0) return HE_EINVAL;
+        nc += plan->inv_deg[j] + 1;
+    }
+    he_ctx::PlanCopy &e = ctx->plans[std::make_tuple(plan->n, plan->M, plan->method)];
+    e = he_ctx::PlanCopy{};
+    e.exp_c.assign(plan->exp_coeffs, plan->exp_coeffs + plan->exp_deg + 1);
+    e.inv_c.assign(plan->inv_coeffs, plan->inv_coeffs + nc);
+    e.deg.assign(plan->inv_deg, plan->inv_deg + k);
+    e.a.assign(plan->inv_a, plan->inv_a + k);
+    e.b.assign(plan->inv_b, plan->inv_b + k);
+    e.gs.assign(plan->gain_s, plan->gain_s + k);
+    if (plan->gain_l) e.gl.assign(plan->gain_l, plan->gain_l + k);
+    if (b4) {
+        e.expo.assign(plan->exponent, plan->exponent + k);
+        e.lam_max.assign(plan->lam_max, plan->lam_max + k);
+        e.b_max.assign(plan->b_max, plan->b_max + k);
+    }
+    e.p = *plan;
+    e.p.exp_coeffs = e.exp_c.data();
+    e.p.inv_coeffs = e.inv_c.data();
+    e.p.inv_deg = e.deg.data();
+    e.p.inv_a = e.a.data();
+    e.p.inv_b = e.b.data();
+    e.p.gain_s = e.gs.data();
+    e.p.gain_l = e.gl.empty() ? nullptr : e.gl.data();
+    e.p.exponent = b4 ? e.expo.data() : nullptr;
+    e.p.lam_max = b4 ? e.lam_max.data() : nullptr;
+    e.p.b_max = b4 ? e.b_max.data() : nullptr;
+    return HE_OK;
+}
+
+int he_softmax_nm(he_ctx *ctx, he_ct *cts, int n, double M, int method, int graph) {
+    if (!ctx) return HE_EINVAL;
+    auto it = ctx->plans.find(std::make_tuple(n, M, method));
+    if (it == ctx->plans.end()) {
+        ctx->err = "he_softmax_nm: no registered plan for this (n, M, method)";
+        return HE_EINVAL;
+    }
+    return graph ? he_softmax_graph(ctx, &it->second.p, cts) : he_softmax(ctx, &it->second.p, cts, 1);
 }
 
 int he_softmax_grouped(he_ctx *ctx, const he_softmax_plan *plan, he_ct *cts, int groups) {

@@ -256,15 +256,12 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
         }
         uint64_t *o = out + c * so_ct + so_digit + k;
         // the digit's own limbs: the NTT-form input limbs themselves (the conversion would
-        // reproduce their coefficients); written by the first target chunk
-        if (blockIdx.y == 0)
-            for (int i = 0; i < dsize; i++)
-                o[(long)(digit_lo + i) * N] = xntt[c * sxn + (long)(digit_lo + i) * N + k];
-        // target chunk blockIdx.y of gridDim.y (small batches: more threads, fewer targets each)
-        const int tc = (ntarget + gridDim.y - 1) / gridDim.y, t1 = min(ntarget, (int)(blockIdx.y + 1) * tc);
-        for (int t = blockIdx.y * tc; t < t1; t++) {
-            if (t >= digit_lo && t < digit_lo + dsize) t = digit_lo + dsize;   // the digit's own limbs
-            if (t >= t1) break;
+        // reproduce their coefficients)
+        for (int i = 0; i < dsize; i++)
+            o[(long)(digit_lo + i) * N] = xntt[c * sxn + (long)(digit_lo + i) * N + k];
+        for (int t = 0; t < ntarget; t++) {
+            if (t == digit_lo) t += dsize;
+            if (t >= ntarget) break;
             const ModC mt = mods[tmap.prime[t]];
             // sum of |y_i| (c or m_t - c): below dsize 2^60 m_t < m_t 2^64
             uint64_t lo = 0, hi = 0;
@@ -279,8 +276,7 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
     }
 }
 
-// ModUp of all digits of nct polynomials in one launch (grid.y = digit j, grid.z = chunk of the
-// targets): every target limb of
+// ModUp of all digits of nct polynomials in one launch (grid.y = digit j): every target limb of
 // the extended basis is converted, the digit's own limbs included (there the conversion is the
 // CRT identity and returns x exactly), so one transform of all digits follows.  Output
 // [nct][ndig][ntarget][N] (coefficient form).
@@ -307,9 +303,7 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
             y[i] = v;
         }
         uint64_t *o = out + c * so_ct + (long)j * ntarget * N + k;
-        // target chunk blockIdx.z of gridDim.z
-        const int tc = (ntarget + gridDim.z - 1) / gridDim.z, t1 = min(ntarget, (int)(blockIdx.z + 1) * tc);
-        for (int t = blockIdx.z * tc; t < t1; t++) {
+        for (int t = 0; t < ntarget; t++) {
             const ModC mt = mods[tmap.prime[t]];
             uint64_t l0 = 0, h0 = 0;
 #pragma unroll
@@ -327,8 +321,7 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
 // out (coefficient domain) for the Q limbs.  x: [npoly][L + alpha][N] with the coefficient-domain
 // P limbs at offset L, already multiplied by phinv_k (folded into the inverse transform's N^{-1}).
 // cv: phinv[alpha], phinv_shoup[alpha], phat[alpha][nqall] (by Q index).
-// One thread per (polynomial, coefficient, chunk of targets; grid.y = chunk): the alpha P limbs are
-// read once per chunk.
+// One thread per (polynomial, coefficient): the alpha P limbs are read once.
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN) {
     grid_dep_enter();
@@ -355,9 +348,7 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
             y[j] = v;
         }
         uint64_t *o = out + (long)pl * L * N + k;
-        // target chunk blockIdx.y of gridDim.y
-        const int tc = (L + gridDim.y - 1) / gridDim.y, i1 = min(L, (int)(blockIdx.y + 1) * tc);
-        for (int i = blockIdx.y * tc; i < i1; i++) {
+        for (int i = 0; i < L; i++) {
             const ModC mi = mods[qmap.prime[i]];
             // one 128-bit sum, reduced once (phat_j mod q_i stored in Montgomery form)
             uint64_t lo = 0, hi = 0;

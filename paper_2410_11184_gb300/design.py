@@ -230,6 +230,24 @@ def cheb_interp(g, deg):
     return c, float(err)
 
 
+def inv_root_interp(e, a, b, deg):
+    """Chebyshev interpolant of v^(-e) on [a, b] at its deg + 1 Chebyshev nodes, with its
+    relative error max |P(v) v^e - 1| measured on 40001 uniform and 40001 Chebyshev-spaced
+    points.  For degrees whose weighted minimax LP is too large for the solver (degree 1023 on
+    the ratio-2^15 intervals of n = 32768): v^(-e) is analytic on a Bernstein ellipse around
+    [a, b] (its singularity at 0 lies 2a / (b - a) below the interval), so the interpolant's
+    error falls geometrically with the degree, close to the minimax error."""
+    n = deg + 1
+    theta = np.pi * (np.arange(n) + 0.5) / n
+    gv = (0.5 * (b - a) * np.cos(theta) + 0.5 * (a + b)) ** -e
+    c = np.array([2.0 / n * np.dot(gv, np.cos(k * theta)) for k in range(n)])
+    c[0] *= 0.5
+    uu = np.concatenate([np.linspace(-1, 1, 40001), cheb_grid(40001)])
+    v = 0.5 * (b - a) * uu + 0.5 * (a + b)
+    err = float(np.max(np.abs(cheb_eval_rec(list(c), uu) * v ** e - 1.0)))
+    return c, err
+
+
 def hexlist(c):
     return [float(v).hex() for v in c]
 
@@ -283,7 +301,7 @@ def design_softmax(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
     }
 
 
-def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
+def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02, interp_from=None):
     """Polynomials of Alg. 4 (version B) for inputs in [-M, 0]^n with k rounds.
 
     Round j needs lambda_j = S_j^(-1/2^j), S_j = sum (y^(j-1))^2 (the reading under which every
@@ -291,7 +309,8 @@ def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
     A relative error eps_j of lambda_j becomes (1 + eps_j)^(2^j) - 1 =: delta_j in y^(j), since
     y^(j) = (lambda y^(0))^(2^j); the next round starts from a vector whose sum is within
     delta_j of 1, so its S lies in [(1 - delta_j)^2 / n, (1 + delta_j)^2].  Iteration 1 takes
-    v = S_1 / n in [e^(-2A), 1], A = M / 2^k, and lambda_1 = P_1(v) n^(-1/2)."""
+    v = S_1 / n in [e^(-2A), 1], A = M / 2^k, and lambda_1 = P_1(v) n^(-1/2).  Rounds of degree at
+    least interp_from take the Chebyshev interpolant of v^(-1/2^j) instead (inv_root_interp)."""
     A = M / 2.0 ** k
     ce, ee = weighted_minimax(lambda u: np.exp(A * (u - 1.0) / 2.0), lambda u: np.ones_like(u),
                               -1.0, 1.0, exp_deg)
@@ -305,10 +324,16 @@ def design_softmax_b(name, chain_name, n, M, k, exp_deg, inv_degs, margin=0.02):
                 raise ValueError("round %d: delta %.3g >= 1 leaves no interval" % (j - 1, delta))
             lo, hi = (1.0 - delta) ** 2 / n, (1.0 + delta) ** 2
         a, b = lo * (1.0 - margin), hi * (1.0 + margin)
-        c, eps = weighted_minimax(lambda v, e=e: v ** -e, lambda v, e=e: v ** e, a, b, d)
+        interp = interp_from is not None and d >= interp_from
+        if interp:
+            c, eps = inv_root_interp(e, a, b, d)
+        else:
+            c, eps = weighted_minimax(lambda v, e=e: v ** -e, lambda v, e=e: v ** e, a, b, d)
         delta = (1.0 + eps) ** (2 ** j) - 1.0
         iters.append({"deg": d, "a": a, "b": b, "coeffs": hexlist(c), "eps": eps, "delta": delta,
                       "exponent": e, "gain_s": 1.0 / n if j == 1 else 1.0})
+        if interp:
+            iters[-1]["fit"] = "chebyshev interpolant"
     return {"name": name, "chain": chain_name, "version": "B", "n": n, "M": M, "k": k, "A": A,
             "exp": {"kind": "exp", "a": -1.0, "b": 1.0, "deg": exp_deg, "coeffs": hexlist(ce), "err": ee},
             "iters": iters}
@@ -372,8 +397,10 @@ def build_b(write=True, names=None):
         "n4096_M64_B": ("fgb16", 4096, 64.0, 4, 15, [255, 511, 511, 511]),
         # n = 32768 (the vocabulary-sized Softmax of the serving mix): after iteration 1 the
         # interval spans a ratio near 2^15, so degree 1023 in iterations 2-4, each evaluated split
-        # (A + T_512 B) since depth 10 exceeds the room above the bootstrapping input
-        "n32768_M64_B": ("fgb16", 32768, 64.0, 4, 15, [255, 1023, 1023, 1023]),
+        # (A + T_512 B) since depth 10 exceeds the room above the bootstrapping input; those three
+        # are Chebyshev interpolants (the weighted minimax LP of degree 1023 on these intervals
+        # did not finish in two hours here; the interpolants reach eps 2e-6 and below)
+        "n32768_M64_B": ("fgb16", 32768, 64.0, 4, 15, [255, 1023, 1023, 1023], 0.02, 1023),
         # the same level map at N = 2^12 (toybts: user levels 12 ... 4), for the oracle's
         # ciphertext circuit: A = 2 keeps every interval narrow enough for degree 63
         "toybts_n16_M32_B": ("toybts", 16, 32.0, 4, 15, [63, 63, 63, 63]),

@@ -69,6 +69,8 @@ def lib():
             "he_encrypt_slots": [vp, dblp, C.c_int, C.c_double, C.c_uint64, C.c_int, C.POINTER(he_ct), C.c_int],
             "he_softmax": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct), C.c_int],
             "he_softmax_graph": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct)],
+            "he_softmax_register": [vp, C.POINTER(he_softmax_plan)],
+            "he_softmax_nm": [vp, C.POINTER(he_ct), C.c_int, C.c_double, C.c_int, C.c_int],
             "he_softmax_grouped": [vp, C.POINTER(he_softmax_plan), C.POINTER(he_ct), C.c_int],
             "he_ntt": [vp, vp, C.c_int, C.c_int, C.c_int],
             "he_ct_to_coeff": [vp, C.POINTER(he_ct), u64p],
@@ -263,6 +265,20 @@ class Context:
             self.check(lib().he_softmax_graph(self.h, C.byref(pl.s), C.byref(h)))
         else:
             self.check(lib().he_softmax(self.h, C.byref(pl.s), C.byref(h), 1 if batched else 0))
+        cts.update(h)
+        return cts
+
+    def softmax_register(self, plan):
+        """he_softmax_register: the context keeps a copy of the plan for he_softmax_nm."""
+        pl = Plan(plan)   # keeps the arrays the struct points into alive during the call
+        self.check(lib().he_softmax_register(self.h, C.byref(pl.s)))
+
+    def softmax_nm(self, cts, n, M, method="alg4", graph=False):
+        """he_softmax_nm: Softmax of dimension n on inputs encrypted with range M, with the plan
+        registered for (n, M, method); method "alg2" or "alg4"."""
+        h = cts.c()
+        code = {"alg2": 0, "alg4": 1}[method]
+        self.check(lib().he_softmax_nm(self.h, C.byref(h), n, float(M), code, 1 if graph else 0))
         cts.update(h)
         return cts
 

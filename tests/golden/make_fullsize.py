@@ -19,6 +19,8 @@ Cases (keys from seed 2024):
   softmax64_alg2   64 ciphertexts = 8192 Softmax of dim 256 (many-ciphertext packing, Sec. 4.2),
                    attention-logit inputs, plan n256_M128
   softmax64_alg4   the same inputs, plan n256_M128_B
+  softmax1_n32768_alg4   1 ciphertext = 1 Softmax of dim 32768 (the serving mix's largest
+                   dimension), plan n32768_M64_B (Alg. 4 + Alg. 3), uniform inputs on [-64, 0]
 """
 import hashlib
 import json
@@ -52,6 +54,8 @@ CASES = {
                        "enc_seed": 101},
     "softmax64_alg4": {"kind": "softmax", "plan": "n256_M128_B", "m": 64, "inputs": "attention", "input_seed": 7,
                        "enc_seed": 101},
+    "softmax1_n32768_alg4": {"kind": "softmax", "plan": "n32768_M64_B", "m": 1, "inputs": "uniform",
+                             "input_seed": 9, "enc_seed": 103},
 }
 
 

@@ -109,3 +109,27 @@ def test_n_equals_m_needs_no_rotation(toy, params):
     y = _softmax_both(g, o, pl, x, n, 22)
     assert g.counters()["rot"] == rot0
     assert np.abs(y - O.softmax_fp64(x)).max() < 2 ** -15
+
+
+def test_softmax_by_dimension_and_range(toy, params):
+    """he_softmax_nm, the problem statement's form (dimension n, inputs in [-M, 0]): with the
+    plan registered for (n, M, method) it gives the words he_softmax gives with that plan, eagerly
+    and by graph replay; an (n, M) with no registered plan is refused before any launch."""
+    g, o = toy
+    pl = params[1]["cfg1_n16_M8"]
+    n, M = pl["n"], pl["M"]
+    g.keygen_softmax(n, 1)
+    x = np.random.default_rng(4).uniform(-M, 0, (g.n0 // n, n))
+    ref = g.encrypt(x, n, 1, M, 9)
+    g.softmax(ref, pl)
+    assert _code(lambda: g.softmax_nm(g.encrypt(x, n, 1, M, 9), n, M, "alg2")) == EINVAL   # nothing registered
+    g.softmax_register(pl)
+    for graph in (False, True, True):
+        ct = g.encrypt(x, n, 1, M, 9)
+        g.softmax_nm(ct, n, M, "alg2", graph=graph)
+        assert (ct.level, ct.scale) == (ref.level, ref.scale)
+        assert torch.equal(ct.tensor[:2 * (ct.level + 1) * g.n], ref.tensor[:2 * (ref.level + 1) * g.n])
+    ct = g.encrypt(x, n, 1, M, 9)
+    assert _code(lambda: g.softmax_nm(ct, n, 2 * M, "alg2")) == EINVAL      # other range
+    assert _code(lambda: g.softmax_nm(ct, 2 * n, M, "alg2")) == EINVAL      # other dimension
+    assert _code(lambda: g.softmax_nm(ct, n, M, "alg4")) == EINVAL          # other method
