@@ -283,7 +283,8 @@ def run_serve(args):
 
 
 def serve_measure(args, requests, rate):
-    """The serving run of run_serve (its own context, keys and server); returns its line."""
+    """The serving run of run_serve (its own contexts, keys and server); returns its line.
+    --serve-lanes contexts with the same keys: batches of different shapes run concurrently."""
     import torch
 
     from paper_2410_11184_gb300 import he, serve, workloads
@@ -291,10 +292,14 @@ def serve_measure(args, requests, rate):
     chains, plans, evalmod = he.load_params()
     plans = dict(plans, **he.load_plans_b())
     names = ["n128_M64", "n256_M64", "n1024_M64", "n4096_M64_B"] + (["n32768_M64_B"] if "n32768_M64_B" in plans else [])
-    g = he.Context(chains["fgb16"], evalmod["fgb16"])
-    g.keygen(5)
-    for nm in names:
-        g.keygen_softmax(plans[nm]["n"], 1)
+    ctxs = []
+    for _ in range(max(1, args.serve_lanes)):
+        c = he.Context(chains["fgb16"], evalmod["fgb16"])
+        c.keygen(5)   # the same keys in every lane
+        for nm in names:
+            c.keygen_softmax(plans[nm]["n"], 1)
+        ctxs.append(c)
+    g = ctxs[0]
     rng = np.random.default_rng(args.seed)
     pool = {}
     for nm in names:   # a few distinct encrypted inputs per dimension, in pinned host memory
@@ -306,16 +311,17 @@ def serve_measure(args, requests, rate):
             host = torch.empty(ct.tensor.numel(), dtype=torch.int64).pin_memory()
             host.copy_(ct.tensor)
             pool[(nm, v)] = (x, host, ct.level, ct.scale)
+    # warm-up: one Softmax per dimension in every lane (first use of each plan's masks and diagonals)
+    for c in ctxs:
+        for nm in names:
+            x, host, lv, sc = pool[(nm, 0)]
+            w = c.alloc(lv, 1, sc)
+            w.tensor.copy_(host)
+            c.softmax_grouped(w, plans[nm], 1)
     torch.cuda.synchronize()
     free, _ = torch.cuda.mem_get_info()
     budget = 0.5 * free
-    srv = serve.Server(g, {nm: plans[nm] for nm in names}, budget, max_batch_ct=args.max_batch_ct)
-    # warm-up: one request per dimension (first use of every plan's masks and diagonals)
-    for nm in names:
-        x, host, lv, sc = pool[(nm, 0)]
-        srv.submit(nm, host, 1, lv, sc).wait(600)
-    srv.finished.clear()
-    srv.batches.clear()
+    srv = serve.Server(ctxs, {nm: plans[nm] for nm in names}, budget, max_batch_ct=args.max_batch_ct)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, requests))
     picks = [(names[rng.integers(len(names))], int(rng.integers(3))) for _ in range(requests)]
     t0 = time.perf_counter()
@@ -349,14 +355,15 @@ def serve_measure(args, requests, rate):
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
         "softmax_per_s": softmax_done / st["span_s"], "requests": st["requests"], "span_s": st["span_s"],
         "arrival_rate_per_s": rate, "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
+        "lanes": st["lanes"],
         "precision_bits_by_n": {str(n): -math.log2(e) if e > 0 else None for n, e in sorted(worst.items())},
         "n_gpus": 1, "dtype": "u64 (RNS residues mod 42-60-bit primes)", "data": "synthetic",
         "config": {"workload": "Poisson arrivals, one ciphertext per request, dims %s on [-64, 0] (4096 and "
                                 "32768 by Alg. 4)" % "/".join(str(plans[nm]["n"]) for nm in names),
-                   "hbm_budget_gb": budget / 1e9, "max_batch_ct": args.max_batch_ct},
+                   "hbm_budget_gb": budget / 1e9, "max_batch_ct": args.max_batch_ct, "lanes": len(ctxs)},
     }
     srv = None
-    del g
+    del g, ctxs, c
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return line
@@ -445,6 +452,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="default workload: requests of the serving leg (0: off)")
     ap.add_argument("--max-batch-ct", type=int, default=16, help="serve: ciphertexts per batched pass")
+    ap.add_argument("--serve-lanes", type=int, default=1,
+                    help="serve: contexts (same keys) whose batches run concurrently")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-kernel", default="ntt")
     ap.add_argument("--no-plain", action="store_true")
@@ -763,7 +772,7 @@ def main():
         try:
             sl = serve_measure(args, args.serve_requests, args.rate)
             serving = {k: sl[k] for k in ("p50_ms", "p99_ms", "max_ms", "softmax_per_s", "requests", "span_s",
-                                          "arrival_rate_per_s", "batches", "mean_batch_requests",
+                                          "arrival_rate_per_s", "batches", "mean_batch_requests", "lanes",
                                           "precision_bits_by_n")}
             serving["workload"] = sl["config"]["workload"]
         except Exception as e:   # a side measurement: report it, keep the line

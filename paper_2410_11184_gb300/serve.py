@@ -9,6 +9,9 @@ group, so its result is the one it would get alone, bit for bit).  Requests that
 a batch runs are admitted as memory frees up and join the next batch; their uploads (host to
 device, on a copy stream) overlap the running batch, and the previous batch's downloads do too.
 
+With several contexts (the same keys in each), every context is a lane with its own worker
+thread and streams, and batches of different shapes run concurrently on the device.
+
 `BatchPolicy` is the host-only admission and batching rule (tested without a GPU); `Server`
 drives the GPU through the C ABI.
 """
@@ -123,40 +126,62 @@ def percentile(xs, p):
     return s[k]
 
 
+class _Lane:
+    """One context with its upload and download streams, its batches in flight and the worker
+    thread that issues them (the only thread that uses this context while the server runs)."""
+
+    def __init__(self, server, ctx):
+        torch = server.torch
+        self.g = ctx
+        # uploads and downloads on separate streams: the next batch's uploads must not queue
+        # behind the running batch's downloads
+        self.up_stream = torch.cuda.Stream(device=ctx.device)
+        self.down_stream = torch.cuda.Stream(device=ctx.device)
+        self.inflight = collections.deque()   # (batch, device buffer, done event)
+        self.wake = threading.Event()
+        self.thread = threading.Thread(target=server._loop, args=(self,), daemon=True)
+
+
 class Server:
-    """The worker thread that owns the context while the server runs (do not use the context
-    from another thread meanwhile).  plans: {name: plan dict}."""
+    """Continuous batching over one or more contexts on the device (ctx: a context, or a list of
+    contexts with the same keys, e.g. made with the same keygen seed).  Every context has its own
+    worker thread and stream, so batches of different shapes -- requests of different
+    dimensions -- run concurrently on the GPU: while one lane's one-ciphertext circuit leaves SMs
+    idle, another lane's fills them.  A batch's result does not depend on the lane that runs it.
+    Do not use the contexts from another thread while the server runs.  plans: {name: plan dict}."""
 
     def __init__(self, ctx, plans, budget_bytes, max_batch_ct=64, work_factor=8.0, max_inflight=2, start=True):
         import torch
 
         self.torch = torch
-        self.g = ctx
+        ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+        self.g = ctxs[0]
         self.plans = plans
         self.policy = BatchPolicy(budget_bytes, max_batch_ct, work_factor)
-        # uploads and downloads on separate streams: the next batch's uploads must not queue
-        # behind the running batch's downloads
-        self.up_stream = torch.cuda.Stream(device=ctx.device)
-        self.down_stream = torch.cuda.Stream(device=ctx.device)
         self.max_inflight = max_inflight
-        self.lock = threading.Lock()
+        self.lock = threading.Lock()   # guards the queues, the policy and the result lists
         self.arrivals = collections.deque()
         self.waiting = collections.deque()
         self.admitted = []
-        self.inflight = collections.deque()   # (batch, device buffer, done event)
         self.finished = []
         self.batches = []                      # sizes (requests, ciphertexts) of the batches run
         self.running = True
-        self.wake = threading.Event()
-        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.lanes = [_Lane(self, c) for c in ctxs]
+        self.started = False
         if start:
-            self.thread.start()
+            self.start()
 
     def start(self):
-        """Starts the worker (for a server created with start=False: requests submitted before
+        """Starts the workers (for a server created with start=False: requests submitted before
         are then admitted together)."""
-        if not self.thread.is_alive():
-            self.thread.start()
+        if not self.started:
+            self.started = True
+            for ln in self.lanes:
+                ln.thread.start()
+
+    def _wake_all(self):
+        for ln in self.lanes:
+            ln.wake.set()
 
     # ---- client side
     def submit(self, plan, host_in, n_ct, level, scale):
@@ -170,15 +195,16 @@ class Server:
         r = Request(plan, n_ct, level, scale, host_in, host_out, words)
         with self.lock:
             self.arrivals.append(r)
-        self.wake.set()
+        self._wake_all()
         return r
 
     def close(self):
-        """Finishes every submitted request, then stops the worker."""
+        """Finishes every submitted request, then stops the workers."""
         self.start()
         self.running = False
-        self.wake.set()
-        self.thread.join()
+        self._wake_all()
+        for ln in self.lanes:
+            ln.thread.join()
 
     def stats(self):
         lat = [r.latency_ms for r in self.finished if r.error is None]
@@ -186,51 +212,57 @@ class Server:
             return {"requests": 0}
         span = max(r.t_done for r in self.finished) - min(r.t_submit for r in self.finished)
         return {"requests": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
-                "max_ms": max(lat), "span_s": span, "batches": len(self.batches),
+                "max_ms": max(lat), "span_s": span, "batches": len(self.batches), "lanes": len(self.lanes),
                 "mean_batch_requests": sum(b[0] for b in self.batches) / len(self.batches),
                 "mean_batch_ct": sum(b[1] for b in self.batches) / len(self.batches)}
 
-    # ---- worker
-    def _loop(self):
+    # ---- workers
+    def _loop(self, ln):
         while True:
             # cleared before the arrivals are drained: a submit() after this point sets it again,
             # so the wait below returns at once instead of sleeping through its timeout
-            self.wake.clear()
+            ln.wake.clear()
             with self.lock:
                 while self.arrivals:
                     self.waiting.append(self.arrivals.popleft())
-            for r in self.policy.admit(self.waiting, self.admitted):
-                self._fail(r, "request larger than the server's HBM budget or batch limit")
-            self._retire()
-            if self.admitted and len(self.inflight) < self.max_inflight:
-                self._launch(self.policy.next_batch(self.admitted))
+                for r in self.policy.admit(self.waiting, self.admitted):
+                    self._fail(r, "request larger than the server's HBM budget or batch limit")
+                freed = self._retire(ln)
+                batch = None
+                if self.admitted and len(ln.inflight) < self.max_inflight:
+                    batch = self.policy.next_batch(self.admitted)
+                idle = not (self.waiting or self.admitted or self.arrivals)
+            if freed:
+                self._wake_all()   # memory was released: the other lanes may admit more
+            if batch:
+                self._launch(ln, batch)
                 continue
-            if not self.running and not (self.waiting or self.admitted or self.inflight or self.arrivals):
+            if not self.running and idle and not ln.inflight:
                 return
-            self.wake.wait(0.0002 if self.inflight else 0.01)
+            ln.wake.wait(0.0002 if ln.inflight else 0.01)
 
-    def _launch(self, batch):
-        torch, g = self.torch, self.g
+    def _launch(self, ln, batch):
+        torch, g = self.torch, ln.g
         r0 = batch[0]
         nct = sum(r.n_ct for r in batch)
-        dev = g.alloc(r0.level, nct, r0.scale)
         try:
+            dev = g.alloc(r0.level, nct, r0.scale)
             # uploads on the upload stream, then the batched circuit on the context stream
-            with torch.cuda.stream(self.up_stream):
+            with torch.cuda.stream(ln.up_stream):
                 off = 0
                 for r in batch:
                     dev.tensor[off:off + r.words].copy_(r.host_in, non_blocking=True)
                     off += r.words
                 up = torch.cuda.Event()
-                up.record(self.up_stream)
+                up.record(ln.up_stream)
             g.stream.wait_event(up)
             g.softmax_grouped(dev, self.plans[r0.plan], len(batch))
             fin = torch.cuda.Event()
             fin.record(g.stream)
             # each request's part back to its host buffer once the batch is done
-            self.down_stream.wait_event(fin)
+            ln.down_stream.wait_event(fin)
             per = 2 * (dev.level + 1) * g.n
-            with torch.cuda.stream(self.down_stream):
+            with torch.cuda.stream(ln.down_stream):
                 off = 0
                 for r in batch:
                     w = r.n_ct * per
@@ -238,17 +270,21 @@ class Server:
                     r.out_level, r.out_scale = dev.level, dev.scale
                     off += w
                 down = torch.cuda.Event()
-                down.record(self.down_stream)
-            self.inflight.append((batch, dev, down))
-            self.batches.append((len(batch), nct))
+                down.record(ln.down_stream)
+            ln.inflight.append((batch, dev, down))
+            with self.lock:
+                self.batches.append((len(batch), nct))
         except Exception as e:  # noqa: BLE001 - reported on every request of the batch
-            for r in batch:
-                self._fail(r, str(e))
-            self.policy.release(batch)
+            with self.lock:
+                for r in batch:
+                    self._fail(r, str(e))
+                self.policy.release(batch)
 
-    def _retire(self):
-        while self.inflight and self.inflight[0][2].query():
-            batch, dev, _ = self.inflight.popleft()
+    def _retire(self, ln):
+        """(lock held) Finishes the lane's batches whose downloads are done; True if any."""
+        freed = False
+        while ln.inflight and ln.inflight[0][2].query():
+            batch, dev, _ = ln.inflight.popleft()
             t = time.perf_counter()
             for r in batch:
                 r.t_done = t
@@ -256,8 +292,11 @@ class Server:
                 r.done.set()
             self.policy.release(batch)
             del dev
+            freed = True
+        return freed
 
     def _fail(self, r, msg):
+        """(lock held)"""
         r.error = msg
         r.t_done = time.perf_counter()
         self.finished.append(r)

@@ -29,7 +29,12 @@ def full(params):
     return g, ch, em
 
 
-def test_fullsize_ops_bit_exact(full):
+@pytest.mark.parametrize("fuse_conv", [-1, 0, 1])
+def test_fullsize_ops_bit_exact(full, fuse_conv):
+    """Multiplication (relinearise + rescale as one division) and rotation at level 12, limb for
+    limb against the oracle; with the basis conversions as the default chooses (-1), forced
+    separate (0) and forced into the forward transforms' column passes (1, NttFuse kinds 4-6 in
+    their N = 2^16 instances)."""
     g, ch, em = full
     o = O.Oracle(ch)
     o.keygen(2024)
@@ -38,8 +43,19 @@ def test_fullsize_ops_bit_exact(full):
     a = o.encrypt(rng.uniform(-1, 1, o.n0), top, 2.0 ** 42, 1, 0)
     b = o.encrypt(rng.uniform(-1, 1, o.n0), top, 2.0 ** 42, 1, 1)
     ga, gb = g.from_coeff(a.data, top, a.scale), g.from_coeff(b.data, top, b.scale)
-    assert np.array_equal(g.to_coeff(g.hmult(ga, gb))[0], o.hmult(a, b).data)
-    assert np.array_equal(g.to_coeff(g.rotate(ga, 1))[0], o.rotate(a, 1).data)
+    g.tune_force("fuse_conv", fuse_conv)
+    try:
+        assert np.array_equal(g.to_coeff(g.hmult(ga, gb))[0], o.hmult(a, b).data)
+        assert np.array_equal(g.to_coeff(g.rotate(ga, 1))[0], o.rotate(a, 1).data)
+        # two ciphertexts in one batch with one ModUp launch per digit (one ciphertext above took
+        # the all-digits launch, the default for small batches)
+        g.tune_force("modup", 0)
+        two = g.from_coeff(np.stack([a.data, b.data]), top, a.scale)
+        got = g.to_coeff(g.hmult(two, two))
+        assert np.array_equal(got[0], o.hmult(a, a).data) and np.array_equal(got[1], o.hmult(b, b).data)
+    finally:
+        g.tune_force("fuse_conv", -1)
+        g.tune_force("modup", -1)
 
 
 @pytest.mark.parametrize("m,kind", [(1, "uniform"), (1, "paper_normal"), (64, "attention")])

@@ -2,8 +2,9 @@
 
 he_softmax_grouped runs independent Softmax groups in one batched pass; every group must come
 out exactly as it would alone (and as the oracle computes it).  The server mixes requests of
-two dimensions and two ciphertext counts, arriving while earlier batches run; every request's
-result must equal the same request run alone, bit for bit, and decrypt to the FP64 Softmax."""
+two dimensions and two ciphertext counts, arriving while earlier batches run, on one context or
+on two (two lanes, batches running concurrently); every request's result must equal the same
+request run alone, bit for bit, and decrypt to the FP64 Softmax."""
 import time
 
 import numpy as np
@@ -74,8 +75,18 @@ def test_grouped_equals_alone_and_oracle(ctx, params, m, groups, plan):
         assert np.array_equal(got[j], outs[j].data), j
 
 
-def test_server_mix_equals_alone(ctx, params):
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_server_mix_equals_alone(ctx, params, lanes):
+    """lanes = 2: a second context with the same keys, so two batches of different shapes run
+    concurrently on the device; every result must still be the one the request gets alone."""
     g, o, em = ctx
+    ctxs = [g]
+    if lanes == 2:
+        g2 = he.Context(params[0]["toybts"], params[2]["toybts"])
+        g2.keygen(SEED)
+        for n, m in ((16, 1), (16, 2), (64, 1)):
+            g2.keygen_softmax(n, m)
+        ctxs.append(g2)
     plans = {k: params[1][k] for k in ("toybts_n16_M32", "toybts_n64_M32")}
     # (plan, ciphertexts per request): two dimensions, two shapes for n = 16
     spec = [("toybts_n16_M32", 1), ("toybts_n64_M32", 1), ("toybts_n16_M32", 2), ("toybts_n16_M32", 1),
@@ -91,7 +102,7 @@ def test_server_mix_equals_alone(ctx, params):
     torch.cuda.synchronize()
     # a budget for six single-ciphertext requests at a time: the last ones wait for memory
     words1 = 2 * (reqs[0][3].level + 1) * g.n
-    srv = serve.Server(g, plans, budget_bytes=6.5 * words1 * 8 * 8.0, max_batch_ct=4, start=False)
+    srv = serve.Server(ctxs, plans, budget_bytes=6.5 * words1 * 8 * 8.0, max_batch_ct=4, start=False)
     handles = [srv.submit(name, host, m, ct.level, ct.scale) for name, m, x, ct, host in reqs[:5]]
     srv.start()                 # the first five arrive together
     time.sleep(0.05)            # the rest arrive while the first batches run
@@ -101,6 +112,7 @@ def test_server_mix_equals_alone(ctx, params):
     srv.close()
     st = srv.stats()
     assert st["requests"] == len(spec) and st["batches"] < len(spec)   # some requests shared a batch
+    assert st["lanes"] == lanes
     for (name, m, x, ct, host), h in zip(reqs, handles):
         pl = plans[name]
         alone = g.like(ct)
