@@ -422,7 +422,14 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     REQUIRE(!fuse || !inverse, HE_EINVAL, "fused transform: forward only");
     // timing family: the call site with the direction ("ntt_modup" forward, "ntt_modup_inv"
     // inverse); algorithmic bytes: the transform's read + write of every limb, 16 N per limb
-    ProfScope ps(c, inverse ? ntt_inv_family(site) : site, 16.0 * count * c->N);
+    // (kind 7 leaves the digits' own limbs: ndc digits per group of ndc polynomials)
+    long work = count;
+    if (fuse && fuse->kind == 7) {
+        long own = 0;
+        for (int j = 0; j < fuse->ndc; j++) own += fuse->dds[j];
+        work -= (long)count / ((long)map.nper * fuse->ndc) * own;
+    }
+    ProfScope ps(c, inverse ? ntt_inv_family(site) : site, 16.0 * work * c->N);
     c->launches++;
     bool small = false;
     if (c->tune_force[HE_TUNE_NTT_SMALL] >= 0) {
@@ -661,10 +668,19 @@ static DPtr ks_modup(he_ctx *c, const uint64_t *x, long sx, int nct, int L) {
         {
             ProfScope ps(c, "modup", 8.0 * c->N * ((double)nct * L + (double)nct * nd * nl));
             klaunch(k_modup_all, grid, 256, 0, c->st)(dig.get(), (long)nd * nl * c->N, tmp.get(), (long)L * c->N, nct, D, nl,
-                                                 em, c->d_mods, c->d_cv + c->cv_off[L - 1][0], c->logN);
+                                                 em, c->d_mods, c->d_cv + c->cv_off[L - 1][0], c->logN, x, sx);
         }
         LAUNCH_CHECK();
-        ntt(c, dig.get(), nct * nd * nl, em, (long)nl * c->N, false, "ntt_modup");
+        // the digits' own limbs were copied in NTT form: the transform leaves them (kind 7)
+        NttFuse F{};
+        F.kind = 7;
+        F.ndc = nd;
+        F.j0 = 0;
+        for (int j = 0; j < nd; j++) {
+            F.dlo[j] = D.lo[j];
+            F.dds[j] = D.ds[j];
+        }
+        ntt(c, dig.get(), nct * nd * nl, em, (long)nl * c->N, false, "ntt_modup", nullptr, 0, &F);
         return dig;
     }
     for (int j = 0; j < nd; j++) {
@@ -1692,9 +1708,13 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         dim3 grid((unsigned)std::min<long>(tiles, c->max_grid / 4), 1);
         size_t smem = (size_t)A.npt * HE_LT_KT * 8;
         ProfScope ps_(c, "lintrans", 8.0 * c->N * ((double)L * A.npt + (double)x.nct * 2 * L * (A.nb + A.na)));
-        if (tune_pick(c, HE_TUNE_LT_ROWS, L, x.nct, 2 * x.nct <= 8))   // a few rows: no staging
-            klaunch(k_lt_bsgs_direct, grid_for(c, (long)L << c->logN), 256, 0, c->st)(A, 2 * x.nct, L, qmap(L), c->d_mods,
-                                                                                 c->logN);
+        if (tune_pick(c, HE_TUNE_LT_ROWS, L, x.nct, 2 * x.nct <= 8)) {   // a few rows: no staging
+            if (x.nct == 1 && (A.nb == 4 || A.nb == 8 || A.nb == 16))     // both rows' baby steps in registers
+                launch_lt_ct1(grid_for(c, (long)L << c->logN), c->st, A, 2, L, qmap(L), c->d_mods, c->logN);
+            else
+                klaunch(k_lt_bsgs_direct, grid_for(c, (long)L << c->logN), 256, 0, c->st)(A, 2 * x.nct, L, qmap(L),
+                                                                                     c->d_mods, c->logN);
+        }
         else
             klaunch(k_lt_bsgs, grid, 256, smem, c->st)(A, 2 * x.nct, L, qmap(L), c->d_mods, c->logN);
     }

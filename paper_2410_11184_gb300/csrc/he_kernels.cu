@@ -199,6 +199,50 @@ __global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const
     }
 }
 
+// The same sums for one ciphertext (two rows) with NB baby steps known at compile time: a thread
+// keeps both rows' NB baby-step values in registers (4 NB words) and reads every plaintext word
+// once, using it for both rows, so each input of the level is read once.  (With the bound
+// HE_LT_MAXB = 16 instead of NB the same idea needed 103 registers and lost occupancy.)
+template <int NB>
+__global__ void __launch_bounds__(256) k_lt_bsgs_ct1(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods,
+                                                     int logN) {
+    grid_dep_enter();
+    const int N = 1 << logN;
+    long total = (long)L << logN;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(id >> logN), k = (int)(id & (N - 1));
+        const ModC m = mods[qmap.prime[l]];
+        const long o0 = (long)l * N + k, o1 = ((long)L + l) * N + k;
+        uint64_t b0[NB], b1[NB];
+#pragma unroll
+        for (int b = 0; b < NB; b++) {
+            b0[b] = A.baby[b][o0];
+            b1[b] = npoly > 1 ? A.baby[b][o1] : 0;
+        }
+        for (int a = 0; a < A.na; a++) {
+            uint64_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll
+            for (int b = 0; b < NB; b++) {
+                const int pi = A.ptix[a][b];
+                if (pi >= 0) {
+                    const uint64_t pv = A.pt[pi][o0];
+                    mac_wide(lo0, hi0, b0[b], pv);
+                    mac_wide(lo1, hi1, b1[b], pv);
+                }
+            }
+            A.out[a][o0] = redc(lo0, hi0, m);
+            if (npoly > 1) A.out[a][o1] = redc(lo1, hi1, m);
+        }
+    }
+}
+
+void launch_lt_ct1(dim3 grid, cudaStream_t st, const LtArgs &A, int npoly, int L, const LimbMap &qmap, const ModC *mods,
+                   int logN) {
+    if (A.nb == 4) klaunch(k_lt_bsgs_ct1<4>, grid, 256, 0, st)(A, npoly, L, qmap, mods, logN);
+    else if (A.nb == 8) klaunch(k_lt_bsgs_ct1<8>, grid, 256, 0, st)(A, npoly, L, qmap, mods, logN);
+    else klaunch(k_lt_bsgs_ct1<16>, grid, 256, 0, st)(A, npoly, L, qmap, mods, logN);
+}
+
 // out[c][p][l] = sum_t x_t[c][p][l] w_t[l] (+ w_nt[l] when p = 0) for l < L: rows t < nt of w in
 // Montgomery form (sums of at most 8 products stay below q 2^64), row nt a plain residue.
 // Reads each input once (only its first L limbs).
@@ -279,9 +323,11 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
 // ModUp of all digits of nct polynomials in one launch (grid.y = digit j): every target limb of
 // the extended basis is converted, the digit's own limbs included (there the conversion is the
 // CRT identity and returns x exactly), so one transform of all digits follows.  Output
-// [nct][ndig][ntarget][N] (coefficient form).
+// [nct][ndig][ntarget][N] (coefficient form).  With xntt given, the digit's own limbs are copied
+// from the NTT-form input instead (xntt + c sxn), and the transform after skips them (kind 7).
 __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long sx, int nct, ModUpDigits D,
-                            int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN) {
+                            int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN,
+                            const uint64_t *xntt, long sxn) {
     grid_dep_enter();
     const int N = 1 << logN;
     const int j = blockIdx.y, lo = D.lo[j], ds = D.ds[j];
@@ -304,6 +350,10 @@ __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long s
         }
         uint64_t *o = out + c * so_ct + (long)j * ntarget * N + k;
         for (int t = 0; t < ntarget; t++) {
+            if (xntt && t >= lo && t < lo + ds) {   // the digit's own limb: the NTT-form input
+                o[(long)t * N] = xntt[c * sxn + (long)t * N + k];
+                continue;
+            }
             const ModC mt = mods[tmap.prime[t]];
             uint64_t l0 = 0, h0 = 0;
 #pragma unroll
@@ -872,6 +922,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_cols_fwd_rb(uint
     // out of place when src is given: read limb l of src, write base
     const uint64_t *in = src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a;
     uint64_t v[E];
+    if (KIND == 7) {
+        // ModUp of all digits: the digit's own limbs are already in NTT form (copied by the
+        // conversion), the transform leaves them
+        const int t = l % nper, dj = F.j0 + (l / nper) % F.ndc;
+        if (t >= F.dlo[dj] && t < F.dlo[dj] + F.dds[dj]) return;   // uniform over the CTA
+    }
     if (KIND == 2) {
         // rescale: t_i = centred last limb mod q_i
         const ModC mi = mods[p];
@@ -934,7 +990,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint
     const uint64_t q = mods[p].q;
     const ulonglong2 *psi = tw2 + (long)p * 2 * N;
     const int k = threadIdx.x % TPS, rr = threadIdx.x / TPS, row = blockIdx.x * SUB + rr;
-    if (KIND == 4) {   // ModUp: the digit's own limbs were copied in NTT form by the column pass
+    if (KIND == 4 || KIND == 7) {   // ModUp: the digit's own limbs are in NTT form already
         const int t = l % nper, dj = F.j0 + (l / nper) % F.ndc;
         if (t >= F.dlo[dj] && t < F.dlo[dj] + F.dds[dj]) return;   // uniform over the CTA
     }
@@ -968,7 +1024,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 12) k_ntt_rows_fwd_rb(uint
         sm[rr * SP + (E + 1) * k + j] = r;
     }
     __syncthreads();
-    if (KIND == 0 || KIND == 4) {
+    if (KIND == 0 || KIND == 4 || KIND == 7) {
 #pragma unroll
         for (int j = 0; j < E; j++) g[k + E * j] = sm[rr * SP + k + (E + 1) * j];
         return;
@@ -1092,6 +1148,7 @@ static void launch_rb(bool inverse, int count, uint64_t *base, int nper, long po
     HE_FWD_KIND(4)
     HE_FWD_KIND(5)
     HE_FWD_KIND(6)
+    HE_FWD_KIND(7)
 #undef HE_FWD_KIND
     if (!inverse && F.kind == 1) {
         klaunch(k_ntt_cols_fwd_rb<LOGE, 1, NT>, g, NT, 0, st)(base, nper, poly_stride, map, mods, tw2, logN, src, src_stride, F);

@@ -81,6 +81,8 @@ struct LtArgs {
 //   kind 5 (ModDown): as kind 1, with conv computed from the ns limbs slo .. slo + ns - 1 of
 //       src + p sstride (moduli sidx[s]); weights cvw[s wstride + prime].
 //   kind 6 (relinearise + rescale): as kind 3, with conv computed as in kind 5.
+//   kind 7 (ModUp of all digits after k_modup_all with its NTT-form copies): a plain forward
+//       transform of the batch that leaves the digits' own limbs (dlo, dds, ndc, j0 as in kind 4).
 struct NttFuse {
     int kind;
     int alpha;
@@ -151,12 +153,16 @@ __global__ void k_automorph_acc(uint64_t *out, long so, const uint64_t *a, long 
                                 const ModC *mods, int g, int logN);
 __global__ void k_lt_bsgs(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN);
 __global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods, int logN);
+// k_lt_bsgs_ct1<nb>: the unstaged sums of one ciphertext (npoly <= 2); A.nb must be 4, 8 or 16
+void launch_lt_ct1(dim3 grid, cudaStream_t st, const LtArgs &A, int npoly, int L, const LimbMap &qmap, const ModC *mods,
+                   int logN);
 __global__ void k_lincomb(uint64_t *out, LcArgs A, int nct, int L, LimbMap qmap, const ModC *mods, int logN);
 __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t *x, long sx, int nct,
                         int digit_lo, int dsize, int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cv,
                         int logN, const uint64_t *xntt, long sxn);
 __global__ void k_modup_all(uint64_t *out, long so_ct, const uint64_t *x, long sx, int nct, ModUpDigits D,
-                            int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN);
+                            int ntarget, LimbMap tmap, const ModC *mods, const uint64_t *cvbase, int logN,
+                            const uint64_t *xntt, long sxn);
 __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int L, int alpha, LimbMap qmap,
                                const int *pidx, const ModC *mods, const uint64_t *cv, int nqall, int logN);
 
