@@ -1709,8 +1709,14 @@ static DCt lt_eval_level(he_ctx *c, const DCt &x, const LtDesc &lv, double gain,
         size_t smem = (size_t)A.npt * HE_LT_KT * 8;
         ProfScope ps_(c, "lintrans", 8.0 * c->N * ((double)L * A.npt + (double)x.nct * 2 * L * (A.nb + A.na)));
         if (tune_pick(c, HE_TUNE_LT_ROWS, L, x.nct, 2 * x.nct <= 8)) {   // a few rows: no staging
-            if (x.nct == 1 && (A.nb == 4 || A.nb == 8 || A.nb == 16))     // both rows' baby steps in registers
-                launch_lt_ct1(grid_for(c, (long)L << c->logN), c->st, A, 2, L, qmap(L), c->d_mods, c->logN);
+            if (x.nct == 1 && (A.nb == 4 || A.nb == 8 || A.nb == 16)) {   // both rows' baby steps in registers
+                // few limbs (the low SlotToCoeff levels): the giant steps over 2 or 4 threads
+                dim3 g1 = grid_for(c, (long)L << c->logN);
+                long cta = ((long)L << c->logN) / 256;
+                g1.y = cta * 4 <= c->max_grid ? 4 : cta * 2 <= c->max_grid ? 2 : 1;
+                if ((int)g1.y > A.na) g1.y = std::max(1, A.na);
+                launch_lt_ct1(g1, c->st, A, 2, L, qmap(L), c->d_mods, c->logN);
+            }
             else
                 klaunch(k_lt_bsgs_direct, grid_for(c, (long)L << c->logN), 256, 0, c->st)(A, 2 * x.nct, L, qmap(L),
                                                                                      c->d_mods, c->logN);

@@ -203,6 +203,8 @@ __global__ void k_lt_bsgs_direct(LtArgs A, int npoly, int L, LimbMap qmap, const
 // keeps both rows' NB baby-step values in registers (4 NB words) and reads every plaintext word
 // once, using it for both rows, so each input of the level is read once.  (With the bound
 // HE_LT_MAXB = 16 instead of NB the same idea needed 103 registers and lost occupancy.)
+// grid.y splits the giant steps of a coefficient over that many threads (each reloads the baby
+// steps): low levels have few limbs and otherwise too few threads to hide the plaintext loads.
 template <int NB>
 __global__ void __launch_bounds__(256) k_lt_bsgs_ct1(LtArgs A, int npoly, int L, LimbMap qmap, const ModC *mods,
                                                      int logN) {
@@ -219,7 +221,8 @@ __global__ void __launch_bounds__(256) k_lt_bsgs_ct1(LtArgs A, int npoly, int L,
             b0[b] = A.baby[b][o0];
             b1[b] = npoly > 1 ? A.baby[b][o1] : 0;
         }
-        for (int a = 0; a < A.na; a++) {
+        const int ag = (A.na + gridDim.y - 1) / gridDim.y, a1 = min(A.na, (int)(blockIdx.y + 1) * ag);
+        for (int a = blockIdx.y * ag; a < a1; a++) {
             uint64_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
 #pragma unroll
             for (int b = 0; b < NB; b++) {
