@@ -306,6 +306,8 @@ __global__ void k_modup(uint64_t *out, long so_ct, long so_digit, const uint64_t
         // reproduce their coefficients)
         for (int i = 0; i < dsize; i++)
             o[(long)(digit_lo + i) * N] = xntt[c * sxn + (long)(digit_lo + i) * N + k];
+        // (two targets per iteration: two independent 128-bit sums in flight per thread)
+#pragma unroll 2
         for (int t = 0; t < ntarget; t++) {
             if (t == digit_lo) t += dsize;
             if (t >= ntarget) break;
@@ -401,6 +403,7 @@ __global__ void k_moddown_conv(uint64_t *out, const uint64_t *x, int npoly, int 
             y[j] = v;
         }
         uint64_t *o = out + (long)pl * L * N + k;
+#pragma unroll 2
         for (int i = 0; i < L; i++) {
             const ModC mi = mods[qmap.prime[i]];
             // one 128-bit sum, reduced once (phat_j mod q_i stored in Montgomery form)
