@@ -511,13 +511,19 @@ def main():
         table = g.tune_table()
         tune = {"seconds": round(time.perf_counter() - t0, 2), "entries": len(table),
                 "keys": "(op, limbs, n_ct) for levels 1..%d and n_ct in %s" % (len(ch["q"]) - 1, sorted({1, m})),
-                "non_default": [e for e in table if e["op"] != "ntt_small"
-                                and e["choice"] != (1 if e["n_ct"] <= 4 else 0)],
+                "non_default": [e for e in table if e["op"] not in ("ntt_small", "ntt_1pass")
+                                and e["choice"] != ((0 if e["op"] == "fuse_conv" else 1) if e["n_ct"] <= 4 else 0)],
                 "ntt_small_cta_at_limbs": {d: [e["limbs"] for e in table if e["op"] == "ntt_small"
                                                and e["n_ct"] == i and e["choice"] == 1]
                                            for i, d in enumerate(("forward", "inverse"))},
                 "ntt_small_cta_ms": {"%s_%d" % ("fwd" if e["n_ct"] == 0 else "inv", e["limbs"]): e["ms"]
-                                     for e in table if e["op"] == "ntt_small"}}
+                                     for e in table if e["op"] == "ntt_small"},
+                # one launch per limb cluster (distributed shared memory) against the two passes
+                "ntt_1pass_at_limbs": {d: [e["limbs"] for e in table if e["op"] == "ntt_1pass"
+                                           and e["n_ct"] == i and e["choice"] == 1]
+                                       for i, d in enumerate(("forward", "inverse"))},
+                "ntt_1pass_ms": {"%s_%d" % ("fwd" if e["n_ct"] == 0 else "inv", e["limbs"]): e["ms"]
+                                 for e in table if e["op"] == "ntt_1pass"}}
     x = attention_logits(L, n, seed=seeds["inputs"])
     src = g.encrypt(x, n, m, M, seeds["encrypt"])
     work = g.like(src)

@@ -285,7 +285,11 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
  * count; 256 until tuned; table entries (HE_TUNE_NTT_SMALL, limbs, 0 forward / 1 inverse)),
  * HE_TUNE_FUSE_CONV (1: the fast basis conversions of ModUp and ModDown computed inside the
  * column pass of the forward transform that follows them, so the converted limbs are never
- * written to HBM; 0: a conversion kernel, then the transform; timed on one relinearisation).
+ * written to HBM; 0: a conversion kernel, then the transform; timed on one relinearisation),
+ * HE_TUNE_NTT_1PASS (N = 2^16 only: 1: a transform without fused neighbours as one launch, one
+ * thread-block cluster of 8 CTAs per limb exchanging between its two passes in distributed shared
+ * memory; 0: the two passes; a ladder of limb counts per direction as for HE_TUNE_NTT_SMALL, off
+ * until tuned).
  * Without a table entry the choice is 1 for batches of at most 4 ciphertexts (8 rows for
  * HE_TUNE_LT_ROWS), and 0 for HE_TUNE_FUSE_CONV.
  * he_autotune times both variants of every operation on the device (CUDA events on the context
@@ -301,6 +305,7 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
 #define HE_TUNE_BRANCHES 4
 #define HE_TUNE_NTT_SMALL 5
 #define HE_TUNE_FUSE_CONV 6
+#define HE_TUNE_NTT_1PASS 7
 int he_autotune(he_ctx *ctx, const int *levels, int n_levels, const int *ncts, int n_ncts, int reps);
 /* the table as text, one line "op limbs n_ct choice ms_variant0 ms_variant1" per entry, into buf
  * (len bytes, NUL-terminated; HE_EINVAL if too small) */

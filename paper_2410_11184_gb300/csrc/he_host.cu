@@ -154,10 +154,13 @@ struct he_ctx {
         float ms[2];
     };
     std::map<std::tuple<int, int, int>, TuneRec> tune;
-    int tune_force[7] = {-1, -1, -1, -1, -1, -1, -1};
+    int tune_force[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     // CTA size of the transforms per direction (forward, inverse): the autotuner's choice at each
     // limb count of its ladder; a launch takes the choice of the largest ladder count <= its own
     std::vector<std::pair<int, int>> ntt_small[2];
+    // one-pass transforms (N = 2^16, no fused neighbours) per direction: the autotuner's choice at
+    // each limb count of its ladder, as for ntt_small (off until tuned)
+    std::vector<std::pair<int, int>> ntt_1pass[2];
     cudaStream_t st = nullptr;
     // side streams for independent branches of a circuit (Branch), created on first use
     static const int NSIDE = 4;
@@ -354,6 +357,10 @@ static dim3 grid_for(he_ctx *c, long total) {
 //                     launch on the context stream, in the same order as the host issues it
 //   HE_TUNE_NTT_SMALL 1: the transform in CTAs of 64 threads (4 sub-transforms each); 0: 256
 //                     threads.  Chosen per direction from a ladder of limb counts (ntt_small).
+//   HE_TUNE_NTT_1PASS 1: a transform of N = 2^16 limbs without fused neighbours as one launch
+//                     per limb cluster (8 CTAs, the passes' exchange in distributed shared
+//                     memory); 0: the two register-blocked passes.  Per direction and limb count
+//                     from a ladder (ntt_1pass); off until tuned.
 //   HE_TUNE_FUSE_CONV 1: the basis conversions of ModUp and ModDown computed in the column pass
 //                     of the forward transform that follows them (NttFuse kinds 4-6); 0: a
 //                     conversion kernel writes the converted limbs, then the transform reads them
@@ -431,6 +438,21 @@ static void ntt(he_ctx *c, uint64_t *base, int count, const LimbMap &map, long p
     }
     ProfScope ps(c, inverse ? ntt_inv_family(site) : site, 16.0 * work * c->N);
     c->launches++;
+    if (c->logN == 16 && !fuse) {
+        bool one = false;
+        if (c->tune_force[HE_TUNE_NTT_1PASS] >= 0) {
+            one = c->tune_force[HE_TUNE_NTT_1PASS] == 1;
+        } else {
+            for (const auto &e : c->ntt_1pass[inverse ? 1 : 0])   // ascending limb counts
+                if (e.first <= count) one = e.second == 1;
+        }
+        if (one) {
+            launch_ntt_1pass(inverse, count, base, map.nper, poly_stride, map, c->d_mods, c->d_tw2,
+                             ninv ? ninv : c->d_ninv, c->logN, c->st, src, src_stride);
+            LAUNCH_CHECK();
+            return;
+        }
+    }
     bool small = false;
     if (c->tune_force[HE_TUNE_NTT_SMALL] >= 0) {
         small = c->tune_force[HE_TUNE_NTT_SMALL] == 1;
@@ -2499,6 +2521,7 @@ static void build_tables(he_ctx *c) {
     REQUIRE(al >= 1 && al <= 8 && c->ndig_top <= 8, HE_EINVAL, "alpha and the digit count must be at most 8");
     // linear-transform inner sums: up to HE_LT_MAXPT staged plaintext tiles of HE_LT_KT words
     CK(cudaFuncSetAttribute(k_lt_bsgs, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_LT_MAXPT * HE_LT_KT * 8));
+    if (c->logN == 16) REQUIRE(ntt_1pass_setup() == 0, HE_EINVAL, "one-pass transform: shared memory limit");
 }
 
 // ---- autotuner
@@ -2606,6 +2629,17 @@ static void autotune(he_ctx *c, const std::vector<int> &levels, const std::vecto
             }
             c->ntt_small[inv] = ladder;
         }
+        // one pass per limb (N = 2^16) against the two passes with the CTA size just chosen
+        if (c->logN == 16)
+            for (int inv = 0; inv < 2; inv++) {
+                std::vector<std::pair<int, int>> ladder;
+                for (int n : counts) {
+                    tune_op(c, HE_TUNE_NTT_1PASS, n, inv, reps,
+                            [&] { ntt(c, buf.get(), n, qmap(1), c->N, inv != 0); });
+                    ladder.push_back({n, c->tune[std::make_tuple(HE_TUNE_NTT_1PASS, n, inv)].choice});
+                }
+                c->ntt_1pass[inv] = ladder;
+            }
     }
     CK(cudaStreamSynchronize(c->st));
     // the tuner's own work is not counted, and its diagonal encodings are dropped
@@ -3402,7 +3436,7 @@ int he_tune_table(const he_ctx *ctx, char *buf, size_t len) {
 }
 
 int he_tune_force(he_ctx *ctx, int op, int choice) {
-    if (!ctx || op < 0 || op > HE_TUNE_FUSE_CONV || choice < -1 || choice > 1) return HE_EINVAL;
+    if (!ctx || op < 0 || op > HE_TUNE_NTT_1PASS || choice < -1 || choice > 1) return HE_EINVAL;
     ctx->tune_force[op] = choice;
     return HE_OK;
 }

@@ -5,6 +5,8 @@
 // lives at base + (l / nper) * poly_stride + (l % nper) * N and uses modulus prime[l % nper].
 #include "he_kernels.cuh"
 
+#include <cooperative_groups.h>
+
 thread_local int he_pdl_launch = 1;   // see klaunch
 
 // ------------------------------------------------------------------------------------------
@@ -1186,4 +1188,167 @@ void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, 
         if (small_cta) launch_rb<3, 64>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
         else launch_rb<3, 256>(inverse, count, base, nper, poly_stride, map, mods, tw2, ninv, logN, st, src, src_stride, F);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// One-pass transforms of N = 2^16 limbs: one thread-block cluster of 8 CTAs (512 threads each)
+// per limb.  CTA q of the cluster runs the column pass on columns 32 q .. 32 q + 31 and the row
+// pass on rows 32 q .. 32 q + 31 (the two passes of the register-blocked transform above, same
+// butterflies and twiddles); the column pass's output goes to the row owners' shared memory
+// through distributed shared memory instead of HBM.  One launch and one read and one write of
+// the limb in HBM, instead of two of each.  The cluster barriers are reached by every thread of
+// every CTA (one limb per cluster, no early exit).
+namespace cg = cooperative_groups;
+
+#define HE_1P_NT 512
+#define HE_1P_CL 8
+#define HE_1P_RS (256 + 8)   // forward: row stride (words) of the received rows
+#define HE_1P_CS (32 + 4)    // inverse: row stride (words) of the received columns
+// shared memory: transposes (max(S * SUB, SP * SUB) = 272 * 32 words) and the exchange buffer
+// (max(32 * RS, 256 * CS) words)
+#define HE_1P_T_WORDS (272 * 32)
+#define HE_1P_X_WORDS (256 * HE_1P_CS)
+#define HE_1P_SMEM ((HE_1P_T_WORDS + HE_1P_X_WORDS) * 8)
+
+__global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
+    k_ntt_fwd_1pass(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods, const ulonglong2 *tw2,
+                    int logN, const uint64_t *src, long src_stride) {
+    grid_dep_enter();
+    constexpr int LOGE = 4, E = 16, S = 256, SUB = HE_1P_NT / E, SP = S + S / E;
+    extern __shared__ uint64_t dsm[];
+    uint64_t *T = dsm, *RB = dsm + HE_1P_T_WORDS;
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank();
+    const int N = 1 << logN, N2 = N / S, N1 = N / S;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t *in = src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a;
+    const uint64_t mq = mods[p].q;
+    const ulonglong2 *psi = tw2 + (long)p * 2 * N;
+    uint64_t v[E];
+    {   // column pass (stages m = 1 .. N1/2) on columns 32 q + c
+        const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = q * SUB + c;
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
+        ct_stages_strided<LOGE>(v, 1, 0, 0, psi, mq);
+#pragma unroll
+        for (int j = 0; j < E; j++) T[(k + E * j) * SUB + c] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = T[(E * k + j) * SUB + c];
+        ct_stages_strided<LOGE>(v, E, k, 1, psi, mq);
+        // element of row r = E k + j goes to the row owner r / SUB (the same CTA for all j)
+        cl.sync();   // every CTA of the cluster runs and has finished reading T
+        const int r0 = E * k;
+        uint64_t *dst = cl.map_shared_rank(RB, r0 / SUB);
+#pragma unroll
+        for (int j = 0; j < E; j++) dst[((r0 + j) % SUB) * HE_1P_RS + col] = v[j];
+        cl.sync();   // every row of this CTA has arrived
+    }
+    {   // row pass (stages m = N1 .. N/2) on rows 32 q + rr
+        const int k = threadIdx.x % E, rr = threadIdx.x / E, row = q * SUB + rr;
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = RB[rr * HE_1P_RS + k + E * j];
+        ct_stages_strided<LOGE>(v, N1, row, 1, psi, mq);
+#pragma unroll
+        for (int j = 0; j < E; j++) T[rr * SP + k + (E + 1) * j] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = T[rr * SP + (E + 1) * k + j];
+        ct_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, psi, mq);
+        // final reduction to [0, q) as in k_ntt_rows_fwd_rb
+        const uint32_t mu6 = (uint32_t)(mods[p].mu >> 57);
+        const int sh = mods[p].s - 6;
+        const uint64_t nq = 0 - mq;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const uint32_t kq = ((uint32_t)(v[j] >> sh) * mu6) >> 12;
+            uint64_t r = v[j] + (uint64_t)kq * nq;
+            if (r >= mq) r -= mq;
+            T[rr * SP + (E + 1) * k + j] = r;
+        }
+        __syncthreads();
+        uint64_t *g = a + (long)row * S;
+#pragma unroll
+        for (int j = 0; j < E; j++) g[k + E * j] = T[rr * SP + k + (E + 1) * j];
+    }
+}
+
+__global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
+    k_ntt_inv_1pass(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods, const ulonglong2 *tw2,
+                    const uint64_t *ninv, int logN, const uint64_t *src, long src_stride) {
+    grid_dep_enter();
+    constexpr int LOGE = 4, E = 16, S = 256, SUB = HE_1P_NT / E, SP = S + S / E;
+    extern __shared__ uint64_t dsm[];
+    uint64_t *T = dsm, *CB = dsm + HE_1P_T_WORDS;
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank();
+    const int N = 1 << logN, N2 = N / S, N1 = N / S;
+    const int l = blockIdx.y, p = map.prime[l % nper];
+    uint64_t *a = base + (long)(l / nper) * poly_stride + (long)(l % nper) * N;
+    const uint64_t *in = src ? src + (long)(l / nper) * src_stride + (long)(l % nper) * N : a;
+    const uint64_t mq = mods[p].q;
+    const ulonglong2 *ipsi = tw2 + (long)p * 2 * N + N;
+    uint64_t v[E];
+    {   // row pass (stages h = N/2 .. N1) on rows 32 q + rr
+        const int k = threadIdx.x % E, rr = threadIdx.x / E, row = q * SUB + rr;
+        const uint64_t *gi = in + (long)row * S;
+#pragma unroll
+        for (int j = 0; j < E; j++) T[rr * SP + k + (E + 1) * j] = gi[k + E * j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = T[rr * SP + (E + 1) * k + j];
+        __syncthreads();
+        gs_stages_strided<LOGE>(v, N1 * E, row * E + k, 1, ipsi, mq);
+#pragma unroll
+        for (int j = 0; j < E; j++) T[rr * SP + (E + 1) * k + j] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = T[rr * SP + k + (E + 1) * j];
+        gs_stages_strided<LOGE>(v, N1, row, 1, ipsi, mq);
+        // element of column col = k + E j goes to the column owner col / SUB (= j / 2)
+        cl.sync();   // every CTA of the cluster runs and has finished reading T
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int col = k + E * j;
+            uint64_t *dst = cl.map_shared_rank(CB, col / SUB);
+            dst[row * HE_1P_CS + col % SUB] = v[j];
+        }
+        cl.sync();   // every column of this CTA has arrived
+    }
+    {   // column pass (stages h = N1/2 .. 1), then the N^{-1} factor, on columns 32 q + c
+        const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = q * SUB + c;
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = CB[(E * k + j) * HE_1P_CS + c];
+        gs_stages_strided<LOGE>(v, E, k, 1, ipsi, mq);
+#pragma unroll
+        for (int j = 0; j < E; j++) T[(E * k + j) * SUB + c] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = T[(k + E * j) * SUB + c];
+        gs_stages_strided<LOGE>(v, 1, 0, 0, ipsi, mq);
+        const uint64_t ni = ninv[2 * p], nip = ninv[2 * p + 1];
+#pragma unroll
+        for (int j = 0; j < E; j++) a[(long)(k + E * j) * N2 + col] = mul_shoup(v[j], ni, nip, mq);
+    }
+}
+
+int ntt_1pass_setup() {
+    if (cudaFuncSetAttribute(k_ntt_fwd_1pass, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_1P_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_ntt_inv_1pass, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_1P_SMEM) != cudaSuccess)
+        return -1;
+    return 0;
+}
+
+void launch_ntt_1pass(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
+                      const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
+                      const uint64_t *src, long src_stride) {
+    dim3 g(HE_1P_CL, count);
+    if (inverse)
+        klaunch(k_ntt_inv_1pass, g, HE_1P_NT, HE_1P_SMEM, st)(base, nper, poly_stride, map, mods, tw2, ninv, logN, src,
+                                                          src_stride);
+    else
+        klaunch(k_ntt_fwd_1pass, g, HE_1P_NT, HE_1P_SMEM, st)(base, nper, poly_stride, map, mods, tw2, logN, src,
+                                                          src_stride);
 }

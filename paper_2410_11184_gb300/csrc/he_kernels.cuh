@@ -202,6 +202,15 @@ void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *
                      const LimbMap &tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all, int g,
                      int logN, int accumulate, const KsMulti &M);
 
+// one-pass transform of `count` limbs of N = 2^16 (no fused neighbours): one cluster of 8 CTAs per
+// limb, the exchange between the column and row passes in distributed shared memory; out of place
+// from src when given (as launch_ntt_rb).  ntt_1pass_setup() raises the kernels' dynamic shared
+// memory limit (once per device; 0 on success).
+int ntt_1pass_setup();
+void launch_ntt_1pass(bool inverse, int count, uint64_t *base, int nper, long poly_stride, const LimbMap &map,
+                      const ModC *mods, const ulonglong2 *tw2, const uint64_t *ninv, int logN, cudaStream_t st,
+                      const uint64_t *src, long src_stride);
+
 // register-blocked NTT of `count` limbs (N = 2^12: logE = 3, N = 2^16: logE = 4); launches
 // the column and row passes on stream st
 // the first pass reads from src (limb l of polynomial i at src + i src_stride + l N) when it is

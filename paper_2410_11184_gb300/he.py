@@ -430,7 +430,7 @@ class Context:
         return out
 
     # ---- autotuner (launch strategies; every variant gives the same words)
-    TUNE_OPS = ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small", "fuse_conv")
+    TUNE_OPS = ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small", "fuse_conv", "ntt_1pass")
 
     def autotune(self, levels, ncts, reps=2):
         lv = np.ascontiguousarray(levels, dtype=np.int32)
@@ -450,7 +450,7 @@ class Context:
 
     def tune_force(self, op, choice):
         """forces variant `choice` (0 or 1) of op ("modup", "rot", "lt_small", "lt_rows", "branches",
-        "ntt_small", "fuse_conv"); -1 restores"""
+        "ntt_small", "fuse_conv", "ntt_1pass"); -1 restores"""
         self.check(lib().he_tune_force(self.h, self.TUNE_OPS.index(op), choice))
 
     def selftest_bounded_wait(self, max_iter):

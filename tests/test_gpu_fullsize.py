@@ -29,12 +29,13 @@ def full(params):
     return g, ch, em
 
 
-@pytest.mark.parametrize("fuse_conv", [-1, 0, 1])
-def test_fullsize_ops_bit_exact(full, fuse_conv):
+@pytest.mark.parametrize("op,choice", [("fuse_conv", -1), ("fuse_conv", 0), ("fuse_conv", 1), ("ntt_1pass", 1)])
+def test_fullsize_ops_bit_exact(full, op, choice):
     """Multiplication (relinearise + rescale as one division) and rotation at level 12, limb for
     limb against the oracle; with the basis conversions as the default chooses (-1), forced
     separate (0) and forced into the forward transforms' column passes (1, NttFuse kinds 4-6 in
-    their N = 2^16 instances)."""
+    their N = 2^16 instances); and with every transform without fused neighbours as one pass per
+    limb cluster (ntt_1pass: in place, out of place, with the folded inverse factors)."""
     g, ch, em = full
     o = O.Oracle(ch)
     o.keygen(2024)
@@ -43,7 +44,7 @@ def test_fullsize_ops_bit_exact(full, fuse_conv):
     a = o.encrypt(rng.uniform(-1, 1, o.n0), top, 2.0 ** 42, 1, 0)
     b = o.encrypt(rng.uniform(-1, 1, o.n0), top, 2.0 ** 42, 1, 1)
     ga, gb = g.from_coeff(a.data, top, a.scale), g.from_coeff(b.data, top, b.scale)
-    g.tune_force("fuse_conv", fuse_conv)
+    g.tune_force(op, choice)
     try:
         assert np.array_equal(g.to_coeff(g.hmult(ga, gb))[0], o.hmult(a, b).data)
         assert np.array_equal(g.to_coeff(g.rotate(ga, 1))[0], o.rotate(a, 1).data)
@@ -54,8 +55,30 @@ def test_fullsize_ops_bit_exact(full, fuse_conv):
         got = g.to_coeff(g.hmult(two, two))
         assert np.array_equal(got[0], o.hmult(a, a).data) and np.array_equal(got[1], o.hmult(b, b).data)
     finally:
-        g.tune_force("fuse_conv", -1)
+        g.tune_force(op, -1)
         g.tune_force("modup", -1)
+
+
+@pytest.mark.parametrize("level", [0, 1, 12, 24])
+def test_fullsize_one_pass_transform_bit_exact(full, level):
+    """The one-pass transform (one cluster of 8 CTAs per limb, the passes' exchange in distributed
+    shared memory) gives the words of the two-pass transform, forward and inverse, on 2 to 50
+    limbs of uniform residues."""
+    g, ch, em = full
+    q = [int(v) for v in ch["q"]]
+    rng = np.random.default_rng(100 + level)
+    d = np.zeros((1, 2, level + 1, g.n), dtype=np.uint64)
+    for t in range(level + 1):
+        d[:, :, t] = rng.integers(0, q[t], (1, 2, g.n), dtype=np.uint64)
+    try:
+        g.tune_force("ntt_1pass", 0)
+        two = g.from_coeff(d, level, 1.0)
+        g.tune_force("ntt_1pass", 1)
+        one = g.from_coeff(d, level, 1.0)
+        assert torch.equal(one.tensor, two.tensor)
+        assert np.array_equal(g.to_coeff(one), d)
+    finally:
+        g.tune_force("ntt_1pass", -1)
 
 
 @pytest.mark.parametrize("m,kind", [(1, "uniform"), (1, "paper_normal"), (64, "attention")])

@@ -391,7 +391,7 @@ def test_autotune_variants_bit_identical(toybts):
         return np.random.default_rng(1000 + k)
 
     ref = run()
-    for op in ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small", "fuse_conv"):
+    for op in ("modup", "rot", "lt_small", "lt_rows", "branches", "ntt_small", "fuse_conv", "ntt_1pass"):
         for choice in (0, 1):
             g.tune_force(op, choice)
             got = run()
