@@ -287,7 +287,7 @@ int he_mod_raise(he_ctx *ctx, const he_ct *a, int top, he_ct *out);
  * column pass of the forward transform that follows them, so the converted limbs are never
  * written to HBM; 0: a conversion kernel, then the transform; timed on one relinearisation),
  * HE_TUNE_NTT_1PASS (N = 2^16 only: 1: a transform without fused neighbours as one launch, one
- * thread-block cluster of 8 CTAs per limb exchanging between its two passes in distributed shared
+ * thread-block cluster of 16 CTAs per limb exchanging between its two passes in distributed shared
  * memory; 0: the two passes; a ladder of limb counts per direction as for HE_TUNE_NTT_SMALL, off
  * until tuned).
  * Without a table entry the choice is 1 for batches of at most 4 ciphertexts (8 rows for

@@ -358,7 +358,7 @@ static dim3 grid_for(he_ctx *c, long total) {
 //   HE_TUNE_NTT_SMALL 1: the transform in CTAs of 64 threads (4 sub-transforms each); 0: 256
 //                     threads.  Chosen per direction from a ladder of limb counts (ntt_small).
 //   HE_TUNE_NTT_1PASS 1: a transform of N = 2^16 limbs without fused neighbours as one launch
-//                     per limb cluster (8 CTAs, the passes' exchange in distributed shared
+//                     per limb cluster (16 CTAs, the passes' exchange in distributed shared
 //                     memory); 0: the two register-blocked passes.  Per direction and limb count
 //                     from a ladder (ntt_1pass); off until tuned.
 //   HE_TUNE_FUSE_CONV 1: the basis conversions of ModUp and ModDown computed in the column pass

@@ -1191,26 +1191,28 @@ void launch_ntt_rb(int logE, bool inverse, int count, uint64_t *base, int nper, 
 }
 
 // ------------------------------------------------------------------------------------------
-// One-pass transforms of N = 2^16 limbs: one thread-block cluster of 8 CTAs (512 threads each)
-// per limb.  CTA q of the cluster runs the column pass on columns 32 q .. 32 q + 31 and the row
-// pass on rows 32 q .. 32 q + 31 (the two passes of the register-blocked transform above, same
+// One-pass transforms of N = 2^16 limbs: one thread-block cluster of CL = 4096 / NT CTAs of NT
+// threads per limb (NT = 256: 16 CTAs, a non-portable cluster size).  CTA q of the cluster runs
+// the column pass on columns SUB q .. SUB q + SUB - 1 and the row pass on rows SUB q .. SUB q +
+// SUB - 1, SUB = NT / 16 (the two passes of the register-blocked transform above, same
 // butterflies and twiddles); the column pass's output goes to the row owners' shared memory
 // through distributed shared memory instead of HBM.  One launch and one read and one write of
 // the limb in HBM, instead of two of each.  The cluster barriers are reached by every thread of
 // every CTA (one limb per cluster, no early exit).
 namespace cg = cooperative_groups;
 
-#define HE_1P_NT 512
-#define HE_1P_CL 8
-#define HE_1P_RS (256 + 8)   // forward: row stride (words) of the received rows
-#define HE_1P_CS (32 + 4)    // inverse: row stride (words) of the received columns
-// shared memory: transposes (max(S * SUB, SP * SUB) = 272 * 32 words) and the exchange buffer
-// (max(32 * RS, 256 * CS) words)
-#define HE_1P_T_WORDS (272 * 32)
-#define HE_1P_X_WORDS (256 * HE_1P_CS)
+#define HE_1P_NT 256
+#define HE_1P_SUB (HE_1P_NT / 16)
+#define HE_1P_CL (256 / HE_1P_SUB)
+#define HE_1P_RS (256 + 8)            // forward: row stride (words) of the received rows
+#define HE_1P_CS (HE_1P_SUB + 2)      // inverse: row stride (words) of the received columns
+// shared memory: transposes (SP * SUB words, SP = 272 >= S) and the exchange buffer
+// (max(SUB * RS, 256 * CS) words); three CTAs per SM
+#define HE_1P_T_WORDS (272 * HE_1P_SUB)
+#define HE_1P_X_WORDS (HE_1P_SUB * HE_1P_RS > 256 * HE_1P_CS ? HE_1P_SUB * HE_1P_RS : 256 * HE_1P_CS)
 #define HE_1P_SMEM ((HE_1P_T_WORDS + HE_1P_X_WORDS) * 8)
 
-__global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
+__global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 3)
     k_ntt_fwd_1pass(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods, const ulonglong2 *tw2,
                     int logN, const uint64_t *src, long src_stride) {
     grid_dep_enter();
@@ -1226,7 +1228,7 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
     const uint64_t mq = mods[p].q;
     const ulonglong2 *psi = tw2 + (long)p * 2 * N;
     uint64_t v[E];
-    {   // column pass (stages m = 1 .. N1/2) on columns 32 q + c
+    {   // column pass (stages m = 1 .. N1/2) on columns SUB q + c
         const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = q * SUB + c;
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = in[(long)(k + E * j) * N2 + col];
@@ -1245,7 +1247,7 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
         for (int j = 0; j < E; j++) dst[((r0 + j) % SUB) * HE_1P_RS + col] = v[j];
         cl.sync();   // every row of this CTA has arrived
     }
-    {   // row pass (stages m = N1 .. N/2) on rows 32 q + rr
+    {   // row pass (stages m = N1 .. N/2) on rows SUB q + rr
         const int k = threadIdx.x % E, rr = threadIdx.x / E, row = q * SUB + rr;
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = RB[rr * HE_1P_RS + k + E * j];
@@ -1275,7 +1277,7 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
     }
 }
 
-__global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
+__global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 3)
     k_ntt_inv_1pass(uint64_t *base, int nper, long poly_stride, LimbMap map, const ModC *mods, const ulonglong2 *tw2,
                     const uint64_t *ninv, int logN, const uint64_t *src, long src_stride) {
     grid_dep_enter();
@@ -1291,7 +1293,7 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
     const uint64_t mq = mods[p].q;
     const ulonglong2 *ipsi = tw2 + (long)p * 2 * N + N;
     uint64_t v[E];
-    {   // row pass (stages h = N/2 .. N1) on rows 32 q + rr
+    {   // row pass (stages h = N/2 .. N1) on rows SUB q + rr
         const int k = threadIdx.x % E, rr = threadIdx.x / E, row = q * SUB + rr;
         const uint64_t *gi = in + (long)row * S;
 #pragma unroll
@@ -1307,7 +1309,7 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = T[rr * SP + k + (E + 1) * j];
         gs_stages_strided<LOGE>(v, N1, row, 1, ipsi, mq);
-        // element of column col = k + E j goes to the column owner col / SUB (= j / 2)
+        // element of column col = k + E j goes to the column owner col / SUB
         cl.sync();   // every CTA of the cluster runs and has finished reading T
 #pragma unroll
         for (int j = 0; j < E; j++) {
@@ -1317,7 +1319,7 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
         }
         cl.sync();   // every column of this CTA has arrived
     }
-    {   // column pass (stages h = N1/2 .. 1), then the N^{-1} factor, on columns 32 q + c
+    {   // column pass (stages h = N1/2 .. 1), then the N^{-1} factor, on columns SUB q + c
         const int c = threadIdx.x % SUB, k = threadIdx.x / SUB, col = q * SUB + c;
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = CB[(E * k + j) * HE_1P_CS + c];
@@ -1337,6 +1339,10 @@ __global__ void __cluster_dims__(HE_1P_CL, 1, 1) __launch_bounds__(HE_1P_NT, 1)
 int ntt_1pass_setup() {
     if (cudaFuncSetAttribute(k_ntt_fwd_1pass, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_1P_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(k_ntt_inv_1pass, cudaFuncAttributeMaxDynamicSharedMemorySize, HE_1P_SMEM) != cudaSuccess)
+        return -1;
+    if (HE_1P_CL > 8 &&
+        (cudaFuncSetAttribute(k_ntt_fwd_1pass, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+         cudaFuncSetAttribute(k_ntt_inv_1pass, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess))
         return -1;
     return 0;
 }

@@ -202,7 +202,7 @@ void launch_ks_inner(dim3 grid, cudaStream_t st, uint64_t *acc, const uint64_t *
                      const LimbMap &tmap, const ModC *mods, const uint64_t *key, int key_nlimb, int nq_all, int g,
                      int logN, int accumulate, const KsMulti &M);
 
-// one-pass transform of `count` limbs of N = 2^16 (no fused neighbours): one cluster of 8 CTAs per
+// one-pass transform of `count` limbs of N = 2^16 (no fused neighbours): one cluster of 16 CTAs per
 // limb, the exchange between the column and row passes in distributed shared memory; out of place
 // from src when given (as launch_ntt_rb).  ntt_1pass_setup() raises the kernels' dynamic shared
 // memory limit (once per device; 0 on success).
