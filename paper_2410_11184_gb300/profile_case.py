@@ -11,6 +11,8 @@
                                                               # 64-thread CTAs (the autotuner's usual pick)
   python -m paper_2410_11184_gb300.profile_case keyswitch_fused   # keyswitch_small with the basis
                                                               # conversions fused into the transforms
+  python -m paper_2410_11184_gb300.profile_case keyswitch_1pass   # keyswitch_small with every plain
+                                                              # transform as one cluster launch per limb
 """
 import sys
 
@@ -29,10 +31,12 @@ def main(which):
         em = None
     g = he.Context(ch, em)
     g.keygen(5)
-    if which in ("keyswitch_small", "keyswitch_fused", "softmax", "softmax_alg2"):
+    if which in ("keyswitch_small", "keyswitch_fused", "keyswitch_1pass", "softmax", "softmax_alg2"):
         g.tune_force("ntt_small", 1)   # the transforms' 64-thread CTAs, the autotuner's pick at almost every size
     if which == "keyswitch_fused":
         g.tune_force("fuse_conv", 1)
+    if which == "keyswitch_1pass":
+        g.tune_force("ntt_1pass", 1)
     if which.startswith("softmax"):
         g.keygen_softmax(256, 1)
         x = workloads.attention_logits(128, 256, 1)
