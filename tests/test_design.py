@@ -152,3 +152,23 @@ def test_newton_refinement_loses_at_equal_depth(params):
     last = rows[-1]
     assert last[3] == last[6] == 7
     assert last[4] < 1e-6 and last[7] > 100 * last[4]
+
+
+def test_inverse_root_interpolant():
+    """design.inv_root_interp (the fit of the n = 32768 plan's degree-1023 rounds), at degree 63 on
+    the ratio-2^15 interval of those rounds: its coefficients are numpy's Chebyshev interpolant of
+    the same function at the same nodes, the error it reports is the relative error measured
+    independently on a grid, and it is within a factor 4 of the weighted minimax (LP) error of
+    the same degree, the best any polynomial of that degree can do on that grid."""
+    n, e, d = 32768, 0.25, 63
+    a, b = 0.98 / n, 1.02
+    c, err = D.inv_root_interp(e, a, b, d)
+    f = lambda u: (0.5 * (b - a) * u + 0.5 * (a + b)) ** -e
+    ref = np.polynomial.chebyshev.chebinterpolate(f, d)
+    assert np.allclose(c, ref, rtol=1e-10, atol=1e-12)
+    v = np.geomspace(a, b, 50001)
+    u = (2 * v - a - b) / (b - a)
+    measured = np.max(np.abs(np.polynomial.chebyshev.chebval(u, ref) * v ** e - 1.0))
+    assert measured <= err * (1 + 1e-6)
+    _, lp = D.weighted_minimax(lambda x: x ** -e, lambda x: x ** e, a, b, d)
+    assert lp <= err <= 4.0 * lp
